@@ -1,0 +1,101 @@
+"""Seeded synthetic inputs for the RS-SRI-GF2 self-energy path.
+
+This module only *draws inputs*; it holds none of the method's arithmetic
+(no screening, no metric root, no Green's function, no self-energy).  Both the
+CUDA path and the fp64 oracle are fed from here, so the two sides see the same
+arrays.
+
+The inputs stand in for the paper's hydrogen-dimer chains (Sec. IV: STO-3G AO
+basis, cc-pVDZ-RI auxiliary basis, beta = 50 1/Eh).  The real integrals and
+basis sets are not available, so a chain-like law is used instead:
+
+* 3-index integrals (ij|A) = N_aux^{-1/2} g_ijA exp(-|i-j|/decay), g ~ N(0,1)
+  drawn for i <= j and mirrored, so (ij|A) = (ji|A) (Eq. 5 symmetry);
+* Coulomb metric V = B B^T / N_aux + 0.5 I with B ~ N(0,1): symmetric positive
+  definite, condition number about 9 (Eq. 6 is SPD);
+* orbital energies: occupied linspace(-1.0, -0.2), virtual linspace(0.2, 2.0),
+  a 0.4 Eh gap with the chemical potential mu = 0 in the middle;
+* orbital coefficients: the orthogonal factor of the QR decomposition of an
+  N(0,1) matrix with diag(R) > 0, i.e. an orthonormal AO basis (S = I, Eq. 2);
+* imaginary-time grid: Gauss-Legendre in u = ln(1 + tau/tau_s) on
+  [0, ln(1 + beta/tau_s)], so dense near tau = 0 where G varies fastest; the
+  weights carry the Jacobian d tau / d u = tau + tau_s.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = ["System", "make_system", "tau_grid", "CONFIGS"]
+
+
+@dataclass
+class System:
+    """One synthetic problem, all arrays float64, C-contiguous."""
+
+    n: int
+    n_occ: int
+    n_aux: int
+    eri3: np.ndarray  # [n][n][n_aux], (ij|A)
+    metric: np.ndarray  # [n_aux][n_aux], V_AB
+    orb_e: np.ndarray  # [n], ascending; first n_occ occupied
+    orb_c: np.ndarray  # [n][n], AO x MO
+    mu: float
+    beta: float
+    tau: np.ndarray  # [n_tau] nodes in (0, beta)
+    tau_w: np.ndarray  # [n_tau] quadrature weights
+
+    @property
+    def n_tau(self) -> int:
+        return int(self.tau.shape[0])
+
+
+def tau_grid(n_tau: int, beta: float = 50.0, tau_s: float = 0.5):
+    """Gauss-Legendre nodes/weights in u = ln(1 + tau/tau_s) mapped to tau."""
+    x, w = np.polynomial.legendre.leggauss(n_tau)
+    umax = np.log1p(beta / tau_s)
+    u = 0.5 * (x + 1.0) * umax
+    wu = 0.5 * umax * w
+    tau = tau_s * np.expm1(u)
+    return np.ascontiguousarray(tau), np.ascontiguousarray(wu * (tau + tau_s))
+
+
+def make_system(n: int, n_occ: int, n_aux: int, n_tau: int, input_seed: int = 0,
+                beta: float = 50.0, tau_s: float = 0.5, decay: float = 3.0,
+                gap_lo: float = -0.2, gap_hi: float = 0.2) -> System:
+    if not (0 < n_occ < n):
+        raise ValueError("need 0 < n_occ < n")
+    rng = np.random.default_rng(input_seed)
+    # (ij|A): one draw per unordered pair i <= j, mirrored
+    g = rng.standard_normal((n, n, n_aux))
+    iu, ju = np.triu_indices(n, 1)
+    g[ju, iu, :] = g[iu, ju, :]
+    idx = np.arange(n)
+    damp = np.exp(-np.abs(idx[:, None] - idx[None, :]) / decay) / np.sqrt(n_aux)
+    eri3 = np.ascontiguousarray(g * damp[:, :, None])
+    # SPD metric
+    b = rng.standard_normal((n_aux, n_aux))
+    metric = b @ b.T / n_aux + 0.5 * np.eye(n_aux)
+    metric = np.ascontiguousarray(0.5 * (metric + metric.T))
+    # orbitals
+    orb_e = np.concatenate([np.linspace(-1.0, gap_lo, n_occ),
+                            np.linspace(gap_hi, 2.0, n - n_occ)])
+    q, r = np.linalg.qr(rng.standard_normal((n, n)))
+    q = q * np.sign(np.diag(r))[None, :]
+    tau, tau_w = tau_grid(n_tau, beta, tau_s)
+    return System(n=n, n_occ=n_occ, n_aux=n_aux, eri3=eri3, metric=metric,
+                  orb_e=np.ascontiguousarray(orb_e), orb_c=np.ascontiguousarray(q),
+                  mu=0.5 * (gap_lo + gap_hi), beta=beta, tau=tau, tau_w=tau_w)
+
+
+# The five workloads the method is exercised on (sizes only; eps is the K^L cut
+# of Eq. 13, eps_prime the (ij|A) screen of Eq. 11 at the paper's 0.02).
+CONFIGS = {
+    "c1_n20": dict(n=20, n_occ=10, n_aux=60, n_tau=32, n_s=64, eps=1e-2,
+                   eps_prime=0.02, seeds=(0,)),
+    "c2_n200": dict(n=200, n_occ=100, n_aux=600, n_tau=64, n_s=300, eps=1e-3,
+                    eps_prime=0.02, seeds=tuple(range(10))),
+    "c3_n1000": dict(n=1000, n_occ=500, n_aux=3000, n_tau=128, n_s=500, eps=1e-3,
+                     eps_prime=0.02, seeds=(0,)),
+}
