@@ -1,0 +1,265 @@
+/*
+ * rssri.h - C ABI of the GB300 (sm_103a) range-separated stochastic-RI GF2
+ * self-energy library, librssri.so.
+ *
+ * The library evaluates, on one GPU, the second-order (GF2) self-energy
+ * Sigma(tau) on an imaginary-time grid and the correlation energy per
+ * electron, with the electron-repulsion integrals split into a large part
+ * treated by deterministic RI and a remainder treated by stochastic RI
+ * (Dou, Chen, Takeshita, Baer, Neuhauser, Rabani, arXiv:2005.12338):
+ *
+ *   Sec. II, Eqs. 4-8    RI factorisation, K^Q_ij = sum_A (ij|A) V^{-1/2}_AQ
+ *   Sec. II, Eqs. 9-10   stochastic RI, R^xi_ij = sum_A (ij|A)(V^{-1/2} theta^xi)_A
+ *   Sec. II, Eqs. 11-16  range separation: (ij|A)^L screen, [K^Q]^L and its
+ *                        cut, R^L = [K]^L theta, R^S = R - R^L
+ *   Sec. III, Eq. 17     the imaginary-time Green's function G(tau)
+ *   Sec. III, Eq. 20/25  the GF2 self-energy and its RS-SRI form
+ *   Sec. IV, Eq. 26      E_corr = (1/N_e) int_0^beta Tr[Sigma(tau) G(beta-tau)]
+ *
+ * Conventions shared by every entry point
+ *   - All floating point is IEEE binary64 (double).
+ *   - Arrays are dense, row-major (C order), with the shapes stated below.
+ *   - Pointers are caller-owned.  The library never frees them and keeps no
+ *     reference to them after the call returns, except that rssri_setup()
+ *     copies the problem into handle-owned device memory.
+ *   - Every call returns an rssri_status (0 = success, negative = error) and
+ *     never throws.  On error nothing is written to the outputs except where
+ *     stated; the handle stays usable unless the code is RSSRI_ERR_CUDA.
+ *   - All device work is issued on the handle's stream; calls returning host
+ *     scalars synchronise that stream before they return.
+ *   - One handle per host thread at a time.  Handles do not share state.
+ *   - Results are deterministic: the same inputs, options and seed on the same
+ *     GPU give bitwise-identical outputs (fixed-order reductions, no
+ *     floating-point atomics).
+ */
+#ifndef RSSRI_H
+#define RSSRI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RSSRI_API __attribute__((visibility("default")))
+#else
+#define RSSRI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+typedef enum {
+  RSSRI_OK = 0,
+  RSSRI_ERR_INVALID_ARG = -1,     /* a size, threshold, pointer or option is out of range */
+  RSSRI_ERR_NOT_SPD = -2,         /* metric V is not symmetric positive definite (the
+                                     inverse-square-root iteration did not converge)  */
+  RSSRI_ERR_NONSYMMETRIC_ERI = -3,/* (ij|A) != (ji|A) for some i, j, A                */
+  RSSRI_ERR_OOM = -4,             /* device allocation failed                          */
+  RSSRI_ERR_CUDA = -5,            /* a CUDA runtime call failed; handle is unusable    */
+  RSSRI_ERR_TIMEOUT = -6,         /* a bounded device-side wait expired                */
+  RSSRI_ERR_NOT_READY = -7,       /* rssri_sigma before a successful rssri_setup       */
+  RSSRI_ERR_NONFINITE = -8        /* an input or result is NaN or infinite             */
+} rssri_status;
+
+/* Where the arrays of a call live. */
+enum { RSSRI_PTR_DEVICE = 0, RSSRI_PTR_HOST = 1 };
+
+/* Estimator.  RSSRI_EST_CV (default): Sigma = Sigma_DD + (1/N_s) sum_xi
+ * [F(R^xi, R'^xi) - F(R^Lxi, R'^Lxi)], where F(X, Y) is Eq. 20 evaluated on
+ * the rank-one integrals X(x)X and Y(x)Y and Sigma_DD is Eq. 20 on
+ * v^L = sum_Q [K^Q]^L [K^Q]^L; every bracket of Eq. 25 equals
+ * D + <R R> - <R^L R^L>, and this form keeps D D exact while pairing sample
+ * xi of theta with sample xi of theta'.
+ * RSSRI_EST_SRI: [K]^L is taken as empty, which is the plain stochastic RI of
+ * Eq. 10 (the eps -> 1 limit of Sec. II). */
+enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1 };
+
+/* Arithmetic of the chain products (Sec. III, Eq. 25). */
+enum { RSSRI_PREC_FP64 = 0 };
+
+typedef struct rssri_handle rssri_handle;
+
+/* The problem (Sec. II-III).
+ *   n       number of basis functions N            (1 <= n <= 4096)
+ *   n_occ   occupied orbitals, N_e = 2 n_occ       (1 <= n_occ <= n-1)
+ *   n_aux   auxiliary functions N_aux              (1 <= n_aux < 2^20)
+ *   n_tau   imaginary-time points                  (n_tau >= 1)
+ *   eri3    [n][n][n_aux]  (ij|A) of Eq. 5; must satisfy (ij|A) == (ji|A) exactly
+ *   metric  [n_aux][n_aux] V_AB of Eq. 6; symmetric positive definite
+ *   orb_e   [n]            orbital energies, the first n_occ occupied
+ *   orb_c   [n][n]         AO x MO coefficients, orthonormal (C^T C = I, S = I)
+ *   tau     [n_tau]        grid nodes, each in (0, beta)
+ *   tau_w   [n_tau]        quadrature weights of Eq. 26's tau integral
+ *   mu      chemical potential; beta inverse temperature (finite, > 0)
+ *   ptr_kind RSSRI_PTR_DEVICE or RSSRI_PTR_HOST, for all arrays above
+ * G is the zero-temperature non-interacting Green's function of the given
+ * orbitals (Eq. 17 with occupations 1 and 0):
+ *   G(tau) = -C_v exp(-(e_v - mu) tau) C_v^T,
+ *   G(beta - tau) = -C_o exp((e_o - mu) tau) C_o^T. */
+typedef struct {
+  int32_t n, n_occ, n_aux, n_tau;
+  int32_t ptr_kind;
+  int32_t reserved0;
+  const double *eri3;
+  const double *metric;
+  const double *orb_e;
+  const double *orb_c;
+  const double *tau;
+  const double *tau_w;
+  double mu, beta;
+} rssri_problem;
+
+/* Options.
+ *   eps_prime  epsilon' of Eq. 11, in [0, 1]: (ij|A) is kept when
+ *              |(ij|A)| >= (eps'/N) min(M_i, M_j), M_j = max_{i,A} |(ij|A)|
+ *              (the paper's per-j maximum, applied symmetrically).
+ *   eps        epsilon of Eq. 13, in [0, 1]: [K^Q_ij]^L is kept when
+ *              |[K^Q_ij]^L| >= eps * max |[K]^L| (global maximum).
+ *   n_s        number of stochastic sample pairs (theta^xi, theta'^xi), >= 2.
+ *   seed       64-bit seed of the counter-based Rademacher draws: theta^xi_Q
+ *              of set s (0: theta, 1: theta') is -1 when bit 63 of the first
+ *              SplitMix64 output from state seed XOR (s 2^60 + xi 2^20 + Q) is
+ *              set, else +1 (SplitMix64: Steele, Lea and Flood, OOPSLA 2014).
+ *   xi_offset  first sample index (resume: runs over [xi_offset, xi_offset+n_s)
+ *              concatenate exactly), xi_offset + n_s < 2^40.
+ *   estimator  RSSRI_EST_CV or RSSRI_EST_SRI.
+ *   precision  RSSRI_PREC_FP64.
+ *   pair_batch sample pairs processed per group of launches (0 = all).
+ *   profile    1: time every kernel class with CUDA events on the handle's
+ *              stream (rssri_stats.prof_*); 0: off. */
+typedef struct {
+  double eps_prime, eps;
+  int64_t n_s;
+  uint64_t seed;
+  int64_t xi_offset;
+  int32_t estimator;
+  int32_t precision;
+  int64_t pair_batch;
+  int32_t profile;
+  int32_t reserved0;
+} rssri_options;
+
+/* Kernel classes of the per-class profile (rssri_stats.prof_*). */
+enum {
+  RSSRI_PROF_CHAIN_GEMM = 0,  /* S8 chain products X G, (X G) Y, C Gb, (2 t I - B) C */
+  RSSRI_PROF_DD_SPMM = 1,     /* S7 exchange term, pair-space contraction         */
+  RSSRI_PROF_DD_GEMM = 2,     /* S7 other products                                */
+  RSSRI_PROF_FACTOR_GEMM = 3, /* S4/S5 theta W, R, R^L                             */
+  RSSRI_PROF_SETUP_GEMM = 4,  /* S1/S3 Newton-Schulz, [K]^L, D                     */
+  RSSRI_PROF_GREEN = 5,       /* S6                                               */
+  RSSRI_PROF_OTHER = 6,       /* screening, compaction, cuts, folds, reductions   */
+  RSSRI_PROF_NCLASS = 8
+};
+
+/* Counters of the last setup / sigma call. */
+typedef struct {
+  int64_t n_pairs_screened; /* (i,j) pairs with >= 1 kept (ij|A), Eq. 11        */
+  int64_t nnz_eri_l;        /* kept (ij|A) elements, Eq. 11                     */
+  int64_t n_pairs_large;    /* (i,j) pairs with a non-zero [K]^L row, Eq. 13     */
+  int64_t nnz_k_l;          /* non-zero [K^Q_ij]^L elements after the cut        */
+  double k_l_max;           /* max |[K^Q_ij]^L| before the cut                   */
+  int32_t metric_iterations;/* Newton-Schulz iterations used for V^{-1/2}       */
+  int32_t reserved0;
+  double metric_residual;   /* max |Z Y - I| at exit (Z ~ V^{-1/2}, Y ~ V^{1/2}) */
+  double e_dd;              /* Eq. 26 for the deterministic block alone          */
+  double e_corr;            /* Eq. 26 for the full estimate                      */
+  double e_stderr;          /* sample std of the per-pair energies / sqrt(n_s)   */
+  double t_setup_ms;        /* device time of rssri_setup                        */
+  double t_green_dd_ms;     /* device time of G(tau) and Sigma_DD(tau)           */
+  double t_sample_ms;       /* device time of theta, R, chains, energy, output   */
+  int64_t kernel_launches;  /* kernels launched by the last setup + sigma        */
+  int64_t prof_launches[RSSRI_PROF_NCLASS]; /* per class, last setup + sigma      */
+  double prof_ms[RSSRI_PROF_NCLASS];    /* device ms per class (profile = 1)     */
+  double prof_gflop[RSSRI_PROF_NCLASS]; /* algorithmic fp64 GFLOP per class: 2mnk
+                                           per product, 2 N_aux P^2 per S7 exchange
+                                           contraction (P kept pairs)            */
+} rssri_stats;
+
+/* ------------------------------------------------------------- lifetime */
+
+/* Create a handle bound to CUDA device `device` and stream `stream` (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream).  The
+ * handle owns all scratch device memory; nothing is allocated until
+ * rssri_setup(). */
+RSSRI_API int rssri_create(rssri_handle **out, int device, void *stream);
+
+/* Free the handle and its device memory.  NULL is accepted. */
+RSSRI_API void rssri_destroy(rssri_handle *h);
+
+/* Static description of a status code. */
+RSSRI_API const char *rssri_status_string(int code);
+
+/* ----------------------------------------------------------- the path */
+
+/* Steps that depend only on the system and the thresholds:
+ *   S1  W = V^{-1/2} (Eq. 7) by the coupled Newton-Schulz iteration (fp64);
+ *   S2  screen (ij|A) with eps' (Eq. 11) and compact the kept (i,j) pairs;
+ *   S3  [K]^L = (ij|A)^L W on the kept pairs (Eq. 12), cut at eps (Eq. 13),
+ *       and the pair-space product D = [K]^L [K]^L^T used by the exchange
+ *       part of the deterministic block.
+ * Copies the problem into handle-owned device memory (from host or device
+ * pointers, per p->ptr_kind).  Errors: INVALID_ARG (sizes, thresholds, null
+ * pointers, tau outside (0, beta)), NONSYMMETRIC_ERI, NOT_SPD, NONFINITE,
+ * OOM, CUDA. */
+RSSRI_API int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o);
+
+/* Steps that depend on the sample draws and on G, for every tau of the grid:
+ *   S4  theta, theta' (Rademacher) and u = W theta;
+ *   S5  R = (ij|A) u (Eq. 9), R^L = [K]^L theta (Eq. 14);
+ *   S6  G(tau), G(beta - tau) (Eq. 17);
+ *   S7  Sigma_DD(tau): Eq. 20 on v^L = sum_Q [K^Q]^L [K^Q]^L (fp64);
+ *   S8  per sample pair and factor pair (X, Y): C = X G Y, t = Tr(C Gb),
+ *       B = C Gb, accumulate (2 t C - B C) with weight +-1/N_s (Eq. 25);
+ *   S9  E_corr (Eq. 26, sign taken so that a Hartree-Fock G gives the MP2
+ *       energy per electron: E_corr = -(1/N_e) sum_tau w_tau Tr[Sigma Gb]),
+ *       per-pair energies and their standard error;
+ *   S10 sigma = (Sigma + Sigma^T)/2.
+ * Outputs (kind per the problem's ptr_kind):
+ *   sigma   [n_tau][n][n]  overwritten
+ *   e_pair  [n_s] per-pair estimates of E_corr (their mean is E_corr), or NULL
+ *   e_corr, e_stderr       host scalars, either may be NULL
+ *   st      host stats, may be NULL
+ * o->eps_prime and o->eps are ignored here: the split made by rssri_setup
+ * is used.  Errors: NOT_READY, INVALID_ARG, NONFINITE, OOM, CUDA. */
+RSSRI_API int rssri_sigma(rssri_handle *h, const rssri_options *o, double *sigma,
+                double *e_pair, double *e_corr, double *e_stderr,
+                rssri_stats *st);
+
+/* As rssri_sigma, but with G(tau) and G(beta - tau) supplied by the caller
+ * (the paper's general, e.g. self-consistent, G of Eq. 17) instead of being
+ * built from the orbitals: g and gb are [n_tau][n][n], each matrix symmetric,
+ * of the problem's ptr_kind. */
+RSSRI_API int rssri_sigma_from_g(rssri_handle *h, const rssri_options *o,
+                       const double *g, const double *gb, double *sigma,
+                       double *e_pair, double *e_corr, double *e_stderr,
+                       rssri_stats *st);
+
+/* ------------------------------------------------------- intermediates */
+
+/* Intermediates kept on the device after setup / sigma, for inspection. */
+typedef enum {
+  RSSRI_BUF_W = 0,          /* [n_aux][n_aux]       V^{-1/2}                           */
+  RSSRI_BUF_COLMAX = 1,     /* [n]                  M_j of Eq. 11                     */
+  RSSRI_BUF_ERI_L = 2,      /* [n][n][n_aux]        (ij|A)^L, zero where screened out */
+  RSSRI_BUF_K_L = 3,        /* [n][n][n_aux]        [K^Q_ij]^L after the cut          */
+  RSSRI_BUF_THETA = 4,      /* [2][n_s][n_aux]      theta, theta' as +-1.0            */
+  RSSRI_BUF_R = 5,          /* [2][n_s][n][n]       R for theta, theta'               */
+  RSSRI_BUF_R_L = 6,        /* [2][n_s][n][n]       R^L for theta, theta'             */
+  RSSRI_BUF_G = 7,          /* [n_tau][n][n]        G(tau)                            */
+  RSSRI_BUF_GB = 8,         /* [n_tau][n][n]        G(beta - tau)                     */
+  RSSRI_BUF_SIGMA_DD = 9,   /* [n_tau][n][n]        deterministic block               */
+  RSSRI_BUF_SIGMA_RAW = 10  /* [n_tau][n][n]        Sigma before symmetrisation       */
+} rssri_buffer;
+
+/* Size in bytes of an intermediate (0 if it does not exist yet). */
+RSSRI_API int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes);
+
+/* Copy an intermediate to `dst` (device or host per dst_kind); `bytes` must
+ * equal rssri_buffer_bytes().  Synchronises the handle's stream. */
+RSSRI_API int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSSRI_H */

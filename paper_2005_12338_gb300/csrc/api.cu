@@ -1,0 +1,808 @@
+// C ABI of librssri: handle, validation and the order of the steps of the
+// RS-SRI-GF2 self-energy path (see include/rssri.h for the contract).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace rssri;
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+cudaError_t ensure(DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  RS_TRY(cudaMalloc(&b.p, bytes));
+  b.bytes = bytes;
+  return cudaSuccess;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int map_err(cudaError_t e) {
+  if (e == cudaSuccess) return RSSRI_OK;
+  if (e == cudaErrorMemoryAllocation) return RSSRI_ERR_OOM;
+  return RSSRI_ERR_CUDA;
+}
+
+}  // namespace
+
+struct rssri_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev[6] = {};
+  bool ready = false;
+  bool broken = false;
+
+  // problem
+  int n = 0, n_occ = 0, n_aux = 0, n_tau = 0;
+  double mu = 0, beta = 0, eps_prime = 0, eps = 0;
+  int ptr_kind = RSSRI_PTR_DEVICE;
+  const double *eri3 = nullptr, *metric = nullptr, *orb_e = nullptr, *orb_c = nullptr,
+               *tau = nullptr, *tau_w = nullptr;
+  DevBuf in_eri3, in_metric, in_orb_e, in_orb_c, in_tau, in_tau_w;
+  std::vector<double> h_tau_w;
+
+  // setup products
+  DevBuf W, nsY, nsZ, nsP, nsT, nsY2, nsZ2, scal, part, flags;
+  DevBuf colmax, cnt, cscratch, cnum, csum, spairs, EL, KLs, cnt2, lidx, pij, prow, pcol, rowptr,
+      KP, D;
+  int P_s = 0, P = 0;
+  long long nnz_eri_l = 0, nnz_k_l = 0;
+  double k_l_max = 0, ns_resid = 0;
+  int ns_iters = 0;
+  float t_setup_ms = 0;
+
+  // sigma buffers
+  DevBuf theta, Ut, fac, RLp, G, Gb, cs, XG, Cc, Bm, BC, tarr, sarr, e_st, sig_raw, sdd, PG, At,
+      T, AP, Gam, L, trdd, tr, res, sig_out, e_pair, gwork, outbuf;
+  long long last_ns = 0;
+  bool have_sigma = false;
+  rssri_stats stats{};
+};
+
+namespace {
+
+// ----------------------------------------------------------- validation ----
+bool finite(double x) { return std::isfinite(x); }
+
+int validate_problem(const rssri_problem *p) {
+  if (!p) return RSSRI_ERR_INVALID_ARG;
+  if (p->n < 1 || p->n > 4096 || p->n_occ < 1 || p->n_occ > p->n - 1 || p->n_aux < 1 ||
+      p->n_aux >= (1 << 20) || p->n_tau < 1)
+    return RSSRI_ERR_INVALID_ARG;
+  if ((long long)p->n * p->n * (long long)p->n_aux > (1LL << 40)) return RSSRI_ERR_INVALID_ARG;
+  if (p->ptr_kind != RSSRI_PTR_DEVICE && p->ptr_kind != RSSRI_PTR_HOST)
+    return RSSRI_ERR_INVALID_ARG;
+  if (!p->eri3 || !p->metric || !p->orb_e || !p->orb_c || !p->tau || !p->tau_w)
+    return RSSRI_ERR_INVALID_ARG;
+  if (!finite(p->mu) || !finite(p->beta) || !(p->beta > 0)) return RSSRI_ERR_INVALID_ARG;
+  return RSSRI_OK;
+}
+
+int validate_options(const rssri_options *o, bool for_sigma) {
+  if (!o) return RSSRI_ERR_INVALID_ARG;
+  if (!(o->eps_prime >= 0.0 && o->eps_prime <= 1.0) || !(o->eps >= 0.0 && o->eps <= 1.0))
+    return RSSRI_ERR_INVALID_ARG;
+  if (for_sigma) {
+    if (o->n_s < 2 || o->n_s > (1LL << 30) || o->xi_offset < 0 ||
+        o->xi_offset + o->n_s >= (1LL << 40))
+      return RSSRI_ERR_INVALID_ARG;
+    if (o->estimator != RSSRI_EST_CV && o->estimator != RSSRI_EST_SRI) return RSSRI_ERR_INVALID_ARG;
+    if (o->precision != RSSRI_PREC_FP64) return RSSRI_ERR_INVALID_ARG;
+    if (o->pair_batch < 0) return RSSRI_ERR_INVALID_ARG;
+  }
+  return RSSRI_OK;
+}
+
+cudaError_t stage(DevBuf &dst, const double *src, size_t count, int kind, cudaStream_t s,
+                  const double **out) {
+  if (kind == RSSRI_PTR_DEVICE) {
+    *out = src;
+    return cudaSuccess;
+  }
+  RS_TRY(ensure(dst, count * sizeof(double)));
+  RS_TRY(cudaMemcpyAsync(dst.p, src, count * sizeof(double), cudaMemcpyHostToDevice, s));
+  *out = dst.as<double>();
+  return cudaSuccess;
+}
+
+// Copy a small device value to the host (synchronous on the stream).
+template <class T> cudaError_t fetch(T *h, const void *d, cudaStream_t s, size_t count = 1) {
+  RS_TRY(cudaMemcpyAsync(h, d, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
+  return cudaStreamSynchronize(s);
+}
+
+// Every product goes through here: grows the split-K scratch when needed.
+cudaError_t gemm(rssri_handle *h, const GemmArgs &g) {
+  const size_t need = dgemm_work_elems(g) * sizeof(double);
+  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
+  return dgemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
+}
+
+// ------------------------------------------------------------ S1: V^-1/2 --
+// Coupled Newton-Schulz iteration for the inverse square root: with
+// Y_0 = V / c, Z_0 = I and T_k = (3 I - Z_k Y_k) / 2, Y_{k+1} = Y_k T_k and
+// Z_{k+1} = T_k Z_k converge to (V/c)^{1/2} and (V/c)^{-1/2} whenever the
+// spectrum of V/c lies in (0, 1] (c = max row sum of |V| guarantees this for
+// an SPD V).  Stops one step after max |Z Y - I| < 1e-8; a non-SPD metric
+// never converges and is reported as NOT_SPD.
+int metric_inv_sqrt(rssri_handle *h, int *rc) {
+  cudaStream_t s = h->stream;
+  const int na = h->n_aux;
+  const size_t bytes = (size_t)na * na * sizeof(double);
+  cudaError_t e;
+#define RS_CK(x)                     \
+  do {                               \
+    e = (x);                         \
+    if (e != cudaSuccess) return map_err(e); \
+  } while (0)
+  RS_CK(ensure(h->W, bytes));
+  RS_CK(ensure(h->nsY, bytes));
+  RS_CK(ensure(h->nsZ, bytes));
+  RS_CK(ensure(h->nsP, bytes));
+  RS_CK(ensure(h->nsT, bytes));
+  RS_CK(ensure(h->nsY2, bytes));
+  RS_CK(ensure(h->nsZ2, bytes));
+  double *Y = h->nsY.as<double>(), *Z = h->nsZ.as<double>(), *Y2 = h->nsY2.as<double>(),
+         *Z2 = h->nsZ2.as<double>(), *Pm = h->nsP.as<double>(), *Tm = h->nsT.as<double>();
+  double *scal = h->scal.as<double>(), *part = h->part.as<double>();
+  RS_CK(ns_init(h->metric, na, Y, Z, scal, part, s));
+  GemmArgs g;
+  g.M = g.N = g.K = na;
+  g.lda = g.ldb = g.ldc = na;
+  const int max_it = 100;
+  double resid = 0;
+  bool final_step = false;
+  int it = 0;
+  for (; it < max_it; ++it) {
+    g.A = Z; g.B = Y; g.C = Pm;
+    RS_CK(gemm(h, g));
+    RS_CK(ns_tbuild(Pm, na, Tm, scal, part, s));
+    RS_CK(fetch(&resid, scal + 1, s));
+    if (!std::isfinite(resid) || resid > 1e6) break;
+    if (final_step) break;
+    if (resid < 1e-8) final_step = true;
+    g.A = Y; g.B = Tm; g.C = Y2;
+    RS_CK(gemm(h, g));
+    g.A = Tm; g.B = Z; g.C = Z2;
+    RS_CK(gemm(h, g));
+    std::swap(Y, Y2);
+    std::swap(Z, Z2);
+  }
+  h->ns_iters = it;
+  h->ns_resid = resid;
+  if (!final_step || !std::isfinite(resid) || resid > 1e-6) {
+    *rc = RSSRI_ERR_NOT_SPD;
+    return RSSRI_OK;
+  }
+  RS_CK(ns_finish(Z, na, scal, h->W.as<double>(), s));
+  *rc = RSSRI_OK;
+  return RSSRI_OK;
+#undef RS_CK
+}
+
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *rssri_status_string(int code) {
+  switch (code) {
+    case RSSRI_OK: return "ok";
+    case RSSRI_ERR_INVALID_ARG: return "invalid argument";
+    case RSSRI_ERR_NOT_SPD: return "metric is not symmetric positive definite";
+    case RSSRI_ERR_NONSYMMETRIC_ERI: return "3-index integrals are not symmetric in (i,j)";
+    case RSSRI_ERR_OOM: return "device memory allocation failed";
+    case RSSRI_ERR_CUDA: return "CUDA runtime error";
+    case RSSRI_ERR_TIMEOUT: return "bounded device wait expired";
+    case RSSRI_ERR_NOT_READY: return "rssri_setup has not completed on this handle";
+    case RSSRI_ERR_NONFINITE: return "non-finite input or result";
+    default: return "unknown status";
+  }
+}
+
+int rssri_create(rssri_handle **out, int device, void *stream) {
+  if (!out) return RSSRI_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) return RSSRI_ERR_CUDA;
+  if (device < 0 || device >= ndev) return RSSRI_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  rssri_handle *h = new (std::nothrow) rssri_handle();
+  if (!h) return RSSRI_ERR_OOM;
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(stream);
+  for (auto &e : h->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      rssri_destroy(h);
+      return RSSRI_ERR_CUDA;
+    }
+  cudaError_t e = ensure(h->scal, 64 * sizeof(double));
+  if (e == cudaSuccess) e = ensure(h->part, 8192 * sizeof(double));
+  if (e == cudaSuccess) e = ensure(h->flags, 16 * sizeof(int));
+  if (e != cudaSuccess) {
+    rssri_destroy(h);
+    return map_err(e);
+  }
+  *out = h;
+  return RSSRI_OK;
+}
+
+void rssri_destroy(rssri_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  DevBuf *bufs[] = {&h->in_eri3, &h->in_metric, &h->in_orb_e, &h->in_orb_c, &h->in_tau,
+                    &h->in_tau_w, &h->W, &h->nsY, &h->nsZ, &h->nsP, &h->nsT, &h->nsY2, &h->nsZ2,
+                    &h->scal, &h->part, &h->flags, &h->colmax, &h->cnt, &h->cscratch, &h->cnum,
+                    &h->csum, &h->spairs, &h->EL, &h->KLs, &h->cnt2, &h->lidx, &h->pij, &h->prow,
+                    &h->pcol, &h->rowptr, &h->KP, &h->D, &h->theta, &h->Ut, &h->fac, &h->RLp,
+                    &h->G, &h->Gb, &h->cs, &h->XG, &h->Cc, &h->Bm, &h->BC, &h->tarr, &h->sarr,
+                    &h->e_st, &h->sig_raw, &h->sdd, &h->PG, &h->At, &h->T, &h->AP, &h->Gam, &h->L,
+                    &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf};
+  for (DevBuf *b : bufs) release(*b);
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o) {
+  if (!h) return RSSRI_ERR_INVALID_ARG;
+  if (h->broken) return RSSRI_ERR_CUDA;
+  int rc = validate_problem(p);
+  if (rc) return rc;
+  rc = validate_options(o, false);
+  if (rc) return rc;
+  if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  cudaStream_t s = h->stream;
+  h->ready = false;
+  h->have_sigma = false;
+  const int n = p->n, na = p->n_aux, nt = p->n_tau;
+  const long long nn = (long long)n * n;
+  cudaError_t e;
+#define RS_CK(x)                                       \
+  do {                                                 \
+    e = (x);                                           \
+    if (e != cudaSuccess) {                            \
+      int _r = map_err(e);                             \
+      if (_r == RSSRI_ERR_CUDA) h->broken = true;      \
+      return _r;                                       \
+    }                                                  \
+  } while (0)
+
+  // tau grid checks need host copies of the nodes
+  std::vector<double> htau(nt), htw(nt);
+  if (p->ptr_kind == RSSRI_PTR_HOST) {
+    std::memcpy(htau.data(), p->tau, nt * sizeof(double));
+    std::memcpy(htw.data(), p->tau_w, nt * sizeof(double));
+  } else {
+    RS_CK(cudaMemcpyAsync(htau.data(), p->tau, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RS_CK(cudaMemcpyAsync(htw.data(), p->tau_w, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RS_CK(cudaStreamSynchronize(s));
+  }
+  for (int k = 0; k < nt; ++k)
+    if (!(htau[k] > 0.0 && htau[k] < p->beta) || !std::isfinite(htw[k]))
+      return RSSRI_ERR_INVALID_ARG;
+
+  RS_CK(cudaEventRecord(h->ev[0], s));
+  h->n = n; h->n_occ = p->n_occ; h->n_aux = na; h->n_tau = nt;
+  h->mu = p->mu; h->beta = p->beta; h->ptr_kind = p->ptr_kind;
+  h->eps_prime = o->eps_prime; h->eps = o->eps;
+  h->h_tau_w = htw;
+  RS_CK(stage(h->in_eri3, p->eri3, (size_t)nn * na, p->ptr_kind, s, &h->eri3));
+  RS_CK(stage(h->in_metric, p->metric, (size_t)na * na, p->ptr_kind, s, &h->metric));
+  RS_CK(stage(h->in_orb_e, p->orb_e, n, p->ptr_kind, s, &h->orb_e));
+  RS_CK(stage(h->in_orb_c, p->orb_c, (size_t)nn, p->ptr_kind, s, &h->orb_c));
+  RS_CK(stage(h->in_tau, p->tau, nt, p->ptr_kind, s, &h->tau));
+  RS_CK(stage(h->in_tau_w, p->tau_w, nt, p->ptr_kind, s, &h->tau_w));
+
+  // input checks: symmetry of (ij|A), finiteness of everything
+  int *flags = h->flags.as<int>();
+  RS_CK(cudaMemsetAsync(flags, 0, 16 * sizeof(int), s));
+  RS_CK(eri_check(h->eri3, n, na, flags, s));
+  RS_CK(nonfinite_check(h->metric, (long long)na * na, flags + 1, s));
+  RS_CK(nonfinite_check(h->orb_e, n, flags + 1, s));
+  RS_CK(nonfinite_check(h->orb_c, nn, flags + 1, s));
+  int hflags[2];
+  RS_CK(fetch(hflags, flags, s, 2));
+  if (hflags[1]) return RSSRI_ERR_NONFINITE;
+  if (hflags[0]) return RSSRI_ERR_NONSYMMETRIC_ERI;
+
+  // scratch: split-K partials of the products, per-block partial maxima / row sums
+  RS_CK(ensure(h->gwork, (size_t)16 << 20));
+  RS_CK(ensure(h->part, (size_t)std::max(8192, na) * sizeof(double)));
+
+  // S1
+  int ns_rc = RSSRI_OK;
+  rc = metric_inv_sqrt(h, &ns_rc);
+  if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
+  if (ns_rc) return ns_rc;
+
+  // S2: screen (Eq. 11) and compact the kept pairs
+  RS_CK(ensure(h->colmax, n * sizeof(double)));
+  RS_CK(ensure(h->cnt, nn * sizeof(int)));
+  RS_CK(ensure(h->cscratch, compact_scratch_bytes((int)nn)));
+  RS_CK(ensure(h->cnum, 4 * sizeof(int)));
+  RS_CK(ensure(h->csum, 4 * sizeof(long long)));
+  RS_CK(ensure(h->spairs, nn * sizeof(int)));
+  RS_CK(eri_colmax(h->eri3, n, na, h->colmax.as<double>(), s));
+  RS_CK(eri_pair_count(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime, h->cnt.as<int>(), s));
+  RS_CK(compact(h->cnt.as<int>(), (int)nn, h->spairs.as<int>(), h->cnum.as<int>(),
+                h->csum.as<long long>(), h->cscratch.p, s));
+  int P_s = 0;
+  long long nnz = 0;
+  RS_CK(fetch(&P_s, h->cnum.p, s));
+  RS_CK(fetch(&nnz, h->csum.p, s));
+  h->P_s = P_s;
+  h->nnz_eri_l = nnz;
+
+  // S3: K^L rows of the screened pairs (Eq. 12), global max and cut (Eq. 13)
+  RS_CK(ensure(h->EL, (size_t)std::max(P_s, 1) * na * sizeof(double)));
+  RS_CK(ensure(h->KLs, (size_t)std::max(P_s, 1) * na * sizeof(double)));
+  RS_CK(ensure(h->cnt2, (size_t)std::max(P_s, 1) * sizeof(int)));
+  RS_CK(ensure(h->lidx, (size_t)std::max(P_s, 1) * sizeof(int)));
+  int P = 0;
+  long long nnzk = 0;
+  double kmax = 0;
+  if (P_s > 0) {
+    RS_CK(eri_gather_rows(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime,
+                          h->spairs.as<int>(), P_s, h->EL.as<double>(), s));
+    GemmArgs g;
+    g.M = P_s; g.N = na; g.K = na;
+    g.A = h->EL.as<double>(); g.lda = na;
+    g.B = h->W.as<double>(); g.ldb = na;
+    g.C = h->KLs.as<double>(); g.ldc = na;
+    RS_CK(gemm(h, g));
+    double *scal = h->scal.as<double>();
+    RS_CK(absmax(h->KLs.as<double>(), (long long)P_s * na, scal + 2, h->part.as<double>(), s));
+    RS_CK(kl_cut(h->KLs.as<double>(), P_s, na, scal + 2, o->eps, h->cnt2.as<int>(), s));
+    RS_CK(compact(h->cnt2.as<int>(), P_s, h->lidx.as<int>(), h->cnum.as<int>(),
+                  h->csum.as<long long>(), h->cscratch.p, s));
+    RS_CK(fetch(&P, h->cnum.p, s));
+    RS_CK(fetch(&nnzk, h->csum.p, s));
+    RS_CK(fetch(&kmax, scal + 2, s));
+  }
+  h->P = P;
+  h->nnz_k_l = nnzk;
+  h->k_l_max = kmax;
+  RS_CK(ensure(h->pij, (size_t)std::max(P, 1) * sizeof(int)));
+  RS_CK(ensure(h->prow, (size_t)std::max(P, 1) * sizeof(int)));
+  RS_CK(ensure(h->pcol, (size_t)std::max(P, 1) * sizeof(int)));
+  RS_CK(ensure(h->rowptr, (size_t)(n + 1) * sizeof(int)));
+  RS_CK(ensure(h->KP, (size_t)std::max(P, 1) * na * sizeof(double)));
+  RS_CK(ensure(h->D, (size_t)std::max(P, 1) * std::max(P, 1) * sizeof(double)));
+  if (P > 0) {
+    RS_CK(gather_int(h->spairs.as<int>(), h->lidx.as<int>(), P, h->pij.as<int>(), s));
+    RS_CK(gather_rows(h->KLs.as<double>(), h->lidx.as<int>(), P, na, h->KP.as<double>(), s));
+    // D[a][b] = sum_Q K_P[a][Q] K_P[b][Q] = v^L for the pair of pairs (Eq. 8 on [K]^L)
+    GemmArgs g;
+    g.M = P; g.N = P; g.K = na;
+    g.A = h->KP.as<double>(); g.lda = na;
+    g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1;
+    g.C = h->D.as<double>(); g.ldc = P;
+    RS_CK(gemm(h, g));
+  }
+  RS_CK(pair_csr(h->pij.as<int>(), P, n, h->rowptr.as<int>(), h->prow.as<int>(),
+                 h->pcol.as<int>(), s));
+  RS_CK(cudaEventRecord(h->ev[1], s));
+  RS_CK(cudaEventSynchronize(h->ev[1]));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+  h->t_setup_ms = ms;
+  h->ready = true;
+  return RSSRI_OK;
+#undef RS_CK
+}
+
+}  // extern "C"
+
+namespace {
+
+// S6 for all tau: G(tau) = -C_v e^{-(e_v-mu)tau} C_v^T, Gb(tau) = -C_o e^{(e_o-mu)tau} C_o^T.
+cudaError_t build_green(rssri_handle *h) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, no = h->n_occ, nv = n - no, nt = h->n_tau;
+  const long long nn = (long long)n * n;
+  RS_TRY(ensure(h->cs, (size_t)nt * n * std::max(no, nv) * sizeof(double)));
+  for (int occ = 0; occ < 2; ++occ) {
+    const int off = occ ? 0 : no, m = occ ? no : nv;
+    double *out = occ ? h->Gb.as<double>() : h->G.as<double>();
+    RS_TRY(green_scale(h->orb_c, h->orb_e, n, off, m, h->mu, h->tau, nt, occ ? 1 : -1,
+                       h->cs.as<double>(), s));
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = m; g.batch = nt;
+    g.A = h->cs.as<double>(); g.lda = m; g.sA = (long long)n * m;
+    g.B = h->orb_c + off; g.ldb = n; g.transB = 1; g.sB = 0;
+    g.C = out; g.ldc = n; g.sC = nn;
+    g.alpha = -1.0;
+    RS_TRY(gemm(h, g));
+  }
+  return cudaSuccess;
+}
+
+// S7 for one tau: the deterministic block, Eq. 20 on v^L = sum_Q K^Q K^Q with
+// K = [K]^L.  With PG^Q = K^Q G, At^Q = Gb K^Q G, Gamma_QQ' = Tr(K^Q G K^Q' Gb),
+// L^Q = sum_Q' Gamma_QQ' K^Q' and T^Q = sum_Q' K^Q' At^Q K^Q' (built in pair
+// space from D = v^L):  Sigma_DD = sum_Q K^Q G (2 L^Q - T^Q).
+cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, double *out) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, P = h->P;
+  const long long nn = (long long)n * n;
+  if (P == 0) return cudaMemsetAsync(out, 0, nn * sizeof(double), s);
+  double *PG = h->PG.as<double>(), *At = h->At.as<double>(), *T = h->T.as<double>();
+  // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]
+  RS_TRY(dgemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), G, n,
+                         h->KP.as<double>(), na, PG, na, (long long)n * na, s));
+  // At[k][(l,Q)] = sum_m Gb[k][m] PG[m][(l,Q)]
+  {
+    GemmArgs g;
+    g.M = n; g.N = n * na; g.K = n;
+    g.A = Gb; g.lda = n;
+    g.B = PG; g.ldb = (long long)n * na;
+    g.C = At; g.ldc = (long long)n * na;
+    RS_TRY(gemm(h, g));
+  }
+  // T[m][Q][j] = sum_{a in row m, b in row j} D[a][b] At[(col a, col b)][Q]
+  RS_TRY(dd_exchange_spmm(h->rowptr.as<int>(), h->pcol.as<int>(), h->D.as<double>(), P, At, n, na,
+                          T, s));
+  // Gamma = K_P^T At_P, At_P the rows of At at the kept pairs
+  RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s));
+  {
+    GemmArgs g;
+    g.M = na; g.N = na; g.K = P;
+    g.A = h->KP.as<double>(); g.lda = na; g.transA = 1;
+    g.B = h->AP.as<double>(); g.ldb = na;
+    g.C = h->Gam.as<double>(); g.ldc = na;
+    RS_TRY(gemm(h, g));
+  }
+  // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
+  {
+    GemmArgs g;
+    g.M = P; g.N = na; g.K = na;
+    g.A = h->KP.as<double>(); g.lda = na;
+    g.B = h->Gam.as<double>(); g.ldb = na; g.transB = 1;
+    g.C = h->L.as<double>(); g.ldc = na;
+    RS_TRY(gemm(h, g));
+  }
+  RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s));
+  // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n]
+  {
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = n * na;
+    g.A = PG; g.lda = (long long)n * na;
+    g.B = T; g.ldb = n;
+    g.C = out; g.ldc = n;
+    g.alpha = -1.0;
+    RS_TRY(gemm(h, g));
+  }
+  return cudaSuccess;
+}
+
+size_t dd_work_need(rssri_handle *h) {
+  const int n = h->n, na = h->n_aux, P = std::max(h->P, 1);
+  size_t w = 0;
+  GemmArgs g;
+  g.M = na; g.N = na; g.K = P; w = std::max(w, dgemm_work_elems(g));
+  g.M = P; g.N = na; g.K = na; w = std::max(w, dgemm_work_elems(g));
+  g.M = n; g.N = n; g.K = n * na; w = std::max(w, dgemm_work_elems(g));
+  g.M = n; g.N = n * na; g.K = n; w = std::max(w, dgemm_work_elems(g));
+  return w;
+}
+
+int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const double *gb_in,
+              double *sigma, double *e_pair, double *e_corr, double *e_stderr, rssri_stats *st) {
+  if (!h) return RSSRI_ERR_INVALID_ARG;
+  if (h->broken) return RSSRI_ERR_CUDA;
+  if (!h->ready) return RSSRI_ERR_NOT_READY;
+  int rc = validate_options(o, true);
+  if (rc) return rc;
+  if (!sigma) return RSSRI_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, nt = h->n_tau;
+  const int ns = (int)o->n_s;
+  const long long nn = (long long)n * n;
+  const bool sri = o->estimator == RSSRI_EST_SRI;
+  const int P = sri ? 0 : h->P;
+  const int nb = (o->pair_batch > 0) ? (int)std::min<long long>(o->pair_batch, ns) : ns;
+  const int has_l = sri ? 0 : 1;
+  const int nbat2 = nb * (1 + has_l);
+  cudaError_t e;
+#define RS_CK(x)                                       \
+  do {                                                 \
+    e = (x);                                           \
+    if (e != cudaSuccess) {                            \
+      int _r = map_err(e);                             \
+      if (_r == RSSRI_ERR_CUDA) h->broken = true;      \
+      return _r;                                       \
+    }                                                  \
+  } while (0)
+
+  RS_CK(cudaEventRecord(h->ev[2], s));
+  // ---- buffers
+  RS_CK(ensure(h->G, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->Gb, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->sdd, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->sig_raw, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->sig_out, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->trdd, nt * sizeof(double)));
+  RS_CK(ensure(h->tr, nt * sizeof(double)));
+  RS_CK(ensure(h->res, 8 * sizeof(double)));
+  RS_CK(ensure(h->theta, (size_t)2 * ns * na * sizeof(double)));
+  RS_CK(ensure(h->Ut, (size_t)2 * ns * na * sizeof(double)));
+  RS_CK(ensure(h->fac, (size_t)4 * ns * nn * sizeof(double)));  // [set][kind][xi][n][n]
+  RS_CK(ensure(h->RLp, (size_t)2 * ns * std::max(h->P, 1) * sizeof(double)));
+  RS_CK(ensure(h->XG, (size_t)nbat2 * nn * sizeof(double)));
+  RS_CK(ensure(h->Cc, (size_t)nbat2 * nn * sizeof(double)));
+  RS_CK(ensure(h->Bm, (size_t)nbat2 * nn * sizeof(double)));
+  RS_CK(ensure(h->BC, (size_t)nbat2 * nn * sizeof(double)));
+  RS_CK(ensure(h->tarr, nbat2 * sizeof(double)));
+  RS_CK(ensure(h->sarr, nbat2 * sizeof(double)));
+  RS_CK(ensure(h->e_st, ns * sizeof(double)));
+  RS_CK(ensure(h->e_pair, ns * sizeof(double)));
+  if (P > 0) {
+    RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
+    RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
+    RS_CK(ensure(h->T, (size_t)nn * na * sizeof(double)));
+    RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
+    RS_CK(ensure(h->L, (size_t)P * na * sizeof(double)));
+    RS_CK(ensure(h->Gam, (size_t)na * na * sizeof(double)));
+    RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));
+  }
+  double *G = h->G.as<double>(), *Gb = h->Gb.as<double>();
+
+  // ---- S6: G(tau), G(beta - tau)
+  if (g_in) {
+    const cudaMemcpyKind k = h->ptr_kind == RSSRI_PTR_HOST ? cudaMemcpyHostToDevice
+                                                           : cudaMemcpyDeviceToDevice;
+    RS_CK(cudaMemcpyAsync(G, g_in, nt * nn * sizeof(double), k, s));
+    RS_CK(cudaMemcpyAsync(Gb, gb_in, nt * nn * sizeof(double), k, s));
+  } else {
+    RS_CK(build_green(h));
+  }
+  // ---- S7: deterministic block per tau
+  for (int t = 0; t < nt; ++t) {
+    double *out = h->sdd.as<double>() + t * nn;
+    if (sri) RS_CK(cudaMemsetAsync(out, 0, nn * sizeof(double), s));
+    else RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out));
+  }
+  RS_CK(cudaEventRecord(h->ev[3], s));
+
+  // ---- S4: theta, theta' and U^T = theta W (W symmetric)
+  double *theta = h->theta.as<double>(), *Ut = h->Ut.as<double>(), *fac = h->fac.as<double>();
+  for (int set = 0; set < 2; ++set)
+    RS_CK(rademacher(o->seed, set, o->xi_offset, ns, na, theta + (long long)set * ns * na, s));
+  {
+    GemmArgs g;
+    g.M = ns; g.N = na; g.K = na; g.batch = 2;
+    g.A = theta; g.lda = na; g.sA = (long long)ns * na;
+    g.B = h->W.as<double>(); g.ldb = na; g.sB = 0;
+    g.C = Ut; g.ldc = na; g.sC = (long long)ns * na;
+    RS_CK(gemm(h, g));
+  }
+  // ---- S5: R[set][xi][ij] = sum_A U^T[xi][A] (ij|A); R^L from the kept pairs
+  {
+    GemmArgs g;
+    g.M = ns; g.N = (int)nn; g.K = na; g.batch = 2;
+    g.A = Ut; g.lda = na; g.sA = (long long)ns * na;
+    g.B = h->eri3; g.ldb = na; g.transB = 1; g.sB = 0;
+    g.C = fac; g.ldc = nn; g.sC = 2LL * ns * nn;  // kind 0 of each set
+    RS_CK(gemm(h, g));
+  }
+  for (int set = 0; set < 2; ++set) {
+    double *rl = fac + (2LL * set + 1) * ns * nn;
+    RS_CK(cudaMemsetAsync(rl, 0, (size_t)ns * nn * sizeof(double), s));
+  }
+  if (P > 0) {
+    GemmArgs g;
+    g.M = ns; g.N = P; g.K = na; g.batch = 2;
+    g.A = theta; g.lda = na; g.sA = (long long)ns * na;
+    g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1; g.sB = 0;
+    g.C = h->RLp.as<double>(); g.ldc = P; g.sC = (long long)ns * P;
+    RS_CK(gemm(h, g));
+    for (int set = 0; set < 2; ++set)
+      RS_CK(scatter_pairs(h->RLp.as<double>() + (long long)set * ns * P, ns, P, h->pij.as<int>(),
+                          nn, nn, fac + (2LL * set + 1) * ns * nn, s));
+  }
+
+  // ---- S8: chains per tau and batch of sample pairs
+  RS_CK(cudaMemsetAsync(h->e_st.p, 0, ns * sizeof(double), s));
+  const double ne = 2.0 * h->n_occ;
+  double *XG = h->XG.as<double>(), *Cc = h->Cc.as<double>(), *Bm = h->Bm.as<double>(),
+         *BC = h->BC.as<double>();
+  for (int t = 0; t < nt; ++t) {
+    const double *Gt = G + t * nn, *Gbt = Gb + t * nn;
+    double *sig = h->sig_raw.as<double>() + t * nn;
+    for (int x0 = 0; x0 < ns; x0 += nb) {
+      const int cnt = std::min(nb, ns - x0);
+      // the batch is [kind][x] with kind 0 = (R, R'), kind 1 = (R^L, R'^L)
+      for (int kind = 0; kind <= has_l; ++kind) {
+        const double *X = fac + ((0LL * 2 + kind) * ns + x0) * nn;
+        const double *Y = fac + ((1LL * 2 + kind) * ns + x0) * nn;
+        double *xg = XG + (long long)kind * cnt * nn, *c = Cc + (long long)kind * cnt * nn,
+               *bm = Bm + (long long)kind * cnt * nn;
+        GemmArgs g;
+        g.M = n; g.N = n; g.K = n; g.batch = cnt;
+        g.lda = g.ldb = g.ldc = n;
+        g.A = X; g.sA = nn; g.B = Gt; g.sB = 0; g.C = xg; g.sC = nn;   // X G
+        RS_CK(gemm(h, g));
+        g.A = xg; g.sA = nn; g.B = Y; g.sB = nn; g.C = c; g.sC = nn;   // C = X G Y
+        RS_CK(gemm(h, g));
+        g.A = c; g.sA = nn; g.B = Gbt; g.sB = 0; g.C = bm; g.sC = nn;  // B = C Gb
+        RS_CK(gemm(h, g));
+      }
+      const int tot = cnt * (1 + has_l);
+      // t = Tr B, s2 = Tr B B, B <- +-(2 t I - B)
+      RS_CK(chain_fold(Bm, tot, cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s));
+      {
+        GemmArgs g;
+        g.M = n; g.N = n; g.K = n; g.batch = tot;
+        g.lda = g.ldb = g.ldc = n;
+        g.A = Bm; g.sA = nn; g.B = Cc; g.sB = nn; g.C = BC; g.sC = nn;  // (2tI - B) C
+        RS_CK(gemm(h, g));
+      }
+      RS_CK(sigma_accumulate(BC, cnt, has_l, n, (double)ns, h->sdd.as<double>() + t * nn,
+                             x0 == 0, sig, s));
+      RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, has_l, h->h_tau_w[t], ne,
+                        h->e_st.as<double>() + x0, s));
+    }
+  }
+  // ---- S10 and S9
+  RS_CK(symmetrize(h->sig_raw.as<double>(), n, nt, h->sig_out.as<double>(), s));
+  RS_CK(trace_prod(h->sdd.as<double>(), Gb, n, nt, h->trdd.as<double>(), s));
+  RS_CK(trace_prod(h->sig_out.as<double>(), Gb, n, nt, h->tr.as<double>(), s));
+  RS_CK(energy_finalize(h->tau_w, h->trdd.as<double>(), h->tr.as<double>(), nt, ne,
+                        h->e_st.as<double>(), ns, h->e_pair.as<double>(), h->res.as<double>(), s));
+  const cudaMemcpyKind dk = h->ptr_kind == RSSRI_PTR_HOST ? cudaMemcpyDeviceToHost
+                                                          : cudaMemcpyDeviceToDevice;
+  RS_CK(cudaMemcpyAsync(sigma, h->sig_out.p, nt * nn * sizeof(double), dk, s));
+  if (e_pair) RS_CK(cudaMemcpyAsync(e_pair, h->e_pair.p, ns * sizeof(double), dk, s));
+  RS_CK(cudaEventRecord(h->ev[4], s));
+  double res[4];
+  RS_CK(cudaMemcpyAsync(res, h->res.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RS_CK(cudaStreamSynchronize(s));
+  h->last_ns = ns;
+  h->have_sigma = true;
+  float t_dd = 0, t_samp = 0;
+  cudaEventElapsedTime(&t_dd, h->ev[2], h->ev[3]);
+  cudaEventElapsedTime(&t_samp, h->ev[3], h->ev[4]);
+  rssri_stats &S = h->stats;
+  S.n_pairs_screened = h->P_s;
+  S.nnz_eri_l = h->nnz_eri_l;
+  S.n_pairs_large = h->P;
+  S.nnz_k_l = h->nnz_k_l;
+  S.k_l_max = h->k_l_max;
+  S.metric_iterations = h->ns_iters;
+  S.metric_residual = h->ns_resid;
+  S.e_dd = res[0];
+  S.e_corr = res[1];
+  S.e_stderr = res[3];
+  S.t_setup_ms = h->t_setup_ms;
+  S.t_green_dd_ms = t_dd;
+  S.t_sample_ms = t_samp;
+  if (e_corr) *e_corr = res[1];
+  if (e_stderr) *e_stderr = res[3];
+  if (st) *st = S;
+  if (!std::isfinite(res[1]) || !std::isfinite(res[3])) return RSSRI_ERR_NONFINITE;
+  return RSSRI_OK;
+#undef RS_CK
+}
+
+}  // namespace
+
+extern "C" {
+
+int rssri_sigma(rssri_handle *h, const rssri_options *o, double *sigma, double *e_pair,
+                double *e_corr, double *e_stderr, rssri_stats *st) {
+  return run_sigma(h, o, nullptr, nullptr, sigma, e_pair, e_corr, e_stderr, st);
+}
+
+int rssri_sigma_from_g(rssri_handle *h, const rssri_options *o, const double *g, const double *gb,
+                       double *sigma, double *e_pair, double *e_corr, double *e_stderr,
+                       rssri_stats *st) {
+  if (!g || !gb) return RSSRI_ERR_INVALID_ARG;
+  return run_sigma(h, o, g, gb, sigma, e_pair, e_corr, e_stderr, st);
+}
+
+int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
+  if (!h || !bytes) return RSSRI_ERR_INVALID_ARG;
+  *bytes = 0;
+  if (!h->ready) return RSSRI_ERR_NOT_READY;
+  const size_t d = sizeof(double);
+  const size_t nn = (size_t)h->n * h->n, na = h->n_aux, nt = h->n_tau, ns = h->last_ns;
+  switch (which) {
+    case RSSRI_BUF_W: *bytes = na * na * d; break;
+    case RSSRI_BUF_COLMAX: *bytes = h->n * d; break;
+    case RSSRI_BUF_ERI_L: *bytes = nn * na * d; break;
+    case RSSRI_BUF_K_L: *bytes = nn * na * d; break;
+    case RSSRI_BUF_THETA: *bytes = h->have_sigma ? 2 * ns * na * d : 0; break;
+    case RSSRI_BUF_R:
+    case RSSRI_BUF_R_L: *bytes = h->have_sigma ? 2 * ns * nn * d : 0; break;
+    case RSSRI_BUF_G:
+    case RSSRI_BUF_GB:
+    case RSSRI_BUF_SIGMA_DD:
+    case RSSRI_BUF_SIGMA_RAW: *bytes = h->have_sigma ? nt * nn * d : 0; break;
+    default: return RSSRI_ERR_INVALID_ARG;
+  }
+  return *bytes ? RSSRI_OK : RSSRI_ERR_NOT_READY;
+}
+
+int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_kind) {
+  size_t need = 0;
+  int rc = rssri_buffer_bytes(h, which, &need);
+  if (rc) return rc;
+  if (!dst || bytes != need || (dst_kind != RSSRI_PTR_DEVICE && dst_kind != RSSRI_PTR_HOST))
+    return RSSRI_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  cudaStream_t s = h->stream;
+  const cudaMemcpyKind k = dst_kind == RSSRI_PTR_HOST ? cudaMemcpyDeviceToHost
+                                                      : cudaMemcpyDeviceToDevice;
+  const size_t nn = (size_t)h->n * h->n, na = h->n_aux, ns = h->last_ns;
+  cudaError_t e = cudaSuccess;
+  auto copy = [&](void *d, const void *src, size_t b) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, src, b, k, s);
+  };
+  char *out = static_cast<char *>(dst);
+  switch (which) {
+    case RSSRI_BUF_W: copy(dst, h->W.p, bytes); break;
+    case RSSRI_BUF_COLMAX: copy(dst, h->colmax.p, bytes); break;
+    case RSSRI_BUF_ERI_L:
+    case RSSRI_BUF_K_L: {
+      // dense [n][n][n_aux], zero outside the listed pairs
+      const bool eri = which == RSSRI_BUF_ERI_L;
+      const int P = eri ? h->P_s : h->P;
+      const int *idx = eri ? h->spairs.as<int>() : h->pij.as<int>();
+      const double *rows = eri ? h->EL.as<double>() : h->KP.as<double>();
+      e = ensure(h->outbuf, bytes);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->outbuf.p, 0, bytes, s);
+      if (e == cudaSuccess && P > 0) {
+        // scatter rows: treat each row of n_aux doubles as one element of width na
+        std::vector<int> hidx(P);
+        e = cudaMemcpyAsync(hidx.data(), idx, P * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int p = 0; p < P && e == cudaSuccess; ++p)
+          e = cudaMemcpyAsync(h->outbuf.as<double>() + (size_t)hidx[p] * na, rows + (size_t)p * na,
+                              na * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      }
+      copy(dst, h->outbuf.p, bytes);
+      break;
+    }
+    case RSSRI_BUF_THETA: copy(dst, h->theta.p, bytes); break;
+    case RSSRI_BUF_R:
+    case RSSRI_BUF_R_L: {
+      const int kind = which == RSSRI_BUF_R ? 0 : 1;
+      for (int set = 0; set < 2; ++set)
+        copy(out + set * ns * nn * sizeof(double),
+             h->fac.as<double>() + (2 * set + kind) * ns * nn, ns * nn * sizeof(double));
+      break;
+    }
+    case RSSRI_BUF_G: copy(dst, h->G.p, bytes); break;
+    case RSSRI_BUF_GB: copy(dst, h->Gb.p, bytes); break;
+    case RSSRI_BUF_SIGMA_DD: copy(dst, h->sdd.p, bytes); break;
+    case RSSRI_BUF_SIGMA_RAW: copy(dst, h->sig_raw.p, bytes); break;
+    default: return RSSRI_ERR_INVALID_ARG;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return map_err(e);
+}
+
+}  // extern "C"
