@@ -1,0 +1,396 @@
+"""Benchmark of the RS-SRI-GF2 self-energy path on GB300.
+
+Workload: N = 200 basis functions, 100 occupied, N_aux = 600, 64 tau points,
+N_s = 300 sample pairs, eps = 1e-3, eps' = 0.02 (synthetic hydrogen-chain-like
+integrals).  One step is one pass of the whole path: V^{-1/2}, screening,
+[K]^L and its cut, the pair-space product, G(tau), the deterministic block,
+the Rademacher draws, R and R^L, the chain products for every (sample pair,
+tau) unit, the energy and the symmetrised output.  The metric is Sigma(tau)
+units per second, a unit being one (sample pair, tau point); inputs are
+resident in HBM when the timed region starts.  Every step draws a new seed.
+
+Multi-GPU: one process per GPU (torchrun); every rank runs independent
+replicas with its own seeds, no collective on the data path (weak scaling).
+
+--impl reference times the fp64 CPU oracle on the host cores on a bounded
+sample of the same workload, extrapolated to the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_12338_gb300 import synth  # noqa: E402
+
+WORKLOAD = "c2_n200"
+# fp64 ALU peak of the DFMA pipe: 152 SMs x 2 fp64 FMA/clock/SM x 2 flop x
+# 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# --------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": reasons,
+                "power_w_median": float(np.median(pw)) if pw else None, "samples": len(rows)}
+
+
+# ---------------------------------------------------------- the oracle -----
+def oracle_sample(s, cfg, seed, budget_s=12.0):
+    """Time the fp64 oracle on a bounded sample of one step and extrapolate.
+
+    The sample: the whole setup (V^{-1/2}, screen, [K]^L); R and R^L for two
+    sample pairs; the chain products of those pairs at two tau points; the
+    deterministic block at one tau point restricted to a few first-index
+    auxiliary functions; G at one tau point.  Each part is scaled by how many
+    times a full step repeats it."""
+    import oracle as O
+    n_s, nt = cfg["n_s"], s.n_tau
+    t0 = time.perf_counter()
+    w = O.metric_inv_sqrt(s.metric)
+    el, _, _ = O.screen(s.eri3, cfg["eps_prime"])
+    kl, _ = O.large_factor(el, w, cfg["eps"])
+    t_setup = time.perf_counter() - t0
+    n_pair = 2
+    t0 = time.perf_counter()
+    th0 = O.rademacher(seed, 0, n_pair, s.n_aux)
+    th1 = O.rademacher(seed, 1, n_pair, s.n_aux)
+    r0, rl0 = O.stochastic_factors(s.eri3, w, kl, th0)
+    r1, rl1 = O.stochastic_factors(s.eri3, w, kl, th1)
+    t_r = (time.perf_counter() - t0) / n_pair
+    taus = [0, nt - 1]
+    t_g = t_chain = 0.0
+    units = 0
+    for it in taus:
+        t0 = time.perf_counter()
+        g, gb = O.green(s.orb_e, s.orb_c, s.n_occ, s.mu, s.tau[it])
+        t_g += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for x in range(n_pair):
+            O.factor_pair(r0[x], r1[x], g, gb)
+            O.factor_pair(rl0[x], rl1[x], g, gb)
+            units += 1
+        t_chain += time.perf_counter() - t0
+    t_g /= len(taus)
+    t_unit = t_chain / units
+    nq = int((np.abs(kl).reshape(-1, s.n_aux).max(axis=0) > 0).sum())
+    n_outer = 1
+    t0 = time.perf_counter()
+    g, gb = O.green(s.orb_e, s.orb_c, s.n_occ, s.mu, s.tau[nt // 2])
+    while True:
+        O.sigma_from_factor(kl, g, gb, outer=range(n_outer))
+        el_t = time.perf_counter() - t0
+        if el_t > budget_s / 3 or n_outer >= nq:
+            break
+        n_outer *= 2
+        t0 = time.perf_counter()
+    t_dd_tau = el_t / n_outer * nq
+    t_step = t_setup + t_r * n_s + t_g * nt + t_unit * n_s * nt + t_dd_tau * nt
+    units_step = n_s * nt
+    try:
+        import threadpoolctl
+        threads = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info())
+    except Exception:
+        threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"oracle timed on: full setup; R/R^L for {n_pair} sample pairs; chain products "
+              f"for {units} (pair, tau) units; G at {len(taus)} tau; deterministic block at 1 tau "
+              f"over {n_outer} of {nq} first-index aux functions; extrapolated to one step "
+              f"({n_s} pairs x {nt} tau)")
+    return dict(value=units_step / t_step, unit="units/s", cores=threads, kind="oracle",
+                sample=sample, t_step_extrapolated_s=t_step,
+                parts_s=dict(setup=t_setup, r_per_pair=t_r, green_per_tau=t_g,
+                             chain_per_unit=t_unit, dd_per_tau=t_dd_tau))
+
+
+def time_to_target(results, ns, target):
+    """Device time to reach a target E_corr standard error: the fixed part
+    (setup, G, deterministic block) once, then sample pairs at the measured
+    cost per pair until sd(e_pair)/sqrt(n) <= target (at least 2 pairs)."""
+    fixed = float(np.mean([r[2] for r in results])) / 1e3
+    per_pair = float(np.mean([r[3] for r in results])) / 1e3 / ns
+    sigma_pair = float(np.mean([r[1] for r in results])) * np.sqrt(ns)
+    pairs = max(2.0, (sigma_pair / target) ** 2)
+    return {"seconds": fixed + per_pair * pairs, "fixed_s": fixed, "per_pair_s": per_pair,
+            "pairs_needed": pairs, "sd_per_pair": sigma_pair, "target": target}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = synth.CONFIGS[args.workload]
+    s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
+    for k in range(args.warmup):
+        oracle_sample(s, cfg, 10_000 + k, budget_s=6.0)
+    vals, times = [], []
+    for k in range(args.steps):
+        r = oracle_sample(s, cfg, k, budget_s=6.0)
+        vals.append(r["value"])
+        times.append(r["t_step_extrapolated_s"])
+    value = float(np.mean(vals))
+    line = {"metric": "Sigma(tau) units/s (unit = one sample pair x one tau point)",
+            "value": value, "unit": "units/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(times)) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: N={cfg['n']} n_occ={cfg['n_occ']} "
+                                   f"N_aux={cfg['n_aux']} N_tau={cfg['n_tau']} N_s={cfg['n_s']} "
+                                   f"eps={cfg['eps']} eps'={cfg['eps_prime']}"},
+            "cpu_baseline": {"value": value, "unit": "units/s", "cores": r["cores"],
+                             "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": value, "unit": "units/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- our arm -----
+def traffic_for(kernel_class):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel_class)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2005_12338_gb300", "csrc", d["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if sha == d.get("source_sha") else None
+
+
+def our_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_12338_gb300 import binding, build
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    cfg = synth.CONFIGS[args.workload]
+    s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
+    n, nt, ns = s.n, s.n_tau, cfg["n_s"]
+    host = [s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w]
+    dev = [torch.from_numpy(a).to(f"cuda:{local}") for a in host]
+    sig = torch.empty((nt, n, n), dtype=torch.float64, device=f"cuda:{local}")
+    ep = torch.empty(ns, dtype=torch.float64, device=f"cuda:{local}")
+    h = binding.Handle(local)
+    stream = torch.cuda.current_stream(local)
+
+    def step(seed, profile=0):
+        o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, profile=profile)
+        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
+        return h.sigma(o, sig, ep)
+
+    for k in range(args.warmup):
+        step(rank * 1_000_000 + 900_000 + k)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof_ms = np.zeros(8)
+    prof_gf = np.zeros(8)
+    prof_l = np.zeros(8, dtype=np.int64)
+    launches = 0
+    results = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            e, se, st = step(rank * 1_000_000 + k, profile=1)
+            results.append((e, se, st["t_setup_ms"] + st["t_green_dd_ms"], st["t_sample_ms"]))
+            prof_ms += st["prof_ms"]
+            prof_gf += st["prof_gflop"]
+            prof_l += np.array(st["prof_launches"], dtype=np.int64)
+            launches += st["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    clocks = clk.summary()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = ns * nt * args.steps * world
+    value = units / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(a).pin_memory().numpy() for a in host]
+        sig_h = torch.empty((nt, n, n), dtype=torch.float64).pin_memory().numpy()
+        ep_h = torch.empty(ns, dtype=torch.float64).pin_memory().numpy()
+        hh = binding.Handle(local)
+
+        def step_host(seed):
+            o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed)
+            hh.setup(*pinned, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
+            return hh.sigma(o, sig_h, ep_h)
+        step_host(rank * 1_000_000 + 990_000)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step_host(rank * 1_000_000 + k)
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device=f"cuda:{local}")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": units / float(te.item()), "unit": "units/s",
+               "h2d_bytes_per_step": int(sum(a.nbytes for a in host)),
+               "d2h_bytes_per_step": int(sig_h.nbytes + ep_h.nbytes + 4 * 8)}
+        hh.close()
+
+    if rank != 0:
+        h.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    dom = int(np.argmax(prof_ms))
+    name = binding.PROF_CLASSES[dom]
+    per_launch_gf = prof_gf[dom] / max(prof_l[dom], 1)
+    achieved = prof_gf[dom] / (prof_ms[dom] / 1e3) / 1e3  # TFLOP/s
+    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for(name),
+                "peak_source": "derived: 152 SMs x 2 fp64 FMA/clk/SM x 2 flop x 2070 MHz "
+                               "(fp64 DFMA pipe; HBM/bf16 peaks " + peak_src + ")",
+                "gflop_per_launch": per_launch_gf, "launches": int(prof_l[dom]),
+                "share_of_step": float(prof_ms[dom] / max(prof_ms.sum(), 1e-9))}
+    classes = {binding.PROF_CLASSES[c]: {"ms_per_step": prof_ms[c] / args.steps,
+                                         "gflop_per_step": prof_gf[c] / args.steps,
+                                         "launches_per_step": int(prof_l[c]) // args.steps,
+                                         "tflops": (prof_gf[c] / (prof_ms[c] / 1e3) / 1e3
+                                                    if prof_ms[c] > 0 else None)}
+               for c in range(len(binding.PROF_CLASSES))}
+    line = {"metric": "Sigma(tau) units/s (unit = one sample pair x one tau point)",
+            "value": value, "unit": "units/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: N={n} n_occ={s.n_occ} N_aux={s.n_aux} "
+                                   f"N_tau={nt} N_s={ns} eps={cfg['eps']} "
+                                   f"eps'={cfg['eps_prime']}, whole path per step",
+                       "l2": "inputs larger than L2 (3-index integrals 192 MB); steps of seconds",
+                       "parallelism": f"replicas x{world} (independent seeds, no collective)"},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+            "e2e": e2e,
+            "extra": {"e_corr_per_step": [r[0] for r in results],
+                      "e_stderr_per_step": [r[1] for r in results],
+                      "time_to_1mEh_s": time_to_target(results, ns, 1e-3),
+                      "classes": classes}}
+    if not args.no_cpu_baseline and world == 1:
+        cb = oracle_sample(s, cfg, 0)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

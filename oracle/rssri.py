@@ -154,16 +154,18 @@ def factor_pair(x: np.ndarray, y: np.ndarray, g: np.ndarray, gb: np.ndarray):
     return 2.0 * t * c - b @ c, t, s
 
 
-def sigma_from_factor(k: np.ndarray, g: np.ndarray, gb: np.ndarray) -> np.ndarray:
+def sigma_from_factor(k: np.ndarray, g: np.ndarray, gb: np.ndarray, outer=None) -> np.ndarray:
     """Eq. 20 with v = sum_Q K^Q K^Q (Eq. 8): since Eq. 20 is bilinear in its
     two integrals, Sigma = sum_{Q, Q'} F(K^Q, K^Q').  Used for the RI
     self-energy and, with K = [K]^L, for the deterministic block of Eq. 25.
+    outer: optionally restrict the first auxiliary index Q to these positions
+    among the non-zero K^Q (partial sums, for timing samples).
     """
     kq = np.ascontiguousarray(np.moveaxis(k, 2, 0))  # [N_aux, N, N]
     keep = np.flatnonzero(np.abs(kq).reshape(kq.shape[0], -1).max(axis=1) > 0)
     kq = kq[keep]
     out = np.zeros_like(g)
-    for q in range(kq.shape[0]):
+    for q in (range(kq.shape[0]) if outer is None else outer):
         c = (kq[q] @ g) @ kq  # [N_aux', N, N]: C = K^Q G K^Q' for all Q'
         b = c @ gb
         t = np.trace(b, axis1=1, axis2=2)

@@ -75,9 +75,75 @@ struct rssri_handle {
   long long last_ns = 0;
   bool have_sigma = false;
   rssri_stats stats{};
+
+  // per-class launch counts and (when profiling) event timings
+  struct Rec {
+    int cls;
+    double gflop;
+    long long launches;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t ev_used = 0;
+  std::vector<Rec> recs;
+  long long setup_launches[RSSRI_PROF_NCLASS] = {};
+  double setup_ms[RSSRI_PROF_NCLASS] = {}, setup_gflop[RSSRI_PROF_NCLASS] = {};
 };
 
 namespace {
+
+// ------------------------------------------------------------ profiling ----
+cudaEvent_t take_event(rssri_handle *h) {
+  if (h->ev_used == h->evpool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->evpool.push_back(e);
+  }
+  return h->evpool[h->ev_used++];
+}
+
+// One group of launches of one kernel class; records its launch count and,
+// when profiling, CUDA events around it on the handle's stream.
+struct Span {
+  rssri_handle *h;
+  int cls;
+  double gflop;
+  long long l0;
+  cudaEvent_t a = nullptr;
+  Span(rssri_handle *h_, int c, double gf) : h(h_), cls(c), gflop(gf), l0(launch_counter()) {
+    if (h->prof_on) {
+      a = take_event(h);
+      if (a && cudaEventRecord(a, h->stream) != cudaSuccess) a = nullptr;
+    }
+  }
+  ~Span() {
+    cudaEvent_t b = nullptr;
+    if (a) {
+      b = take_event(h);
+      if (b && cudaEventRecord(b, h->stream) != cudaSuccess) b = nullptr;
+    }
+    h->recs.push_back({cls, gflop, launch_counter() - l0, a, b});
+  }
+};
+#define SPAN(cls, gf) Span span_(h, (cls), (gf))
+
+// Sum the recorded spans (the stream must have completed them) and reset.
+void collect(rssri_handle *h, long long *launches, double *ms, double *gflop) {
+  for (int c = 0; c < RSSRI_PROF_NCLASS; ++c) {
+    launches[c] = 0;
+    ms[c] = 0;
+    gflop[c] = 0;
+  }
+  for (const auto &r : h->recs) {
+    launches[r.cls] += r.launches;
+    gflop[r.cls] += r.gflop;
+    float t = 0;
+    if (r.a && r.b && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.cls] += t;
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+}
 
 // ----------------------------------------------------------- validation ----
 bool finite(double x) { return std::isfinite(x); }
@@ -136,6 +202,12 @@ cudaError_t gemm(rssri_handle *h, const GemmArgs &g) {
   return dgemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
 }
 
+// A product counted under kernel class `cls` with its 2 M N K batch flops.
+cudaError_t gemm_p(rssri_handle *h, int cls, const GemmArgs &g) {
+  SPAN(cls, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
+  return gemm(h, g);
+}
+
 // ------------------------------------------------------------ S1: V^-1/2 --
 // Coupled Newton-Schulz iteration for the inverse square root: with
 // Y_0 = V / c, Z_0 = I and T_k = (3 I - Z_k Y_k) / 2, Y_{k+1} = Y_k T_k and
@@ -163,7 +235,7 @@ int metric_inv_sqrt(rssri_handle *h, int *rc) {
   double *Y = h->nsY.as<double>(), *Z = h->nsZ.as<double>(), *Y2 = h->nsY2.as<double>(),
          *Z2 = h->nsZ2.as<double>(), *Pm = h->nsP.as<double>(), *Tm = h->nsT.as<double>();
   double *scal = h->scal.as<double>(), *part = h->part.as<double>();
-  RS_CK(ns_init(h->metric, na, Y, Z, scal, part, s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(ns_init(h->metric, na, Y, Z, scal, part, s)); }
   GemmArgs g;
   g.M = g.N = g.K = na;
   g.lda = g.ldb = g.ldc = na;
@@ -173,16 +245,16 @@ int metric_inv_sqrt(rssri_handle *h, int *rc) {
   int it = 0;
   for (; it < max_it; ++it) {
     g.A = Z; g.B = Y; g.C = Pm;
-    RS_CK(gemm(h, g));
-    RS_CK(ns_tbuild(Pm, na, Tm, scal, part, s));
+    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(ns_tbuild(Pm, na, Tm, scal, part, s)); }
     RS_CK(fetch(&resid, scal + 1, s));
     if (!std::isfinite(resid) || resid > 1e6) break;
     if (final_step) break;
     if (resid < 1e-8) final_step = true;
     g.A = Y; g.B = Tm; g.C = Y2;
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
     g.A = Tm; g.B = Z; g.C = Z2;
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
     std::swap(Y, Y2);
     std::swap(Z, Z2);
   }
@@ -192,7 +264,7 @@ int metric_inv_sqrt(rssri_handle *h, int *rc) {
     *rc = RSSRI_ERR_NOT_SPD;
     return RSSRI_OK;
   }
-  RS_CK(ns_finish(Z, na, scal, h->W.as<double>(), s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(ns_finish(Z, na, scal, h->W.as<double>(), s)); }
   *rc = RSSRI_OK;
   return RSSRI_OK;
 #undef RS_CK
@@ -262,6 +334,7 @@ void rssri_destroy(rssri_handle *h) {
   for (DevBuf *b : bufs) release(*b);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (auto e : h->evpool) cudaEventDestroy(e);
   delete h;
 }
 
@@ -303,6 +376,9 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
     if (!(htau[k] > 0.0 && htau[k] < p->beta) || !std::isfinite(htw[k]))
       return RSSRI_ERR_INVALID_ARG;
 
+  h->recs.clear();
+  h->ev_used = 0;
+  h->prof_on = o->profile != 0;
   RS_CK(cudaEventRecord(h->ev[0], s));
   h->n = n; h->n_occ = p->n_occ; h->n_aux = na; h->n_tau = nt;
   h->mu = p->mu; h->beta = p->beta; h->ptr_kind = p->ptr_kind;
@@ -318,10 +394,10 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   // input checks: symmetry of (ij|A), finiteness of everything
   int *flags = h->flags.as<int>();
   RS_CK(cudaMemsetAsync(flags, 0, 16 * sizeof(int), s));
-  RS_CK(eri_check(h->eri3, n, na, flags, s));
-  RS_CK(nonfinite_check(h->metric, (long long)na * na, flags + 1, s));
-  RS_CK(nonfinite_check(h->orb_e, n, flags + 1, s));
-  RS_CK(nonfinite_check(h->orb_c, nn, flags + 1, s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(eri_check(h->eri3, n, na, flags, s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(nonfinite_check(h->metric, (long long)na * na, flags + 1, s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(nonfinite_check(h->orb_e, n, flags + 1, s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(nonfinite_check(h->orb_c, nn, flags + 1, s)); }
   int hflags[2];
   RS_CK(fetch(hflags, flags, s, 2));
   if (hflags[1]) return RSSRI_ERR_NONFINITE;
@@ -344,10 +420,10 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   RS_CK(ensure(h->cnum, 4 * sizeof(int)));
   RS_CK(ensure(h->csum, 4 * sizeof(long long)));
   RS_CK(ensure(h->spairs, nn * sizeof(int)));
-  RS_CK(eri_colmax(h->eri3, n, na, h->colmax.as<double>(), s));
-  RS_CK(eri_pair_count(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime, h->cnt.as<int>(), s));
-  RS_CK(compact(h->cnt.as<int>(), (int)nn, h->spairs.as<int>(), h->cnum.as<int>(),
-                h->csum.as<long long>(), h->cscratch.p, s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(eri_colmax(h->eri3, n, na, h->colmax.as<double>(), s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(eri_pair_count(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime, h->cnt.as<int>(), s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(compact(h->cnt.as<int>(), (int)nn, h->spairs.as<int>(), h->cnum.as<int>(),
+                h->csum.as<long long>(), h->cscratch.p, s)); }
   int P_s = 0;
   long long nnz = 0;
   RS_CK(fetch(&P_s, h->cnum.p, s));
@@ -364,19 +440,19 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   long long nnzk = 0;
   double kmax = 0;
   if (P_s > 0) {
-    RS_CK(eri_gather_rows(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime,
-                          h->spairs.as<int>(), P_s, h->EL.as<double>(), s));
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(eri_gather_rows(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime,
+                          h->spairs.as<int>(), P_s, h->EL.as<double>(), s)); }
     GemmArgs g;
     g.M = P_s; g.N = na; g.K = na;
     g.A = h->EL.as<double>(); g.lda = na;
     g.B = h->W.as<double>(); g.ldb = na;
     g.C = h->KLs.as<double>(); g.ldc = na;
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
     double *scal = h->scal.as<double>();
-    RS_CK(absmax(h->KLs.as<double>(), (long long)P_s * na, scal + 2, h->part.as<double>(), s));
-    RS_CK(kl_cut(h->KLs.as<double>(), P_s, na, scal + 2, o->eps, h->cnt2.as<int>(), s));
-    RS_CK(compact(h->cnt2.as<int>(), P_s, h->lidx.as<int>(), h->cnum.as<int>(),
-                  h->csum.as<long long>(), h->cscratch.p, s));
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(absmax(h->KLs.as<double>(), (long long)P_s * na, scal + 2, h->part.as<double>(), s)); }
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(kl_cut(h->KLs.as<double>(), P_s, na, scal + 2, o->eps, h->cnt2.as<int>(), s)); }
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(compact(h->cnt2.as<int>(), P_s, h->lidx.as<int>(), h->cnum.as<int>(),
+                  h->csum.as<long long>(), h->cscratch.p, s)); }
     RS_CK(fetch(&P, h->cnum.p, s));
     RS_CK(fetch(&nnzk, h->csum.p, s));
     RS_CK(fetch(&kmax, scal + 2, s));
@@ -391,23 +467,24 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   RS_CK(ensure(h->KP, (size_t)std::max(P, 1) * na * sizeof(double)));
   RS_CK(ensure(h->D, (size_t)std::max(P, 1) * std::max(P, 1) * sizeof(double)));
   if (P > 0) {
-    RS_CK(gather_int(h->spairs.as<int>(), h->lidx.as<int>(), P, h->pij.as<int>(), s));
-    RS_CK(gather_rows(h->KLs.as<double>(), h->lidx.as<int>(), P, na, h->KP.as<double>(), s));
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_int(h->spairs.as<int>(), h->lidx.as<int>(), P, h->pij.as<int>(), s)); }
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_rows(h->KLs.as<double>(), h->lidx.as<int>(), P, na, h->KP.as<double>(), s)); }
     // D[a][b] = sum_Q K_P[a][Q] K_P[b][Q] = v^L for the pair of pairs (Eq. 8 on [K]^L)
     GemmArgs g;
     g.M = P; g.N = P; g.K = na;
     g.A = h->KP.as<double>(); g.lda = na;
     g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1;
     g.C = h->D.as<double>(); g.ldc = P;
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
   }
-  RS_CK(pair_csr(h->pij.as<int>(), P, n, h->rowptr.as<int>(), h->prow.as<int>(),
-                 h->pcol.as<int>(), s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_csr(h->pij.as<int>(), P, n, h->rowptr.as<int>(), h->prow.as<int>(),
+                 h->pcol.as<int>(), s)); }
   RS_CK(cudaEventRecord(h->ev[1], s));
   RS_CK(cudaEventSynchronize(h->ev[1]));
   float ms = 0;
   cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
   h->t_setup_ms = ms;
+  collect(h, h->setup_launches, h->setup_ms, h->setup_gflop);
   h->ready = true;
   return RSSRI_OK;
 #undef RS_CK
@@ -426,15 +503,15 @@ cudaError_t build_green(rssri_handle *h) {
   for (int occ = 0; occ < 2; ++occ) {
     const int off = occ ? 0 : no, m = occ ? no : nv;
     double *out = occ ? h->Gb.as<double>() : h->G.as<double>();
-    RS_TRY(green_scale(h->orb_c, h->orb_e, n, off, m, h->mu, h->tau, nt, occ ? 1 : -1,
-                       h->cs.as<double>(), s));
+    { SPAN(RSSRI_PROF_GREEN, 0.0); RS_TRY(green_scale(h->orb_c, h->orb_e, n, off, m, h->mu, h->tau, nt, occ ? 1 : -1,
+                       h->cs.as<double>(), s)); }
     GemmArgs g;
     g.M = n; g.N = n; g.K = m; g.batch = nt;
     g.A = h->cs.as<double>(); g.lda = m; g.sA = (long long)n * m;
     g.B = h->orb_c + off; g.ldb = n; g.transB = 1; g.sB = 0;
     g.C = out; g.ldc = n; g.sC = nn;
     g.alpha = -1.0;
-    RS_TRY(gemm(h, g));
+    RS_TRY(gemm_p(h, RSSRI_PROF_GREEN, g));
   }
   return cudaSuccess;
 }
@@ -450,8 +527,8 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
   if (P == 0) return cudaMemsetAsync(out, 0, nn * sizeof(double), s);
   double *PG = h->PG.as<double>(), *At = h->At.as<double>(), *T = h->T.as<double>();
   // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]
-  RS_TRY(dgemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), G, n,
-                         h->KP.as<double>(), na, PG, na, (long long)n * na, s));
+  { SPAN(RSSRI_PROF_DD_GEMM, 2.0 * n * (double)na * P * 1e-9); RS_TRY(dgemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), G, n,
+                         h->KP.as<double>(), na, PG, na, (long long)n * na, s)); }
   // At[k][(l,Q)] = sum_m Gb[k][m] PG[m][(l,Q)]
   {
     GemmArgs g;
@@ -459,20 +536,20 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = Gb; g.lda = n;
     g.B = PG; g.ldb = (long long)n * na;
     g.C = At; g.ldc = (long long)n * na;
-    RS_TRY(gemm(h, g));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // T[m][Q][j] = sum_{a in row m, b in row j} D[a][b] At[(col a, col b)][Q]
-  RS_TRY(dd_exchange_spmm(h->rowptr.as<int>(), h->pcol.as<int>(), h->D.as<double>(), P, At, n, na,
-                          T, s));
+  { SPAN(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9); RS_TRY(dd_exchange_spmm(h->rowptr.as<int>(), h->pcol.as<int>(), h->D.as<double>(), P, At, n, na,
+                          T, s)); }
   // Gamma = K_P^T At_P, At_P the rows of At at the kept pairs
-  RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
   {
     GemmArgs g;
     g.M = na; g.N = na; g.K = P;
     g.A = h->KP.as<double>(); g.lda = na; g.transA = 1;
     g.B = h->AP.as<double>(); g.ldb = na;
     g.C = h->Gam.as<double>(); g.ldc = na;
-    RS_TRY(gemm(h, g));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
   {
@@ -481,9 +558,9 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = h->KP.as<double>(); g.lda = na;
     g.B = h->Gam.as<double>(); g.ldb = na; g.transB = 1;
     g.C = h->L.as<double>(); g.ldc = na;
-    RS_TRY(gemm(h, g));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
-  RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s)); }
   // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n]
   {
     GemmArgs g;
@@ -492,7 +569,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.B = T; g.ldb = n;
     g.C = out; g.ldc = n;
     g.alpha = -1.0;
-    RS_TRY(gemm(h, g));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   return cudaSuccess;
 }
@@ -537,6 +614,9 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     }                                                  \
   } while (0)
 
+  h->recs.clear();
+  h->ev_used = 0;
+  h->prof_on = o->profile != 0;
   RS_CK(cudaEventRecord(h->ev[2], s));
   // ---- buffers
   RS_CK(ensure(h->G, (size_t)nt * nn * sizeof(double)));
@@ -590,14 +670,14 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   // ---- S4: theta, theta' and U^T = theta W (W symmetric)
   double *theta = h->theta.as<double>(), *Ut = h->Ut.as<double>(), *fac = h->fac.as<double>();
   for (int set = 0; set < 2; ++set)
-    RS_CK(rademacher(o->seed, set, o->xi_offset, ns, na, theta + (long long)set * ns * na, s));
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(rademacher(o->seed, set, o->xi_offset, ns, na, theta + (long long)set * ns * na, s)); }
   {
     GemmArgs g;
     g.M = ns; g.N = na; g.K = na; g.batch = 2;
     g.A = theta; g.lda = na; g.sA = (long long)ns * na;
     g.B = h->W.as<double>(); g.ldb = na; g.sB = 0;
     g.C = Ut; g.ldc = na; g.sC = (long long)ns * na;
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
   }
   // ---- S5: R[set][xi][ij] = sum_A U^T[xi][A] (ij|A); R^L from the kept pairs
   {
@@ -606,7 +686,7 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     g.A = Ut; g.lda = na; g.sA = (long long)ns * na;
     g.B = h->eri3; g.ldb = na; g.transB = 1; g.sB = 0;
     g.C = fac; g.ldc = nn; g.sC = 2LL * ns * nn;  // kind 0 of each set
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
   }
   for (int set = 0; set < 2; ++set) {
     double *rl = fac + (2LL * set + 1) * ns * nn;
@@ -618,10 +698,10 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     g.A = theta; g.lda = na; g.sA = (long long)ns * na;
     g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1; g.sB = 0;
     g.C = h->RLp.as<double>(); g.ldc = P; g.sC = (long long)ns * P;
-    RS_CK(gemm(h, g));
+    RS_CK(gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
     for (int set = 0; set < 2; ++set)
-      RS_CK(scatter_pairs(h->RLp.as<double>() + (long long)set * ns * P, ns, P, h->pij.as<int>(),
-                          nn, nn, fac + (2LL * set + 1) * ns * nn, s));
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(scatter_pairs(h->RLp.as<double>() + (long long)set * ns * P, ns, P, h->pij.as<int>(),
+                          nn, nn, fac + (2LL * set + 1) * ns * nn, s)); }
   }
 
   // ---- S8: chains per tau and batch of sample pairs
@@ -644,34 +724,34 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
         g.M = n; g.N = n; g.K = n; g.batch = cnt;
         g.lda = g.ldb = g.ldc = n;
         g.A = X; g.sA = nn; g.B = Gt; g.sB = 0; g.C = xg; g.sC = nn;   // X G
-        RS_CK(gemm(h, g));
+        RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
         g.A = xg; g.sA = nn; g.B = Y; g.sB = nn; g.C = c; g.sC = nn;   // C = X G Y
-        RS_CK(gemm(h, g));
+        RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
         g.A = c; g.sA = nn; g.B = Gbt; g.sB = 0; g.C = bm; g.sC = nn;  // B = C Gb
-        RS_CK(gemm(h, g));
+        RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
       }
       const int tot = cnt * (1 + has_l);
       // t = Tr B, s2 = Tr B B, B <- +-(2 t I - B)
-      RS_CK(chain_fold(Bm, tot, cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s));
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(chain_fold(Bm, tot, cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s)); }
       {
         GemmArgs g;
         g.M = n; g.N = n; g.K = n; g.batch = tot;
         g.lda = g.ldb = g.ldc = n;
         g.A = Bm; g.sA = nn; g.B = Cc; g.sB = nn; g.C = BC; g.sC = nn;  // (2tI - B) C
-        RS_CK(gemm(h, g));
+        RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
       }
-      RS_CK(sigma_accumulate(BC, cnt, has_l, n, (double)ns, h->sdd.as<double>() + t * nn,
-                             x0 == 0, sig, s));
-      RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, has_l, h->h_tau_w[t], ne,
-                        h->e_st.as<double>() + x0, s));
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, has_l, n, (double)ns, h->sdd.as<double>() + t * nn,
+                             x0 == 0, sig, s)); }
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, has_l, h->h_tau_w[t], ne,
+                        h->e_st.as<double>() + x0, s)); }
     }
   }
   // ---- S10 and S9
-  RS_CK(symmetrize(h->sig_raw.as<double>(), n, nt, h->sig_out.as<double>(), s));
-  RS_CK(trace_prod(h->sdd.as<double>(), Gb, n, nt, h->trdd.as<double>(), s));
-  RS_CK(trace_prod(h->sig_out.as<double>(), Gb, n, nt, h->tr.as<double>(), s));
-  RS_CK(energy_finalize(h->tau_w, h->trdd.as<double>(), h->tr.as<double>(), nt, ne,
-                        h->e_st.as<double>(), ns, h->e_pair.as<double>(), h->res.as<double>(), s));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(symmetrize(h->sig_raw.as<double>(), n, nt, h->sig_out.as<double>(), s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(trace_prod(h->sdd.as<double>(), Gb, n, nt, h->trdd.as<double>(), s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(trace_prod(h->sig_out.as<double>(), Gb, n, nt, h->tr.as<double>(), s)); }
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(energy_finalize(h->tau_w, h->trdd.as<double>(), h->tr.as<double>(), nt, ne,
+                        h->e_st.as<double>(), ns, h->e_pair.as<double>(), h->res.as<double>(), s)); }
   const cudaMemcpyKind dk = h->ptr_kind == RSSRI_PTR_HOST ? cudaMemcpyDeviceToHost
                                                           : cudaMemcpyDeviceToDevice;
   RS_CK(cudaMemcpyAsync(sigma, h->sig_out.p, nt * nn * sizeof(double), dk, s));
@@ -699,6 +779,16 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   S.t_setup_ms = h->t_setup_ms;
   S.t_green_dd_ms = t_dd;
   S.t_sample_ms = t_samp;
+  long long pl[RSSRI_PROF_NCLASS];
+  double pm[RSSRI_PROF_NCLASS], pg[RSSRI_PROF_NCLASS];
+  collect(h, pl, pm, pg);
+  S.kernel_launches = 0;
+  for (int c = 0; c < RSSRI_PROF_NCLASS; ++c) {
+    S.prof_launches[c] = pl[c] + h->setup_launches[c];
+    S.prof_ms[c] = pm[c] + h->setup_ms[c];
+    S.prof_gflop[c] = pg[c] + h->setup_gflop[c];
+    S.kernel_launches += S.prof_launches[c];
+  }
   if (e_corr) *e_corr = res[1];
   if (e_stderr) *e_stderr = res[3];
   if (st) *st = S;
