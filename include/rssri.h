@@ -259,6 +259,38 @@ RSSRI_API int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes);
  * equal rssri_buffer_bytes().  Synchronises the handle's stream. */
 RSSRI_API int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_kind);
 
+/* ---------------------------------------------------- allocation-free */
+
+/* Capacity, in tau points, of the fixed scratch of rssri_energy_static. */
+#define RSSRI_STATIC_MAX_TAU 4096
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory: code that runs while a stream is being
+ * captured into a CUDA graph (an allocation there invalidates the capture),
+ * hosts whose pool allocator owns all device memory and forbids libraries
+ * from allocating, and loops that must never wait on the allocator.
+ *
+ * It evaluates E_corr = -(1/N_e) sum_t tau_w[t] Tr[sigma[t] gb[t]] (Eq. 26,
+ * N_e = 2 n_occ, same sign and same summation order as rssri_sigma) for a
+ * self-energy the caller already holds, with no handle and no allocation.
+ *   sigma  device, [n_tau][n][n]  Sigma(tau)
+ *   gb     device, [n_tau][n][n]  G(beta - tau)
+ *   tau_w  device, [n_tau]        quadrature weights
+ *   e_corr device, [1]            output, written on `stream`
+ *   stream cudaStream_t as void* (NULL = legacy default stream)
+ * Its scratch is a static device array of RSSRI_STATIC_MAX_TAU doubles
+ * (32 KiB), present on every GPU that loads the library until the process
+ * exits.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU (different streams, or concurrent host threads) race on it and must
+ * be serialised by the caller.  Returns RSSRI_ERR_INVALID_ARG for null
+ * pointers, n outside [1, 4096], n_occ < 1 or n_tau outside
+ * [1, RSSRI_STATIC_MAX_TAU]; RSSRI_ERR_CUDA if a launch fails.  Does not
+ * synchronise. */
+RSSRI_API int rssri_energy_static(const double *sigma, const double *gb, const double *tau_w,
+                                  int n, int n_tau, int n_occ, double *e_corr, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

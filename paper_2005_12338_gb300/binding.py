@@ -78,7 +78,10 @@ SIGNATURES = {
                                      C.POINTER(rssri_stats)]),
     "rssri_buffer_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
     "rssri_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
+    "rssri_energy_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                      C.c_int, C.c_void_p, C.c_void_p]),
 }
+RSSRI_STATIC_MAX_TAU = 4096
 
 
 def lib() -> C.CDLL:
