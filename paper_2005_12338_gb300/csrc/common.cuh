@@ -46,6 +46,8 @@ int dgemm_ksplit(const GemmArgs &g);
 // Scratch doubles needed by dgemm() for `g`.
 size_t dgemm_work_elems(const GemmArgs &g);
 cudaError_t dgemm(const GemmArgs &g, double *work, size_t work_elems, cudaStream_t s);
+// Edge of the tile the autotuner chose for this shape (-1 before first use).
+int dgemm_tile_edge(const GemmArgs &g);
 
 // Segmented product used by the deterministic block (Sec. III):
 //   C[b][m][q] = sum_{a in [seg[b], seg[b+1])} A[col[a]*lda + m] * B[a*ldb + q]

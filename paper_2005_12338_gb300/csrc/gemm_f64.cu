@@ -2,30 +2,58 @@
 //
 // On GB300 the fp64 ceiling is the scalar DFMA pipe (two fp64 FMAs per clock
 // per SM, about 1.2 TFLOP/s for the GPU; the fp64 mma.sync path is slower),
-// so these are register-tiled SIMT kernels: a 64x64 output tile per 256
-// threads, 4x4 outputs per thread, 16-deep K slabs double-buffered through
-// shared memory with coalesced global loads for either operand layout.
+// so these are register-tiled SIMT kernels: an output tile per block (64, 40,
+// 48 or 100 wide, 4x4 or 5x5 outputs per thread), K slabs double-buffered
+// through shared memory with coalesced global loads for either operand
+// layout.  Since the DFMA pipe is the bound, the work that matters is the
+// zero-padded part of the edge tiles; the tile is chosen per problem shape.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
 namespace rssri {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
-constexpr int PAD = 2;  // keeps rows 16-byte aligned, spreads banks
+// Tile shape: BM x BN outputs per block, BK-deep K slabs, TM x TN outputs per
+// thread.  Every shape accumulates each output over k in ascending order with
+// one fma per k, so all shapes give bitwise-identical results; the launcher
+// picks the shape that is fastest for each problem shape (padded work on the
+// DFMA pipe is what differs: 200-wide operands waste 39% of 64-wide tiles).
+template <int BM_, int BN_, int BK_, int TM_, int TN_>
+struct Tile {
+  static constexpr int BM = BM_, BN = BN_, BK = BK_, TM = TM_, TN = TN_;
+  static constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
+};
+using T64 = Tile<64, 64, 16, 4, 4>;
+using T40 = Tile<40, 40, 8, 4, 4>;
+using T48 = Tile<48, 48, 16, 4, 4>;
+using T100 = Tile<100, 100, 8, 5, 5>;
+constexpr int kNumTiles = 4;
+constexpr int kTileEdge[kNumTiles] = {64, 40, 48, 100};
+constexpr int kTileDepth[kNumTiles] = {16, 8, 16, 8};
+// split-K planning always uses the 64-wide reference tile, so the chunking of
+// K (and therefore the result) does not depend on the tile shape chosen.
+constexpr int RBM = 64, RBN = 64, RBK = 16;
+constexpr int PAD = 1;
 
 // MODE 0: strided operands (transA/transB per TA/TB).
 // MODE 1: segmented: A(m,kk) = A[col[s0+kk]*lda + m], B(kk,q) = B[(s0+kk)*ldb + q],
 //         with s0 = seg[b] and K_b = seg[b+1] - seg[b].
-template <int MODE, int TA, int TB>
-__global__ void __launch_bounds__(NT) dgemm_kernel(
+template <class TL, int MODE, int TA, int TB>
+__global__ void __launch_bounds__(TL::NT) dgemm_kernel(
     int M, int N, int K, int kchunk, int ksplit, const double *__restrict__ A, long long lda,
     long long sA, const double *__restrict__ B, long long ldb, long long sB,
     double *__restrict__ C, long long ldc, long long sC, double alpha, double beta,
     int partial, const int *__restrict__ seg, const int *__restrict__ col) {
-  __shared__ __align__(16) double As[2][BK][BM + PAD];
-  __shared__ __align__(16) double Bs[2][BK][BN + PAD];
+  constexpr int BM = TL::BM, BN = TL::BN, BK = TL::BK, TM = TL::TM, TN = TL::TN, NT = TL::NT;
+  constexpr int LA = (BM * BK + NT - 1) / NT, LB = (BN * BK + NT - 1) / NT;
+  constexpr bool AK = (MODE == 0 && TA == 0);  // A tile loaded along k
+  constexpr bool BKc = (MODE == 0 && TB == 1); // B tile loaded along k
+  __shared__ double As[2][BK][BM + PAD];
+  __shared__ double Bs[2][BK][BN + PAD];
 
   const int z = blockIdx.z;
   const int b = z / ksplit, ks = z % ksplit;
@@ -45,62 +73,62 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(
   const long long ldcb = partial ? N : ldc;
 
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  const int tid = threadIdx.x, tx = tid % TL::TX, ty = tid / TL::TX;
+  double acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
-  double ra[4], rb[4];
+  double ra[LA], rb[LB];
   auto load = [&](int kt) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LA; ++r) {
       const int e = tid + r * NT;
-      int i, k;
-      if (MODE == 0 && TA == 0) { i = e >> 4; k = e & 15; }
-      else { k = e >> 6; i = e & 63; }
-      const int gi = row0 + i, gk = kt + k;
       double v = 0.0;
-      if (gi < M && gk < kend) {
-        if (MODE == 1) v = A[(long long)col[s0 + gk] * lda + gi];
-        else if (TA == 0) v = A[(long long)gi * lda + gk];
-        else v = A[(long long)gk * lda + gi];
+      if (e < BM * BK) {
+        const int i = AK ? e / BK : e % BM, k = AK ? e % BK : e / BM;
+        const int gi = row0 + i, gk = kt + k;
+        if (gi < M && gk < kend) {
+          if (MODE == 1) v = A[(long long)col[s0 + gk] * lda + gi];
+          else if (TA == 0) v = A[(long long)gi * lda + gk];
+          else v = A[(long long)gk * lda + gi];
+        }
       }
       ra[r] = v;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LB; ++r) {
       const int e = tid + r * NT;
-      int j, k;
-      if (MODE == 0 && TB == 1) { j = e >> 4; k = e & 15; }
-      else { k = e >> 6; j = e & 63; }
-      const int gj = col0 + j, gk = kt + k;
       double v = 0.0;
-      if (gj < N && gk < kend) {
-        if (MODE == 1) v = B[(s0 + gk) * ldb + gj];
-        else if (TB == 0) v = B[(long long)gk * ldb + gj];
-        else v = B[(long long)gj * ldb + gk];
+      if (e < BN * BK) {
+        const int j = BKc ? e / BK : e % BN, k = BKc ? e % BK : e / BN;
+        const int gj = col0 + j, gk = kt + k;
+        if (gj < N && gk < kend) {
+          if (MODE == 1) v = B[(s0 + gk) * ldb + gj];
+          else if (TB == 0) v = B[(long long)gk * ldb + gj];
+          else v = B[(long long)gj * ldb + gk];
+        }
       }
       rb[r] = v;
     }
   };
   auto store = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LA; ++r) {
       const int e = tid + r * NT;
-      int i, k;
-      if (MODE == 0 && TA == 0) { i = e >> 4; k = e & 15; }
-      else { k = e >> 6; i = e & 63; }
-      As[buf][k][i] = ra[r];
+      if (e < BM * BK) {
+        const int i = AK ? e / BK : e % BM, k = AK ? e % BK : e / BM;
+        As[buf][k][i] = ra[r];
+      }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LB; ++r) {
       const int e = tid + r * NT;
-      int j, k;
-      if (MODE == 0 && TB == 1) { j = e >> 4; k = e & 15; }
-      else { k = e >> 6; j = e & 63; }
-      Bs[buf][k][j] = rb[r];
+      if (e < BN * BK) {
+        const int j = BKc ? e / BK : e % BN, k = BKc ? e % BK : e / BN;
+        Bs[buf][k][j] = rb[r];
+      }
     }
   };
 
@@ -114,16 +142,15 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(
       if (more) load(kt + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        const double2 a01 = *reinterpret_cast<const double2 *>(&As[buf][kk][ty * 4]);
-        const double2 a23 = *reinterpret_cast<const double2 *>(&As[buf][kk][ty * 4 + 2]);
-        const double2 b01 = *reinterpret_cast<const double2 *>(&Bs[buf][kk][tx * 4]);
-        const double2 b23 = *reinterpret_cast<const double2 *>(&Bs[buf][kk][tx * 4 + 2]);
-        const double a[4] = {a01.x, a01.y, a23.x, a23.y};
-        const double bb[4] = {b01.x, b01.y, b23.x, b23.y};
+        double a[TM], bb[TN];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty * TM + i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
       }
       if (more) {
         store(buf ^ 1);
@@ -134,12 +161,12 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(
   }
 
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gi = row0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    const int gi = row0 + ty * TM + i;
     if (gi >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gj = col0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      const int gj = col0 + tx * TN + j;
       if (gj >= N) continue;
       double *p = Cb + (long long)gi * ldcb + gj;
       if (partial) *p = acc[i][j];
@@ -167,12 +194,12 @@ __global__ void splitk_reduce_kernel(int M, int N, int batch, int ksplit,
   }
 }
 
-template <int TA, int TB>
-cudaError_t launch_strided(const GemmArgs &g, int ksplit, int kchunk, int b0, int nb,
-                           double *work, cudaStream_t s) {
-  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), nb * ksplit);
+template <class TL, int TA, int TB>
+cudaError_t launch_strided_t(const GemmArgs &g, int ksplit, int kchunk, int b0, int nb,
+                             double *work, cudaStream_t s) {
+  dim3 grid(ceil_div(g.N, TL::BN), ceil_div(g.M, TL::BM), nb * ksplit);
   const bool part = ksplit > 1;
-  dgemm_kernel<0, TA, TB><<<grid, NT, 0, s>>>(
+  dgemm_kernel<TL, 0, TA, TB><<<grid, TL::NT, 0, s>>>(
       g.M, g.N, g.K, kchunk, ksplit, g.A + (long long)b0 * g.sA, g.lda, g.sA,
       g.B + (long long)b0 * g.sB, g.ldb, g.sB, part ? work : g.C + (long long)b0 * g.sC,
       g.ldc, g.sC, g.alpha, g.beta, part ? 1 : 0, nullptr, nullptr);
@@ -190,18 +217,68 @@ cudaError_t launch_strided(const GemmArgs &g, int ksplit, int kchunk, int b0, in
   return cudaSuccess;
 }
 
+template <class TL>
+cudaError_t launch_strided(const GemmArgs &g, int ks, int kc, int b0, int nb, double *work,
+                           cudaStream_t s) {
+  if (!g.transA && !g.transB) return launch_strided_t<TL, 0, 0>(g, ks, kc, b0, nb, work, s);
+  if (!g.transA && g.transB) return launch_strided_t<TL, 0, 1>(g, ks, kc, b0, nb, work, s);
+  if (g.transA && !g.transB) return launch_strided_t<TL, 1, 0>(g, ks, kc, b0, nb, work, s);
+  return launch_strided_t<TL, 1, 1>(g, ks, kc, b0, nb, work, s);
+}
+
+cudaError_t launch_tile(int tile, const GemmArgs &g, int ks, int kc, int b0, int nb,
+                        double *work, cudaStream_t s) {
+  switch (tile) {
+    case 1: return launch_strided<T40>(g, ks, kc, b0, nb, work, s);
+    case 2: return launch_strided<T48>(g, ks, kc, b0, nb, work, s);
+    case 3: return launch_strided<T100>(g, ks, kc, b0, nb, work, s);
+    default: return launch_strided<T64>(g, ks, kc, b0, nb, work, s);
+  }
+}
+
 void split_plan(const GemmArgs &g, int *ksplit, int *kchunk) {
-  const long long tiles = (long long)ceil_div(g.M, BM) * ceil_div(g.N, BN) * g.batch;
+  const long long tiles = (long long)ceil_div(g.M, RBM) * ceil_div(g.N, RBN) * g.batch;
   int ks = 1;
   if (tiles < 2 * 152 && g.K >= 1024) {
     ks = (int)std::min<long long>((4 * 152 + tiles - 1) / tiles, g.K / 256);
     ks = std::max(1, std::min(ks, 256));
   }
   int kc = ceil_div(g.K, ks);
-  kc = ceil_div(kc, BK) * BK;
+  kc = ceil_div(kc, RBK) * RBK;
   ks = std::max(1, ceil_div(g.K, kc));
   *ksplit = ks;
-  *kchunk = std::max(kc, BK);
+  *kchunk = std::max(kc, RBK);
+}
+
+// ------------------------------------------------------------ autotuner ----
+// The tile shape of each distinct problem shape is chosen once per process:
+// by timing every shape on the first call (when the product does not read C,
+// so repeating it is harmless), else by a model of the padded work.
+struct ShapeKey {
+  int M, N, K, batch, ta, tb, mode;
+  bool operator<(const ShapeKey &o) const {
+    return std::tie(M, N, K, batch, ta, tb, mode) <
+           std::tie(o.M, o.N, o.K, o.batch, o.ta, o.tb, o.mode);
+  }
+};
+std::mutex g_tune_mutex;
+std::map<ShapeKey, int> g_tune;
+
+int model_tile(int M, int N, int K, int batch) {
+  int best = 0;
+  double best_cost = 0;
+  for (int t = 0; t < kNumTiles; ++t) {
+    const int e = kTileEdge[t], d = kTileDepth[t];
+    const double padded = (double)ceil_div(M, e) * e * ceil_div(N, e) * e * ceil_div(K, d) * d;
+    const double blocks = (double)ceil_div(M, e) * ceil_div(N, e) * batch;
+    const double fill = std::min(1.0, blocks / (2.0 * 152));
+    const double cost = padded / fill;
+    if (t == 0 || cost < best_cost * 0.97) {
+      best = t;
+      best_cost = cost;
+    }
+  }
+  return best;
 }
 
 }  // namespace
@@ -226,30 +303,89 @@ cudaError_t dgemm(const GemmArgs &g, double *work, size_t work_elems, cudaStream
   split_plan(g, &ks, &kc);
   if (ks > 1 && work_elems < dgemm_work_elems(g)) return cudaErrorInvalidValue;
   const int per = std::max(1, 65535 / ks);
-  for (int b0 = 0; b0 < g.batch; b0 += per) {
-    const int nb = std::min(per, g.batch - b0);
-    cudaError_t e;
-    if (!g.transA && !g.transB) e = launch_strided<0, 0>(g, ks, kc, b0, nb, work, s);
-    else if (!g.transA && g.transB) e = launch_strided<0, 1>(g, ks, kc, b0, nb, work, s);
-    else if (g.transA && !g.transB) e = launch_strided<1, 0>(g, ks, kc, b0, nb, work, s);
-    else e = launch_strided<1, 1>(g, ks, kc, b0, nb, work, s);
-    RS_TRY(e);
+  const ShapeKey key{g.M, g.N, g.K, g.batch, g.transA, g.transB, 0};
+  int tile = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) tile = it->second;
   }
-  return cudaSuccess;
+  auto run = [&](int t) -> cudaError_t {
+    for (int b0 = 0; b0 < g.batch; b0 += per) {
+      const int nb = std::min(per, g.batch - b0);
+      RS_TRY(launch_tile(t, g, ks, kc, b0, nb, work, s));
+    }
+    return cudaSuccess;
+  };
+  if (tile < 0) {
+    tile = model_tile(g.M, g.N, g.K, g.batch);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    RS_TRY(cudaStreamIsCapturing(s, &cap));
+    if (g.beta == 0.0 && cap == cudaStreamCaptureStatusNone) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      RS_TRY(cudaEventCreate(&e0));
+      RS_TRY(cudaEventCreate(&e1));
+      float best_ms = 0;
+      cudaError_t err = cudaSuccess;
+      for (int t = 0; t < kNumTiles && err == cudaSuccess; ++t) {
+        float ms = 0;
+        err = cudaEventRecord(e0, s);
+        if (err == cudaSuccess) err = run(t);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && (t == 0 || ms < best_ms)) {
+          best_ms = ms;
+          tile = t;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      RS_TRY(err);
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[key] = tile;
+  }
+  return run(tile);
 }
+
+int dgemm_tile_edge(const GemmArgs &g) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune.find(ShapeKey{g.M, g.N, g.K, g.batch, g.transA, g.transB, 0});
+  return it == g_tune.end() ? -1 : kTileEdge[it->second];
+}
+
+namespace {
+template <class TL>
+cudaError_t launch_segmented(int nb, int M, int N, const int *seg, const int *col,
+                             const double *A, long long lda, const double *B, long long ldb,
+                             double *C, long long ldc, long long sC, cudaStream_t s) {
+  dim3 grid(ceil_div(N, TL::BN), ceil_div(M, TL::BM), nb);
+  dgemm_kernel<TL, 1, 1, 0><<<grid, TL::NT, 0, s>>>(M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C, ldc,
+                                                    sC, 1.0, 0.0, 0, seg, col);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t dgemm_segmented(int batch, int M, int N, const int *seg, const int *col,
                             const double *A, long long lda, const double *B, long long ldb,
                             double *C, long long ldc, long long sC, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  // segment lengths vary; plan the tile on a typical depth of 40
+  const int tile = model_tile(M, N, 40, batch);
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     const int nb = std::min(65535, batch - b0);
-    dim3 grid(ceil_div(N, BN), ceil_div(M, BM), nb);
-    dgemm_kernel<1, 1, 0><<<grid, NT, 0, s>>>(M, N, 0, 0, 1, A, lda, 0, B, ldb, 0,
-                                             C + (long long)b0 * sC, ldc, sC, 1.0, 0.0, 0,
-                                             seg + b0, col);
-    ++launch_counter();
-    RS_TRY(cudaGetLastError());
+    double *Cb = C + (long long)b0 * sC;
+    const int *sg = seg + b0;
+    cudaError_t e;
+    switch (tile) {
+      case 1: e = launch_segmented<T40>(nb, M, N, sg, col, A, lda, B, ldb, Cb, ldc, sC, s); break;
+      case 2: e = launch_segmented<T48>(nb, M, N, sg, col, A, lda, B, ldb, Cb, ldc, sC, s); break;
+      case 3: e = launch_segmented<T100>(nb, M, N, sg, col, A, lda, B, ldb, Cb, ldc, sC, s); break;
+      default: e = launch_segmented<T64>(nb, M, N, sg, col, A, lda, B, ldb, Cb, ldc, sC, s);
+    }
+    RS_TRY(e);
   }
   return cudaSuccess;
 }

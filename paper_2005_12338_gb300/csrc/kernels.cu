@@ -416,8 +416,11 @@ __global__ void green_scale_kernel(const double *__restrict__ C, const double *_
 }
 
 // ------------------------------------------------------------------ S7 ----
-constexpr int SP_QC = 8;  // fp64 accumulators per lane: 256 aux functions per pass
-
+// Warp per output row pair (m, j): lanes run over the auxiliary index Q, QC
+// fp64 accumulators per lane (32*QC values of Q per pass).  QC is chosen so
+// that the passes cover N_aux with little padding (the DFMA pipe spends its
+// cycles on padded lanes too).
+template <int QC>
 __global__ void __launch_bounds__(128) dd_spmm_kernel(
     const int *__restrict__ rowptr, const int *__restrict__ pcol, const double *__restrict__ D,
     int P, const double *__restrict__ At, int n, int naux, double *__restrict__ T) {
@@ -427,10 +430,10 @@ __global__ void __launch_bounds__(128) dd_spmm_kernel(
   if (j >= n) return;
   const int a0 = rowptr[m], a1 = rowptr[m + 1];
   const int b0 = rowptr[j], b1 = rowptr[j + 1];
-  for (int q0 = 0; q0 < naux; q0 += 32 * SP_QC) {
-    double acc[SP_QC];
+  for (int q0 = 0; q0 < naux; q0 += 32 * QC) {
+    double acc[QC];
 #pragma unroll
-    for (int c = 0; c < SP_QC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < QC; ++c) acc[c] = 0.0;
     const int qv = naux - q0 - lane;  // lanes with q0 + lane + 32c < naux
     for (int a = a0; a < a1; ++a) {
       const double *Drow = D + (long long)a * P;
@@ -439,12 +442,12 @@ __global__ void __launch_bounds__(128) dd_spmm_kernel(
         const double d = Drow[b];
         const double *ap = Ak + (long long)pcol[b] * naux;
 #pragma unroll
-        for (int c = 0; c < SP_QC; ++c)
+        for (int c = 0; c < QC; ++c)
           if (32 * c < qv) acc[c] = fma(d, ap[32 * c], acc[c]);
       }
     }
 #pragma unroll
-    for (int c = 0; c < SP_QC; ++c)
+    for (int c = 0; c < QC; ++c)
       if (32 * c < qv) T[((long long)m * naux + q0 + lane + 32 * c) * n + j] = acc[c];
   }
 }
@@ -744,8 +747,27 @@ cudaError_t green_scale(const double *C, const double *e, int n, int off, int m,
 
 cudaError_t dd_exchange_spmm(const int *rowptr, const int *pcol, const double *D, int P,
                              const double *At, int n, int naux, double *T, cudaStream_t s) {
+  // accumulators per lane: fewest padded lanes over ceil(naux / (32 QC)) passes
+  static const int kQC[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24};
+  int best = 8;
+  long long best_lanes = -1;
+  for (int qc : kQC) {
+    const long long passes = (naux + 32LL * qc - 1) / (32LL * qc);
+    const long long lanes = passes * 32 * qc + passes * 64;  // small cost per pass
+    if (best_lanes < 0 || lanes < best_lanes) {
+      best_lanes = lanes;
+      best = qc;
+    }
+  }
   dim3 grid(ceil_div(n, 4), n);
-  dd_spmm_kernel<<<grid, 128, 0, s>>>(rowptr, pcol, D, P, At, n, naux, T);
+#define RS_SPMM(QC) \
+  case QC: dd_spmm_kernel<QC><<<grid, 128, 0, s>>>(rowptr, pcol, D, P, At, n, naux, T); break;
+  switch (best) {
+    RS_SPMM(1) RS_SPMM(2) RS_SPMM(3) RS_SPMM(4) RS_SPMM(5) RS_SPMM(6) RS_SPMM(8) RS_SPMM(10)
+    RS_SPMM(12) RS_SPMM(16) RS_SPMM(20) RS_SPMM(24)
+    default: return cudaErrorInvalidValue;
+  }
+#undef RS_SPMM
   RS_LAUNCHED();
   return cudaSuccess;
 }
