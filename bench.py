@@ -31,12 +31,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2005_12338_gb300 import synth  # noqa: E402
+from paper_2005_12338_gb300 import replicas, synth  # noqa: E402
 
 WORKLOAD = "c2_n200"
 # fp64 ALU peak of the DFMA pipe: 152 SMs x 2 fp64 FMA/clock/SM x 2 flop x
 # 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Double-float multiply-add (the exchange contraction with --dd df64): 12 fp32
+# instructions each (TwoProduct with 3 fma, TwoSum, error collection) on
+# 152 SMs x 128 fp32 lanes x 2070 MHz, counted as 2 fp64-equivalent flop.
+DF64_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -47,6 +51,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp64"],
+                    help="chain products: bf16 tensor cores (the chosen form) or fp64 (plain)")
+    ap.add_argument("--dd", default="df64", choices=["df64", "fp64"],
+                    help="exchange contraction of the deterministic block: double-float on "
+                         "the fp32 pipes (chosen) or IEEE fp64")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--eps", type=float, default=None,
+                    help="override the K^L cut eps of the workload (e.g. the paper's 0.1)")
+    ap.add_argument("--cv", action="store_true",
+                    help="also train the learned control variate on an independent run and "
+                         "report its estimate (fp64 chain)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -258,7 +273,9 @@ def our_arm(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     build.build()
-    cfg = synth.CONFIGS[args.workload]
+    cfg = dict(synth.CONFIGS[args.workload])
+    if args.eps is not None:
+        cfg["eps"] = args.eps
     s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
     n, nt, ns = s.n, s.n_tau, cfg["n_s"]
     host = [s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w]
@@ -268,13 +285,17 @@ def our_arm(args):
     h = binding.Handle(local)
     stream = torch.cuda.current_stream(local)
 
-    def step(seed, profile=0):
-        o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, profile=profile)
+    prec = binding.RSSRI_PREC_BF16 if args.precision == "bf16" else binding.RSSRI_PREC_FP64
+    dd = binding.RSSRI_DD_DF64 if args.dd == "df64" else binding.RSSRI_DD_FP64
+
+    def step(seed, profile=0, precision=prec, dd_arith=dd, estimator=binding.RSSRI_EST_CV):
+        o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, profile=profile,
+                                   precision=precision, dd_arith=dd_arith, estimator=estimator)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
         return h.sigma(o, sig, ep)
 
     for k in range(args.warmup):
-        step(rank * 1_000_000 + 900_000 + k)
+        step(replicas.rank_seed(rank, 900_000 + k))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -291,8 +312,10 @@ def our_arm(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(args.steps):
-            e, se, st = step(rank * 1_000_000 + k, profile=1)
+            e, se, st = step(replicas.rank_seed(rank, k), profile=1)
             results.append((e, se, st["t_setup_ms"] + st["t_green_dd_ms"], st["t_sample_ms"]))
+            if k == 0:
+                sig_first = sig.clone()
             prof_ms += st["prof_ms"]
             prof_gf += st["prof_gflop"]
             prof_l += np.array(st["prof_launches"], dtype=np.int64)
@@ -302,13 +325,69 @@ def our_arm(args):
         if world > 1:
             dist.barrier()
     clocks = clk.summary()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replicas.max_over_ranks(e0.elapsed_time(e1), device=f"cuda:{local}")
     units = ns * nt * args.steps * world
-    value = units / (ms_max / 1e3)
+    value = replicas.job_throughput(ns * nt, args.steps, world, ms_max / 1e3)
+
+    # the plain fp64 form on the same seed: throughput and the error of the chosen form
+    compare = None
+    plain = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=binding.RSSRI_DD_FP64)
+    if (args.precision == "bf16" or args.dd == "df64") and not args.no_fp64_compare:
+        step(replicas.rank_seed(rank, 990_001), **plain)  # tunes the fp64 chain shapes
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        e64, se64, st64 = step(replicas.rank_seed(rank, 0), profile=1, **plain)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        sdd = torch.from_numpy(h.export("SIGMA_DD").reshape(nt, n, n)).to(sig.device)
+        st_ref = sig - 0.5 * (sdd + sdd.transpose(1, 2))
+        err_sigma = float(torch.linalg.norm(sig_first - sig) / torch.linalg.norm(sig))
+        err_st = float(torch.linalg.norm(sig_first - sig) / torch.linalg.norm(st_ref))
+        res64 = [(e64, se64, st64["t_setup_ms"] + st64["t_green_dd_ms"], st64["t_sample_ms"])]
+        compare = {"plain_fp64_units_per_s": ns * nt / (ms64 / 1e3),
+                   "plain_fp64_ms_per_step": ms64,
+                   "plain_fp64_sampling_ms_per_step": st64["t_sample_ms"],
+                   "chosen_sampling_ms_per_step": float(np.mean([r[3] for r in results])),
+                   "sampling_speedup": st64["t_sample_ms"] / float(np.mean([r[3] for r in results])),
+                   "bf16_vs_fp64_same_seed": {
+                       "sigma_rel_fro": err_sigma,
+                       "sigma_stochastic_part_rel_fro": err_st,
+                       "e_corr_abs": abs(results[0][0] - e64),
+                       "e_corr_rel": abs(results[0][0] - e64) / abs(e64),
+                       "e_stderr": se64},
+                   "time_to_1mEh_plain_fp64_s": time_to_target(res64, ns, 1e-3)}
+
+    # Sec. IV: the range-separated estimator against plain stochastic RI at the
+    # same number of sample pairs and the same seed
+    e_sri, se_sri, _ = step(replicas.rank_seed(rank, 0), estimator=binding.RSSRI_EST_SRI)
+    rs_vs_sri = {"e_corr_rs": results[0][0], "stderr_rs": results[0][1], "e_corr_sri": e_sri,
+                 "stderr_sri": se_sri, "stderr_ratio_sri_over_rs": se_sri / results[0][1],
+                 "agree_within_3_sigma": abs(e_sri - results[0][0]) <
+                 3 * (se_sri ** 2 + results[0][1] ** 2) ** 0.5}
+
+    # learned control variate (fp64 chain): train on an independent run, then
+    # estimate with it on the first timed seed, next to the plain estimate
+    cv_report = None
+    if args.cv:
+        tr = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 777),
+                                    dd_arith=dd)
+        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=tr)
+        c0 = time.perf_counter()
+        lb, la = h.cv_train(tr, synth.mlp_init(0), 400, 4096, 1e-3)
+        t_train = time.perf_counter() - c0
+        ev = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=dd)
+        e_cv, se_cv, st_cv = step(replicas.rank_seed(rank, 0), **ev,
+                                  estimator=binding.RSSRI_EST_CV)
+        o_cv = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 0),
+                                      dd_arith=dd, cv=1)
+        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o_cv)
+        e_l, se_l, st_l = h.sigma(o_cv, sig, ep)
+        cv_report = {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
+                     "e_corr_plain": e_cv, "stderr_plain": se_cv, "e_corr_learned": e_l,
+                     "stderr_learned": se_l, "stderr_ratio_plain_over_learned": se_cv / se_l}
 
     # end to end through the C ABI with host buffers (pinned), copies included
     e2e = None
@@ -319,20 +398,18 @@ def our_arm(args):
         hh = binding.Handle(local)
 
         def step_host(seed):
-            o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed)
+            o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, precision=prec,
+                                       dd_arith=dd)
             hh.setup(*pinned, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
             return hh.sigma(o, sig_h, ep_h)
-        step_host(rank * 1_000_000 + 990_000)
+        step_host(replicas.rank_seed(rank, 990_000))
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            step_host(rank * 1_000_000 + k)
-        el = time.perf_counter() - t0
-        te = torch.tensor([el], dtype=torch.float64, device=f"cuda:{local}")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": units / float(te.item()), "unit": "units/s",
+            step_host(replicas.rank_seed(rank, k))
+        el = replicas.max_over_ranks(time.perf_counter() - t0, device=f"cuda:{local}")
+        e2e = {"value": units / el, "unit": "units/s",
                "h2d_bytes_per_step": int(sum(a.nbytes for a in host)),
                "d2h_bytes_per_step": int(sig_h.nbytes + ep_h.nbytes + 4 * 8)}
         hh.close()
@@ -347,13 +424,30 @@ def our_arm(args):
     name = binding.PROF_CLASSES[dom]
     per_launch_gf = prof_gf[dom] / max(prof_l[dom], 1)
     achieved = prof_gf[dom] / (prof_ms[dom] / 1e3) / 1e3  # TFLOP/s
-    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+    if name in ("dd_spmm", "dd_gemm") and args.dd == "df64":
+        peak = DF64_PEAK_TFLOPS
+        psrc = ("derived: 152 SMs x 128 fp32 lanes x 2070 MHz / 12 fp32 instructions per "
+                "double-float multiply-add x 2 flop (fp64-equivalent)")
+    elif name == "chain_gemm" and args.precision == "bf16":
+        peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        psrc = "bf16 dense tensor peak, " + peak_src
+    else:
+        peak = FP64_PEAK_TFLOPS
+        psrc = "derived: 152 SMs x 2 fp64 FMA/clk/SM x 2 flop x 2070 MHz (fp64 DFMA pipe)"
+    roofline = {"bound": "tensor" if (name == "chain_gemm" and args.precision == "bf16") else "alu",
+                "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_for(name),
-                "peak_source": "derived: 152 SMs x 2 fp64 FMA/clk/SM x 2 flop x 2070 MHz "
-                               "(fp64 DFMA pipe; HBM/bf16 peaks " + peak_src + ")",
+                "peak_source": psrc + "; HBM/bf16 peaks " + peak_src,
                 "gflop_per_launch": per_launch_gf, "launches": int(prof_l[dom]),
                 "share_of_step": float(prof_ms[dom] / max(prof_ms.sum(), 1e-9))}
+    tensor = None
+    if args.precision == "bf16":
+        bf16_peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        tf = prof_gf[0] / (prof_ms[0] / 1e3) / 1e3
+        tensor = {"kernel": "chain_gemm (tcgen05 bf16)", "bound": "tensor", "achieved": tf,
+                  "peak": bf16_peak, "unit": "TFLOP/s", "frac": tf / bf16_peak,
+                  "peak_source": peak_src}
     classes = {binding.PROF_CLASSES[c]: {"ms_per_step": prof_ms[c] / args.steps,
                                          "gflop_per_step": prof_gf[c] / args.steps,
                                          "launches_per_step": int(prof_l[c]) // args.steps,
@@ -363,10 +457,14 @@ def our_arm(args):
     line = {"metric": "Sigma(tau) units/s (unit = one sample pair x one tau point)",
             "value": value, "unit": "units/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("bf16+" if args.precision == "bf16" else "") +
+                     ("df64+f64" if args.dd == "df64" else "f64"), "data": "synthetic",
             "config": {"workload": f"{args.workload}: N={n} n_occ={s.n_occ} N_aux={s.n_aux} "
                                    f"N_tau={nt} N_s={ns} eps={cfg['eps']} "
                                    f"eps'={cfg['eps_prime']}, whole path per step",
+                       "chain_precision": args.precision,
+                       "dd_exchange_arith": args.dd,
                        "l2": "inputs larger than L2 (3-index integrals 192 MB); steps of seconds",
                        "parallelism": f"replicas x{world} (independent seeds, no collective)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
@@ -374,7 +472,9 @@ def our_arm(args):
             "extra": {"e_corr_per_step": [r[0] for r in results],
                       "e_stderr_per_step": [r[1] for r in results],
                       "time_to_1mEh_s": time_to_target(results, ns, 1e-3),
-                      "classes": classes}}
+                      "classes": classes, "tensor_roofline": tensor,
+                      "chosen_vs_plain_fp64": compare, "rs_vs_sri_same_n_s": rs_vs_sri,
+                      "learned_control_variate": cv_report}}
     if not args.no_cpu_baseline and world == 1:
         cb = oracle_sample(s, cfg, 0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

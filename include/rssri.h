@@ -75,8 +75,16 @@ enum { RSSRI_PTR_DEVICE = 0, RSSRI_PTR_HOST = 1 };
  * Eq. 10 (the eps -> 1 limit of Sec. II). */
 enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1 };
 
-/* Arithmetic of the chain products (Sec. III, Eq. 25). */
-enum { RSSRI_PREC_FP64 = 0 };
+/* Arithmetic of the chain products of the stochastic part (S8).
+ * RSSRI_PREC_FP64: every product in fp64 (the plain form).
+ * RSSRI_PREC_BF16: the chain is evaluated in the range-separated split of
+ *   Eqs. 14-15 (C^L = R^L G R'^L, dC = R^S G R' + R^L G R'^S, so that the
+ *   difference F(R,R') - F(R^L,R'^L) is formed from small terms only) with
+ *   bf16 operands and fp32 accumulation on the tensor cores; V^{-1/2}, the
+ *   deterministic block, traces and energies stay fp64.  Needs N >= 16 and a
+ *   GPU with tcgen05 (sm_100 family); its error is of relative order 1e-3 of
+ *   the stochastic remainder Sigma - Sigma_DD. */
+enum { RSSRI_PREC_FP64 = 0, RSSRI_PREC_BF16 = 1 };
 
 typedef struct rssri_handle rssri_handle;
 
@@ -124,10 +132,18 @@ typedef struct {
  *   xi_offset  first sample index (resume: runs over [xi_offset, xi_offset+n_s)
  *              concatenate exactly), xi_offset + n_s < 2^40.
  *   estimator  RSSRI_EST_CV or RSSRI_EST_SRI.
- *   precision  RSSRI_PREC_FP64.
- *   pair_batch sample pairs processed per group of launches (0 = all).
+ *   precision  RSSRI_PREC_FP64 or RSSRI_PREC_BF16 (chain products only).
+ *   pair_batch sample pairs processed per group of launches (0 = all;
+ *              fp64 chain only, the bf16 chain takes all pairs at once).
  *   profile    1: time every kernel class with CUDA events on the handle's
- *              stream (rssri_stats.prof_*); 0: off. */
+ *              stream (rssri_stats.prof_*); 0: off.
+ *   cv         1: weight the large-part control variate element-wise by the
+ *              coefficients c_ij(tau) of the network trained by
+ *              rssri_cv_train (fp64 chain and RSSRI_EST_CV only); 0: c = 1.
+ *   dd_arith   arithmetic of the exchange contraction of the deterministic
+ *              block: RSSRI_DD_FP64 (IEEE fp64 FMAs) or RSSRI_DD_DF64
+ *              (double-float: each fp64 value as a pair of floats, error-free
+ *              products and sums on the fp32 pipes, ~1e-13 relative). */
 typedef struct {
   double eps_prime, eps;
   int64_t n_s;
@@ -137,8 +153,12 @@ typedef struct {
   int32_t precision;
   int64_t pair_batch;
   int32_t profile;
+  int32_t dd_arith;
+  int32_t cv;         /* 1: apply the learned control variate (see rssri_cv_train) */
   int32_t reserved0;
 } rssri_options;
+
+enum { RSSRI_DD_FP64 = 0, RSSRI_DD_DF64 = 1 };
 
 /* Kernel classes of the per-class profile (rssri_stats.prof_*). */
 enum {
@@ -249,7 +269,9 @@ typedef enum {
   RSSRI_BUF_G = 7,          /* [n_tau][n][n]        G(tau)                            */
   RSSRI_BUF_GB = 8,         /* [n_tau][n][n]        G(beta - tau)                     */
   RSSRI_BUF_SIGMA_DD = 9,   /* [n_tau][n][n]        deterministic block               */
-  RSSRI_BUF_SIGMA_RAW = 10  /* [n_tau][n][n]        Sigma before symmetrisation       */
+  RSSRI_BUF_SIGMA_RAW = 10, /* [n_tau][n][n]        Sigma before symmetrisation       */
+  RSSRI_BUF_CV_PARAMS = 11, /* [RSSRI_CV_NPARAM] float: network parameters             */
+  RSSRI_BUF_CV_C = 12       /* [n_tau][n][n]        coefficients c of the last cv run   */
 } rssri_buffer;
 
 /* Size in bytes of an intermediate (0 if it does not exist yet). */
@@ -258,6 +280,47 @@ RSSRI_API int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes);
 /* Copy an intermediate to `dst` (device or host per dst_kind); `bytes` must
  * equal rssri_buffer_bytes().  Synchronises the handle's stream. */
 RSSRI_API int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_kind);
+
+/* ------------------------------------------- learned control variate */
+
+/* The large part of Eq. 25 is a control variate with an exactly known mean:
+ * for independent theta, theta', E[F(R^L, R'^L)] = Sigma_DD.  So for any
+ * coefficients c_ij(tau) fixed independently of the draws they are used with,
+ *   Sigma_c = mean_xi F(R, R') - c o (mean_xi F(R^L, R'^L) - Sigma_DD)
+ * is unbiased (c = 1 is the default estimator), and per element its variance
+ * is smallest at c* = Cov(F, F^L) / Var(F^L).  A network maps features of
+ * (i, j, tau) to c: |i-j|/N, ln tau / ln beta, Sigma_DD_ij / max|Sigma_DD|,
+ * G_ii, G_jj, Gb_ii, Gb_jj (each over its largest diagonal magnitude), the
+ * norms of rows i and j of [K]^L over their largest, [i == j]; layers
+ * 10 -> 256 -> 256 -> 256 -> 1 with SiLU, c = 1 + output; fp32.
+ * Parameter layout (floats): W0[256][10] b0[256] W1[256][256] b1[256]
+ * W2[256][256] b2[256] W3[1][256] b3[1]. */
+#define RSSRI_CV_NPARAM 134657
+
+/* Train the network on an independent run: evaluates the fp64 chain with
+ * options `o` (precision FP64, estimator CV; use a seed not used for the
+ * estimates), collects per-element sums of F, F^L and their products, forms
+ * the targets c* and weights Var(F^L), and runs `steps` Adam steps (learning
+ * rate lr, betas 0.9/0.999) on minibatches of `batch` elements, minimising
+ * sum w (c - c*)^2 / sum w, on the GPU.  init_params: host, RSSRI_CV_NPARAM
+ * floats.  loss_before/after (host, may be NULL): that loss at init_params and
+ * after training, over the first 65536 elements in a fixed order.
+ * Errors: NOT_READY, INVALID_ARG, OOM, CUDA. */
+RSSRI_API int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_params,
+                             int steps, int batch, float lr, double *loss_before,
+                             double *loss_after);
+
+/* Load network parameters (host, RSSRI_CV_NPARAM floats) instead of training;
+ * they are used by rssri_sigma with options.cv = 1. */
+RSSRI_API int rssri_cv_set_params(rssri_handle *h, const float *params);
+
+/* The training loss and its gradient for given parameters and data (all host
+ * arrays): x [m][10] features, target [m], weight [m], params
+ * [RSSRI_CV_NPARAM]; writes loss (1 float) and grad [RSSRI_CV_NPARAM].
+ * Evaluated by the same GPU kernels that train the network. */
+RSSRI_API int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target,
+                                 const float *weight, int m, const float *params, float *loss,
+                                 float *grad);
 
 /* ---------------------------------------------------- allocation-free */
 

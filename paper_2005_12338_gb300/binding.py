@@ -18,9 +18,11 @@ LIB_PATH = os.path.join(HERE, "librssri.so")
 
 RSSRI_PTR_DEVICE, RSSRI_PTR_HOST = 0, 1
 RSSRI_EST_CV, RSSRI_EST_SRI = 0, 1
-RSSRI_PREC_FP64 = 0
+RSSRI_PREC_FP64, RSSRI_PREC_BF16 = 0, 1
+RSSRI_DD_FP64, RSSRI_DD_DF64 = 0, 1
 BUF = dict(W=0, COLMAX=1, ERI_L=2, K_L=3, THETA=4, R=5, R_L=6, G=7, GB=8, SIGMA_DD=9,
-           SIGMA_RAW=10)
+           SIGMA_RAW=10, CV_PARAMS=11, CV_C=12)
+RSSRI_CV_NPARAM = 134657
 PROF_CLASSES = ["chain_gemm", "dd_spmm", "dd_gemm", "factor_gemm", "setup_gemm", "green", "other"]
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_SPD", -3: "NONSYMMETRIC_ERI", -4: "OOM",
           -5: "CUDA", -6: "TIMEOUT", -7: "NOT_READY", -8: "NONFINITE"}
@@ -38,7 +40,7 @@ class rssri_options(C.Structure):
     _fields_ = [("eps_prime", C.c_double), ("eps", C.c_double), ("n_s", C.c_int64),
                 ("seed", C.c_uint64), ("xi_offset", C.c_int64), ("estimator", C.c_int32),
                 ("precision", C.c_int32), ("pair_batch", C.c_int64), ("profile", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("dd_arith", C.c_int32), ("cv", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class rssri_stats(C.Structure):
@@ -80,6 +82,12 @@ SIGNATURES = {
     "rssri_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
     "rssri_energy_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                       C.c_int, C.c_void_p, C.c_void_p]),
+    "rssri_cv_train": (C.c_int, [C.c_void_p, C.POINTER(rssri_options), C.c_void_p, C.c_int,
+                                 C.c_int, C.c_float, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
+    "rssri_cv_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rssri_cv_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 RSSRI_STATIC_MAX_TAU = 4096
 
@@ -156,9 +164,10 @@ class Handle:
 
     @staticmethod
     def options(eps_prime=0.02, eps=1e-3, n_s=64, seed=0, xi_offset=0, estimator=RSSRI_EST_CV,
-                pair_batch=0, profile=0) -> rssri_options:
+                pair_batch=0, profile=0, precision=RSSRI_PREC_FP64,
+                dd_arith=RSSRI_DD_FP64, cv=0) -> rssri_options:
         return rssri_options(eps_prime, eps, n_s, seed & ((1 << 64) - 1), xi_offset, estimator,
-                             RSSRI_PREC_FP64, pair_batch, profile, 0)
+                             precision, pair_batch, profile, dd_arith, cv, 0)
 
     def setup(self, eri3, metric, orb_e, orb_c, tau, tau_w, n_occ: int, mu: float, beta: float,
               opts: rssri_options):
@@ -192,11 +201,47 @@ class Handle:
             check(rc, "rssri_sigma_from_g")
         return e.value, se.value, st.as_dict()
 
+    def cv_train(self, opts: rssri_options, init_params: np.ndarray, steps: int, batch: int,
+                 lr: float):
+        """rssri_cv_train; returns (loss_before, loss_after)."""
+        p = np.ascontiguousarray(init_params, dtype=np.float32)
+        if p.size != RSSRI_CV_NPARAM:
+            raise ValueError("init_params must hold RSSRI_CV_NPARAM floats")
+        a, b = C.c_double(), C.c_double()
+        check(lib().rssri_cv_train(self._h, C.byref(opts), p.ctypes.data, steps, batch, lr,
+                                   C.byref(a), C.byref(b)), "rssri_cv_train")
+        return a.value, b.value
+
+    def cv_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != RSSRI_CV_NPARAM:
+            raise ValueError("params must hold RSSRI_CV_NPARAM floats")
+        check(lib().rssri_cv_set_params(self._h, p.ctypes.data), "rssri_cv_set_params")
+
+    def cv_loss_grad(self, x, target, weight, params):
+        """rssri_cv_loss_grad on host float32 arrays; returns (loss, grad)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        w = np.ascontiguousarray(weight, dtype=np.float32)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        grad = np.zeros(RSSRI_CV_NPARAM, dtype=np.float32)
+        check(lib().rssri_cv_loss_grad(self._h, x.ctypes.data, t.ctypes.data, w.ctypes.data,
+                                       x.shape[0], p.ctypes.data, loss.ctypes.data,
+                                       grad.ctypes.data), "rssri_cv_loss_grad")
+        return float(loss[0]), grad
+
     def export(self, name: str) -> np.ndarray:
-        """Copy an intermediate (rssri_export) to a host float64 array."""
+        """Copy an intermediate (rssri_export) to a host array (float32 for
+        CV_PARAMS, float64 otherwise)."""
         which = BUF[name]
         nb = C.c_size_t()
         check(lib().rssri_buffer_bytes(self._h, which, C.byref(nb)), "rssri_buffer_bytes")
+        if name == "CV_PARAMS":
+            out = np.empty(nb.value // 4, dtype=np.float32)
+            check(lib().rssri_export(self._h, which, out.ctypes.data, nb.value, RSSRI_PTR_HOST),
+                  "rssri_export")
+            return out
         out = np.empty(nb.value // 8, dtype=np.float64)
         check(lib().rssri_export(self._h, which, out.ctypes.data, nb.value, RSSRI_PTR_HOST),
               "rssri_export")

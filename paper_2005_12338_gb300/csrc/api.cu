@@ -6,7 +6,11 @@
 #include <new>
 #include <vector>
 
+#include "chain_bf16.cuh"
+#include "cv_mlp.cuh"
+#include "dd_df64.cuh"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 
 using namespace rssri;
 
@@ -72,6 +76,21 @@ struct rssri_handle {
   // sigma buffers
   DevBuf theta, Ut, fac, RLp, G, Gb, cs, XG, Cc, Bm, BC, tarr, sarr, e_st, sig_raw, sdd, PG, At,
       T, AP, Gam, L, trdd, tr, res, sig_out, e_pair, gwork, outbuf;
+  // learned control variate
+  DevBuf cv_params, cv_m, cv_v, cv_grad, cv_ptmp, cv_act, cv_work, cv_X, cv_t, cv_w, cv_stats, cv_c,
+      cv_scr, cv_bx, cv_bt, cv_bw, cv_loss;
+  bool cv_ready = false, cv_c_ready = false;
+  // double-float copies for the exchange contraction
+  DevBuf Dhl, Ahl;
+  bool d_df64_ready = false;
+  // bf16 chain buffers
+  DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
+  // the bf16 chain captured as a CUDA graph, valid for the key it was built for
+  cudaGraphExec_t chain_graph = nullptr;
+  cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot capture)
+  std::vector<uintptr_t> chain_key_ptr;
+  std::vector<double> chain_key_w;
+  long long chain_graph_launches = 0;
   long long last_ns = 0;
   bool have_sigma = false;
   rssri_stats stats{};
@@ -171,8 +190,11 @@ int validate_options(const rssri_options *o, bool for_sigma) {
         o->xi_offset + o->n_s >= (1LL << 40))
       return RSSRI_ERR_INVALID_ARG;
     if (o->estimator != RSSRI_EST_CV && o->estimator != RSSRI_EST_SRI) return RSSRI_ERR_INVALID_ARG;
-    if (o->precision != RSSRI_PREC_FP64) return RSSRI_ERR_INVALID_ARG;
+    if (o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_BF16)
+      return RSSRI_ERR_INVALID_ARG;
     if (o->pair_batch < 0) return RSSRI_ERR_INVALID_ARG;
+    if (o->dd_arith != RSSRI_DD_FP64 && o->dd_arith != RSSRI_DD_DF64) return RSSRI_ERR_INVALID_ARG;
+    if (o->cv != 0 && o->cv != 1) return RSSRI_ERR_INVALID_ARG;
   }
   return RSSRI_OK;
 }
@@ -206,6 +228,15 @@ cudaError_t gemm(rssri_handle *h, const GemmArgs &g) {
 cudaError_t gemm_p(rssri_handle *h, int cls, const GemmArgs &g) {
   SPAN(cls, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
   return gemm(h, g);
+}
+
+// The same in double-float arithmetic when `df64` (deterministic block).
+cudaError_t gemm_dd(rssri_handle *h, const GemmArgs &g, bool df64) {
+  if (!df64) return gemm_p(h, RSSRI_PROF_DD_GEMM, g);
+  SPAN(RSSRI_PROF_DD_GEMM, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
+  const size_t need = dgemm_work_elems(g) * sizeof(double);
+  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
+  return dgemm_df64(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
 }
 
 // ------------------------------------------------------------ S1: V^-1/2 --
@@ -330,11 +361,18 @@ void rssri_destroy(rssri_handle *h) {
                     &h->pcol, &h->rowptr, &h->KP, &h->D, &h->theta, &h->Ut, &h->fac, &h->RLp,
                     &h->G, &h->Gb, &h->cs, &h->XG, &h->Cc, &h->Bm, &h->BC, &h->tarr, &h->sarr,
                     &h->e_st, &h->sig_raw, &h->sdd, &h->PG, &h->At, &h->T, &h->AP, &h->Gam, &h->L,
-                    &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf};
+                    &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
+                    &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
+                    &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
+                    &h->Ahl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
+                    &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
+                    &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss};
   for (DevBuf *b : bufs) release(*b);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto e : h->evpool) cudaEventDestroy(e);
+  if (h->chain_graph) cudaGraphExecDestroy(h->chain_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
@@ -349,6 +387,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   cudaStream_t s = h->stream;
   h->ready = false;
   h->have_sigma = false;
+  h->d_df64_ready = false;
   const int n = p->n, na = p->n_aux, nt = p->n_tau;
   const long long nn = (long long)n * n;
   cudaError_t e;
@@ -520,7 +559,8 @@ cudaError_t build_green(rssri_handle *h) {
 // K = [K]^L.  With PG^Q = K^Q G, At^Q = Gb K^Q G, Gamma_QQ' = Tr(K^Q G K^Q' Gb),
 // L^Q = sum_Q' Gamma_QQ' K^Q' and T^Q = sum_Q' K^Q' At^Q K^Q' (built in pair
 // space from D = v^L):  Sigma_DD = sum_Q K^Q G (2 L^Q - T^Q).
-cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, double *out) {
+cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, double *out,
+                         bool df64) {
   cudaStream_t s = h->stream;
   const int n = h->n, na = h->n_aux, P = h->P;
   const long long nn = (long long)n * n;
@@ -536,11 +576,21 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = Gb; g.lda = n;
     g.B = PG; g.ldb = (long long)n * na;
     g.C = At; g.ldc = (long long)n * na;
-    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+    RS_TRY(gemm_dd(h, g, df64));
   }
   // T[m][Q][j] = sum_{a in row m, b in row j} D[a][b] At[(col a, col b)][Q]
+  if (df64) {
+    {
+      SPAN(RSSRI_PROF_OTHER, 0.0);
+      RS_TRY(to_df64(At, nn * na, h->Ahl.as<float2>(), s));
+    }
+    SPAN(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9);
+    RS_TRY(dd_exchange_spmm_df64(h->rowptr.as<int>(), h->pcol.as<int>(), h->Dhl.as<float2>(), P,
+                                 h->Ahl.as<float2>(), n, na, T, s));
+  } else {
   { SPAN(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9); RS_TRY(dd_exchange_spmm(h->rowptr.as<int>(), h->pcol.as<int>(), h->D.as<double>(), P, At, n, na,
                           T, s)); }
+  }
   // Gamma = K_P^T At_P, At_P the rows of At at the kept pairs
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
   {
@@ -549,7 +599,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = h->KP.as<double>(); g.lda = na; g.transA = 1;
     g.B = h->AP.as<double>(); g.ldb = na;
     g.C = h->Gam.as<double>(); g.ldc = na;
-    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+    RS_TRY(gemm_dd(h, g, df64));
   }
   // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
   {
@@ -558,7 +608,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = h->KP.as<double>(); g.lda = na;
     g.B = h->Gam.as<double>(); g.ldb = na; g.transB = 1;
     g.C = h->L.as<double>(); g.ldc = na;
-    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+    RS_TRY(gemm_dd(h, g, df64));
   }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s)); }
   // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n]
@@ -569,7 +619,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.B = T; g.ldb = n;
     g.C = out; g.ldc = n;
     g.alpha = -1.0;
-    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+    RS_TRY(gemm_dd(h, g, df64));
   }
   return cudaSuccess;
 }
@@ -585,14 +635,199 @@ size_t dd_work_need(rssri_handle *h) {
   return w;
 }
 
+// S8 in bf16 on the tensor cores, all sample pairs at once, for every tau:
+//   P = [R^S; R^L] G,  dC = P_S R' + P_L R'^S,  C^L = P_L R'^L,
+//   [X; Y] = [dC; C^L] Gb,  fold (traces, energy, 2 dt I - X, 2 t^L I - Y, C^T, dC^T),
+//   sum_x (2 dt I - X) C + (2 t^L I - Y) dC  (one contraction over the pairs).
+// sig[t] = sdd[t] + that sum / n_s.  e_st accumulates the pair energies.
+// The launches are issued into a CUDA graph once and the graph is replayed
+// while the shapes, buffers and tau weights stay the same.
+struct ChainBufs {
+  __nv_bfloat16 *xsl, *y3, *gh, *gbh, *P, *dcl16, *a6, *ct, *dct;
+  float *dc32, *cl32, *xy32, *part;
+  double *fold;
+  int bpc, groups;
+};
+
+cudaError_t issue_chain_bf16(rssri_handle *h, cudaStream_t s, int ns, const double *G,
+                             const double *Gb, double *sig, int *err, const ChainBufs &b) {
+  const int n = h->n, nt = h->n_tau;
+  const int ldp = (n + 7) / 8 * 8;
+  const long long nn = (long long)n * n, mat = (long long)n * ldp;
+  RS_TRY(bf16_factors(h->fac.as<double>(), ns, n, ldp, b.xsl, b.y3, s));
+  RS_TRY(bf16_matrices(G, nt, n, ldp, b.gh, s));
+  RS_TRY(bf16_matrices(Gb, nt, n, ldp, b.gbh, s));
+  const double ne = 2.0 * h->n_occ;
+  auto op = [&](const __nv_bfloat16 *p, long long sb, int rows) {
+    TcOperand t;
+    t.ptr = p;
+    t.ld = ldp;
+    t.sb = sb;
+    t.rows = rows;
+    return t;
+  };
+  for (int t = 0; t < nt; ++t) {
+    const __nv_bfloat16 *gt = b.gh + t * mat, *gbt = b.gbh + t * mat;
+    {  // P = [R^S; R^L] G (stacked rows of all pairs)
+      TcGemm g;
+      g.M = 2 * ns * n; g.N = n; g.K[0] = n;
+      g.A[0] = op(b.xsl, 0, 2 * ns * n); g.B[0] = op(gt, 0, n);
+      g.c16 = b.P; g.ldc16 = ldp; g.err = err;
+      RS_TRY(tc_gemm(g, s));
+    }
+    {  // dC = P_S R' + P_L R'^S
+      TcGemm g;
+      g.M = n; g.N = n; g.batch = ns; g.nseg = 2; g.K[0] = g.K[1] = n;
+      g.A[0] = op(b.P, mat, n); g.B[0] = op(b.y3, mat, n);
+      g.A[1] = op(b.P + ns * mat, mat, n); g.B[1] = op(b.y3 + ns * mat, mat, n);
+      g.c32 = b.dc32; g.c16 = b.dcl16; g.ldc16 = ldp; g.err = err;
+      RS_TRY(tc_gemm(g, s));
+    }
+    {  // C^L = P_L R'^L
+      TcGemm g;
+      g.M = n; g.N = n; g.batch = ns; g.K[0] = n;
+      g.A[0] = op(b.P + ns * mat, mat, n); g.B[0] = op(b.y3 + 2 * ns * mat, mat, n);
+      g.c32 = b.cl32; g.c16 = b.dcl16 + ns * mat; g.ldc16 = ldp; g.err = err;
+      RS_TRY(tc_gemm(g, s));
+    }
+    {  // [X; Y] = [dC; C^L] Gb
+      TcGemm g;
+      g.M = 2 * ns * n; g.N = n; g.K[0] = n;
+      g.A[0] = op(b.dcl16, 0, 2 * ns * n); g.B[0] = op(gbt, 0, n);
+      g.c32 = b.xy32; g.err = err;
+      RS_TRY(tc_gemm(g, s));
+    }
+    RS_TRY(fold_bf16(b.xy32, b.dc32, b.cl32, ns, n, ldp, h->h_tau_w[t], ne, b.a6, b.ct, b.dct,
+                     h->e_st.as<double>(), b.fold, s));
+    {  // sum over pairs of (2 dt I - X) C + (2 t^L I - Y) dC
+      TcGemm g;
+      g.M = n; g.N = n; g.batch = ns; g.bpc = b.bpc; g.nseg = 2; g.K[0] = g.K[1] = n;
+      g.A[0] = op(b.a6, mat, n); g.B[0] = op(b.ct, mat, n);
+      g.A[1] = op(b.a6 + ns * mat, mat, n); g.B[1] = op(b.dct, mat, n);
+      g.c32 = b.part; g.err = err;
+      RS_TRY(tc_gemm(g, s));
+    }
+    RS_TRY(reduce_bf16(b.part, b.groups, n, h->sdd.as<double>() + t * nn, (double)ns,
+                       sig + t * nn, s));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t chain_bf16(rssri_handle *h, int ns, const double *G, const double *Gb, double *sig,
+                       int *err) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, nt = h->n_tau;
+  const int ldp = (n + 7) / 8 * 8;
+  const long long nn = (long long)n * n, mat = (long long)n * ldp;
+  const size_t b16 = sizeof(__nv_bfloat16);
+  ChainBufs b;
+  b.bpc = std::max(1, ceil_div(ns, 152));
+  b.groups = ceil_div(ns, b.bpc);
+  RS_TRY(ensure(h->hxsl, 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hy3, 3 * ns * mat * b16));
+  RS_TRY(ensure(h->hg, nt * mat * b16));
+  RS_TRY(ensure(h->hgb, nt * mat * b16));
+  RS_TRY(ensure(h->hP, 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hdc32, ns * nn * sizeof(float)));
+  RS_TRY(ensure(h->hcl32, ns * nn * sizeof(float)));
+  RS_TRY(ensure(h->hdcl16, 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hxy32, 2 * ns * nn * sizeof(float)));
+  RS_TRY(ensure(h->ha6, 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hct, ns * mat * b16));
+  RS_TRY(ensure(h->hdct, ns * mat * b16));
+  RS_TRY(ensure(h->hpart, b.groups * nn * sizeof(float)));
+  RS_TRY(ensure(h->hfold, (size_t)ns * ceil_div(n, 32) * 4 * sizeof(double)));
+  auto bf = [](DevBuf &x) { return x.as<__nv_bfloat16>(); };
+  b.xsl = bf(h->hxsl); b.y3 = bf(h->hy3); b.gh = bf(h->hg); b.gbh = bf(h->hgb); b.P = bf(h->hP);
+  b.dcl16 = bf(h->hdcl16); b.a6 = bf(h->ha6); b.ct = bf(h->hct); b.dct = bf(h->hdct);
+  b.dc32 = h->hdc32.as<float>(); b.cl32 = h->hcl32.as<float>(); b.xy32 = h->hxy32.as<float>();
+  b.part = h->hpart.as<float>();
+  b.fold = h->hfold.as<double>();
+  RS_TRY(tc_prepare());
+  // the graph is keyed on every pointer and value baked into its launches
+  std::vector<uintptr_t> key = {(uintptr_t)ns, (uintptr_t)n, (uintptr_t)nt, (uintptr_t)h->n_occ,
+                                (uintptr_t)G, (uintptr_t)Gb, (uintptr_t)sig, (uintptr_t)err,
+                                (uintptr_t)h->fac.p, (uintptr_t)h->e_st.p, (uintptr_t)h->sdd.p};
+  for (DevBuf *d : {&h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32, &h->hdcl16,
+                    &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold})
+    key.push_back((uintptr_t)d->p);
+  if (!h->chain_graph || key != h->chain_key_ptr || h->h_tau_w != h->chain_key_w) {
+    if (h->chain_graph) cudaGraphExecDestroy(h->chain_graph);
+    h->chain_graph = nullptr;
+    cudaGraph_t graph = nullptr;
+    if (!h->cap_stream) RS_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    RS_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = launch_counter();
+    const cudaError_t ei = issue_chain_bf16(h, h->cap_stream, ns, G, Gb, sig, err, b);
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    const long long captured = launch_counter() - l0;
+    launch_counter() = l0;  // captured, not yet run
+    if (ei != cudaSuccess || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return ei != cudaSuccess ? ei : ec;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t eg = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    RS_TRY(eg);
+    h->chain_graph = exec;
+    h->chain_key_ptr = key;
+    h->chain_key_w = h->h_tau_w;
+    h->chain_graph_launches = captured;
+  }
+  SPAN(RSSRI_PROF_CHAIN_GEMM, 18.0 * ns * (double)n * n * n * nt * 1e-9);
+  RS_TRY(cudaGraphLaunch(h->chain_graph, s));
+  launch_counter() += h->chain_graph_launches;
+  return cudaSuccess;
+}
+
+// Coefficients c(tau, i, j) of the trained network for the current G and Sigma_DD.
+constexpr int CV_CHUNK = 65536;
+
+size_t cv_work_floats(int batch) {
+  const int m = std::max(batch, 2048);
+  return std::max({sgemm_work_floats(CV_HIDDEN, CV_HIDDEN, m),
+                   sgemm_work_floats(CV_HIDDEN, CV_NFEAT, m), sgemm_work_floats(1, CV_HIDDEN, m),
+                   (size_t)1024});
+}
+
+cudaError_t cv_compute_c(rssri_handle *h, const double *G, const double *Gb) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, nt = h->n_tau;
+  const long long nn = (long long)n * n, total = nn * nt;
+  RS_TRY(ensure(h->cv_X, total * CV_NFEAT * sizeof(float)));
+  RS_TRY(ensure(h->cv_scr, (3 * nt + n + 1) * sizeof(double)));
+  RS_TRY(ensure(h->cv_c, total * sizeof(double)));
+  RS_TRY(ensure(h->cv_act, cv_act_floats(CV_CHUNK) * sizeof(float)));
+  RS_TRY(ensure(h->cv_work, cv_work_floats(CV_CHUNK) * sizeof(float)));
+  SPAN(RSSRI_PROF_OTHER, 0.0);
+  RS_TRY(cv_features(h->sdd.as<double>(), G, Gb, h->tau, h->beta, h->KP.as<double>(),
+                     h->rowptr.as<int>(), h->n_aux, n, nt, h->cv_scr.as<double>(),
+                     h->cv_X.as<float>(), s));
+  for (long long m0 = 0; m0 < total; m0 += CV_CHUNK) {
+    const int m = (int)std::min<long long>(CV_CHUNK, total - m0);
+    RS_TRY(cv_forward(h->cv_params.as<float>(), h->cv_X.as<float>() + m0 * CV_NFEAT, m,
+                      h->cv_act.as<float>(), h->cv_work.as<float>(), s));
+    RS_TRY(cv_coefficients(h->cv_act.as<float>() + 6LL * m * CV_HIDDEN, m,
+                           h->cv_c.as<double>() + m0, s));
+  }
+  return cudaSuccess;
+}
+
 int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const double *gb_in,
-              double *sigma, double *e_pair, double *e_corr, double *e_stderr, rssri_stats *st) {
+              double *sigma, double *e_pair, double *e_corr, double *e_stderr, rssri_stats *st,
+              bool collect_stats = false) {
   if (!h) return RSSRI_ERR_INVALID_ARG;
   if (h->broken) return RSSRI_ERR_CUDA;
   if (!h->ready) return RSSRI_ERR_NOT_READY;
   int rc = validate_options(o, true);
   if (rc) return rc;
-  if (!sigma) return RSSRI_ERR_INVALID_ARG;
+  if (!sigma && !collect_stats) return RSSRI_ERR_INVALID_ARG;
+  const bool use_cv = o->cv != 0;
+  if ((use_cv || collect_stats) &&
+      (o->precision != RSSRI_PREC_FP64 || o->estimator != RSSRI_EST_CV))
+    return RSSRI_ERR_INVALID_ARG;
+  if (use_cv && !h->cv_ready) return RSSRI_ERR_NOT_READY;
   if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
   cudaStream_t s = h->stream;
   const int n = h->n, na = h->n_aux, nt = h->n_tau;
@@ -603,6 +838,8 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   const int nb = (o->pair_batch > 0) ? (int)std::min<long long>(o->pair_batch, ns) : ns;
   const int has_l = sri ? 0 : 1;
   const int nbat2 = nb * (1 + has_l);
+  const bool bf16 = o->precision == RSSRI_PREC_BF16;
+  if (bf16 && (n < 16 || !tc_available())) return RSSRI_ERR_INVALID_ARG;
   cudaError_t e;
 #define RS_CK(x)                                       \
   do {                                                 \
@@ -631,10 +868,12 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   RS_CK(ensure(h->Ut, (size_t)2 * ns * na * sizeof(double)));
   RS_CK(ensure(h->fac, (size_t)4 * ns * nn * sizeof(double)));  // [set][kind][xi][n][n]
   RS_CK(ensure(h->RLp, (size_t)2 * ns * std::max(h->P, 1) * sizeof(double)));
-  RS_CK(ensure(h->XG, (size_t)nbat2 * nn * sizeof(double)));
-  RS_CK(ensure(h->Cc, (size_t)nbat2 * nn * sizeof(double)));
-  RS_CK(ensure(h->Bm, (size_t)nbat2 * nn * sizeof(double)));
-  RS_CK(ensure(h->BC, (size_t)nbat2 * nn * sizeof(double)));
+  if (!bf16) {
+    RS_CK(ensure(h->XG, (size_t)nbat2 * nn * sizeof(double)));
+    RS_CK(ensure(h->Cc, (size_t)nbat2 * nn * sizeof(double)));
+    RS_CK(ensure(h->Bm, (size_t)nbat2 * nn * sizeof(double)));
+    RS_CK(ensure(h->BC, (size_t)nbat2 * nn * sizeof(double)));
+  }
   RS_CK(ensure(h->tarr, nbat2 * sizeof(double)));
   RS_CK(ensure(h->sarr, nbat2 * sizeof(double)));
   RS_CK(ensure(h->e_st, ns * sizeof(double)));
@@ -647,6 +886,15 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     RS_CK(ensure(h->L, (size_t)P * na * sizeof(double)));
     RS_CK(ensure(h->Gam, (size_t)na * na * sizeof(double)));
     RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));
+    if (o->dd_arith == RSSRI_DD_DF64) {
+      RS_CK(ensure(h->Ahl, (size_t)nn * na * sizeof(float2)));
+      if (!h->d_df64_ready) {
+        RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
+        SPAN(RSSRI_PROF_OTHER, 0.0);
+        RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s));
+        h->d_df64_ready = true;
+      }
+    }
   }
   double *G = h->G.as<double>(), *Gb = h->Gb.as<double>();
 
@@ -663,7 +911,7 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   for (int t = 0; t < nt; ++t) {
     double *out = h->sdd.as<double>() + t * nn;
     if (sri) RS_CK(cudaMemsetAsync(out, 0, nn * sizeof(double), s));
-    else RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out));
+    else RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out, o->dd_arith == RSSRI_DD_DF64));
   }
   RS_CK(cudaEventRecord(h->ev[3], s));
 
@@ -704,12 +952,27 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
                           nn, nn, fac + (2LL * set + 1) * ns * nn, s)); }
   }
 
+  // ---- learned control variate: coefficients, or statistics for training
+  if (use_cv) {
+    RS_CK(cv_compute_c(h, G, Gb));
+    h->cv_c_ready = true;
+  }
+  if (collect_stats) {
+    RS_CK(ensure(h->cv_stats, (size_t)nt * 5 * nn * sizeof(double)));
+    RS_CK(cudaMemsetAsync(h->cv_stats.p, 0, (size_t)nt * 5 * nn * sizeof(double), s));
+  }
+
   // ---- S8: chains per tau and batch of sample pairs
   RS_CK(cudaMemsetAsync(h->e_st.p, 0, ns * sizeof(double), s));
   const double ne = 2.0 * h->n_occ;
   double *XG = h->XG.as<double>(), *Cc = h->Cc.as<double>(), *Bm = h->Bm.as<double>(),
          *BC = h->BC.as<double>();
-  for (int t = 0; t < nt; ++t) {
+  int *tc_err = h->flags.as<int>() + 4;
+  if (bf16) {
+    RS_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
+    RS_CK(chain_bf16(h, ns, G, Gb, h->sig_raw.as<double>(), tc_err));
+  }
+  for (int t = 0; t < nt && !bf16; ++t) {
     const double *Gt = G + t * nn, *Gbt = Gb + t * nn;
     double *sig = h->sig_raw.as<double>() + t * nn;
     for (int x0 = 0; x0 < ns; x0 += nb) {
@@ -740,26 +1003,49 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
         g.A = Bm; g.sA = nn; g.B = Cc; g.sB = nn; g.C = BC; g.sC = nn;  // (2tI - B) C
         RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
       }
-      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, has_l, n, (double)ns, h->sdd.as<double>() + t * nn,
-                             x0 == 0, sig, s)); }
-      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, has_l, h->h_tau_w[t], ne,
-                        h->e_st.as<double>() + x0, s)); }
+      if (collect_stats) {
+        SPAN(RSSRI_PROF_OTHER, 0.0);
+        RS_CK(cv_stats(BC, cnt, n, h->cv_stats.as<double>() + (long long)t * 5 * nn, s));
+      }
+      if (use_cv) {
+        SPAN(RSSRI_PROF_OTHER, 0.0);
+        const double *ct = h->cv_c.as<double>() + t * nn;
+        RS_CK(cv_accumulate(BC, cnt, n, (double)ns, h->sdd.as<double>() + t * nn, ct, x0 == 0,
+                            sig, s));
+        RS_CK(cv_pair_energy(BC, cnt, n, ct, Gbt, h->tarr.as<double>(), h->sarr.as<double>(),
+                             h->h_tau_w[t], ne, h->e_st.as<double>() + x0, s));
+      } else {
+        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, has_l, n, (double)ns, h->sdd.as<double>() + t * nn,
+                               x0 == 0, sig, s)); }
+        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, has_l, h->h_tau_w[t], ne,
+                          h->e_st.as<double>() + x0, s)); }
+      }
     }
   }
   // ---- S10 and S9
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(symmetrize(h->sig_raw.as<double>(), n, nt, h->sig_out.as<double>(), s)); }
-  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(trace_prod(h->sdd.as<double>(), Gb, n, nt, h->trdd.as<double>(), s)); }
+  if (use_cv) {
+    SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_CK(trace_prod_w(h->sdd.as<double>(), Gb, h->cv_c.as<double>(), n, nt,
+                       h->trdd.as<double>(), s));
+  } else {
+    SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_CK(trace_prod(h->sdd.as<double>(), Gb, n, nt, h->trdd.as<double>(), s));
+  }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(trace_prod(h->sig_out.as<double>(), Gb, n, nt, h->tr.as<double>(), s)); }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(energy_finalize(h->tau_w, h->trdd.as<double>(), h->tr.as<double>(), nt, ne,
                         h->e_st.as<double>(), ns, h->e_pair.as<double>(), h->res.as<double>(), s)); }
   const cudaMemcpyKind dk = h->ptr_kind == RSSRI_PTR_HOST ? cudaMemcpyDeviceToHost
                                                           : cudaMemcpyDeviceToDevice;
-  RS_CK(cudaMemcpyAsync(sigma, h->sig_out.p, nt * nn * sizeof(double), dk, s));
+  if (sigma) RS_CK(cudaMemcpyAsync(sigma, h->sig_out.p, nt * nn * sizeof(double), dk, s));
   if (e_pair) RS_CK(cudaMemcpyAsync(e_pair, h->e_pair.p, ns * sizeof(double), dk, s));
   RS_CK(cudaEventRecord(h->ev[4], s));
   double res[4];
+  int tc_flag = 0;
   RS_CK(cudaMemcpyAsync(res, h->res.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RS_CK(cudaMemcpyAsync(&tc_flag, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   RS_CK(cudaStreamSynchronize(s));
+  if (bf16 && tc_flag) return RSSRI_ERR_TIMEOUT;
   h->last_ns = ns;
   h->have_sigma = true;
   float t_dd = 0, t_samp = 0;
@@ -813,6 +1099,138 @@ int rssri_sigma_from_g(rssri_handle *h, const rssri_options *o, const double *g,
   return run_sigma(h, o, g, gb, sigma, e_pair, e_corr, e_stderr, st);
 }
 
+int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_params, int steps,
+                   int batch, float lr, double *loss_before, double *loss_after) {
+  if (!h || !o || !init_params || steps < 0 || batch < 1 || batch > CV_CHUNK || !(lr > 0.f))
+    return RSSRI_ERR_INVALID_ARG;
+  if (h->broken) return RSSRI_ERR_CUDA;
+  if (!h->ready) return RSSRI_ERR_NOT_READY;
+  rssri_options ot = *o;
+  ot.cv = 0;
+  int rc = run_sigma(h, &ot, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  const int n = h->n, nt = h->n_tau, ns = (int)o->n_s;
+  const long long nn = (long long)n * n, total = nn * nt;
+  const int E = (int)std::min<long long>(CV_CHUNK, total);
+  cudaError_t e = cudaSuccess;
+  auto ck = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  const size_t pb = CV_NPARAM * sizeof(float);
+  ck(ensure(h->cv_params, pb));
+  ck(ensure(h->cv_m, pb));
+  ck(ensure(h->cv_v, pb));
+  ck(ensure(h->cv_grad, pb));
+  ck(ensure(h->cv_X, total * CV_NFEAT * sizeof(float)));
+  ck(ensure(h->cv_t, total * sizeof(float)));
+  ck(ensure(h->cv_w, total * sizeof(float)));
+  ck(ensure(h->cv_scr, (3 * nt + n + 1) * sizeof(double)));
+  ck(ensure(h->cv_act, cv_act_floats(std::max(batch, E)) * sizeof(float)));
+  ck(ensure(h->cv_work, cv_work_floats(std::max(batch, E)) * sizeof(float)));
+  ck(ensure(h->cv_bx, (size_t)std::max(batch, E) * CV_NFEAT * sizeof(float)));
+  ck(ensure(h->cv_bt, (size_t)std::max(batch, E) * sizeof(float)));
+  ck(ensure(h->cv_bw, (size_t)std::max(batch, E) * sizeof(float)));
+  ck(ensure(h->cv_loss, 4 * sizeof(float)));
+  if (e != cudaSuccess) return map_err(e);
+  float *P = h->cv_params.as<float>(), *X = h->cv_X.as<float>(), *T = h->cv_t.as<float>(),
+        *Wt = h->cv_w.as<float>(), *act = h->cv_act.as<float>(), *work = h->cv_work.as<float>(),
+        *bx = h->cv_bx.as<float>(), *bt = h->cv_bt.as<float>(), *bw = h->cv_bw.as<float>(),
+        *grad = h->cv_grad.as<float>(), *loss = h->cv_loss.as<float>();
+  ck(cv_features(h->sdd.as<double>(), h->G.as<double>(), h->Gb.as<double>(), h->tau, h->beta,
+                 h->KP.as<double>(), h->rowptr.as<int>(), h->n_aux, n, nt,
+                 h->cv_scr.as<double>(), X, s));
+  ck(cv_targets(h->cv_stats.as<double>(), n, nt, ns, T, Wt, s));
+  ck(cudaMemcpyAsync(P, init_params, pb, cudaMemcpyHostToDevice, s));
+  ck(cudaMemsetAsync(h->cv_m.p, 0, pb, s));
+  ck(cudaMemsetAsync(h->cv_v.p, 0, pb, s));
+  // fixed evaluation set: the first E elements
+  auto eval = [&](double *out) {
+    ck(cv_forward(P, X, E, act, work, s));
+    ck(cv_backward(P, X, E, T, Wt, act, grad, loss, work, s));
+    float l = 0;
+    ck(cudaMemcpyAsync(&l, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    if (out) *out = l;
+  };
+  eval(loss_before);
+  // minibatches: elements (start + k stride) mod total, stride coprime to total
+  long long stride = 1000003 % total;
+  if (stride < 1) stride = 1;
+  auto gcd = [](long long a, long long b) {
+    while (b) {
+      const long long t2 = a % b;
+      a = b;
+      b = t2;
+    }
+    return a;
+  };
+  while (gcd(stride, total) != 1) ++stride;
+  for (int step = 1; step <= steps && e == cudaSuccess; ++step) {
+    const long long start = ((long long)(step - 1) * batch) % total;
+    ck(cv_gather(X, CV_NFEAT, total, start, stride, batch, bx, s));
+    ck(cv_gather(T, 1, total, start, stride, batch, bt, s));
+    ck(cv_gather(Wt, 1, total, start, stride, batch, bw, s));
+    ck(cv_forward(P, bx, batch, act, work, s));
+    ck(cv_backward(P, bx, batch, bt, bw, act, grad, nullptr, work, s));
+    ck(cv_adam(P, grad, h->cv_m.as<float>(), h->cv_v.as<float>(), (int)CV_NPARAM, lr, step, s));
+  }
+  eval(loss_after);
+  if (e != cudaSuccess) return map_err(e);
+  h->cv_ready = true;
+  return RSSRI_OK;
+}
+
+int rssri_cv_set_params(rssri_handle *h, const float *params) {
+  if (!h || !params) return RSSRI_ERR_INVALID_ARG;
+  if (h->broken) return RSSRI_ERR_CUDA;
+  if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  cudaError_t e = ensure(h->cv_params, CV_NPARAM * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->cv_params.p, params, CV_NPARAM * sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) h->cv_ready = true;
+  return map_err(e);
+}
+
+int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, const float *weight,
+                       int m, const float *params, float *loss, float *grad) {
+  if (!h || !x || !target || !weight || !params || !loss || !grad || m < 1 || m > CV_CHUNK)
+    return RSSRI_ERR_INVALID_ARG;
+  if (h->broken) return RSSRI_ERR_CUDA;
+  if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaSuccess;
+  auto ck = [&](cudaError_t v) {
+    if (e == cudaSuccess) e = v;
+  };
+  const size_t pb = CV_NPARAM * sizeof(float);
+  ck(ensure(h->cv_ptmp, pb));
+  ck(ensure(h->cv_grad, pb));
+  ck(ensure(h->cv_act, std::max(h->cv_act.bytes, cv_act_floats(m) * sizeof(float))));
+  ck(ensure(h->cv_work, std::max(h->cv_work.bytes, cv_work_floats(m) * sizeof(float))));
+  ck(ensure(h->cv_bx, std::max(h->cv_bx.bytes, (size_t)m * CV_NFEAT * sizeof(float))));
+  ck(ensure(h->cv_bt, std::max(h->cv_bt.bytes, (size_t)m * sizeof(float))));
+  ck(ensure(h->cv_bw, std::max(h->cv_bw.bytes, (size_t)m * sizeof(float))));
+  ck(ensure(h->cv_loss, 4 * sizeof(float)));
+  if (e != cudaSuccess) return map_err(e);
+  ck(cudaMemcpyAsync(h->cv_ptmp.p, params, pb, cudaMemcpyHostToDevice, s));
+  ck(cudaMemcpyAsync(h->cv_bx.p, x, (size_t)m * CV_NFEAT * sizeof(float), cudaMemcpyHostToDevice, s));
+  ck(cudaMemcpyAsync(h->cv_bt.p, target, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, s));
+  ck(cudaMemcpyAsync(h->cv_bw.p, weight, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, s));
+  ck(cv_forward(h->cv_ptmp.as<float>(), h->cv_bx.as<float>(), m, h->cv_act.as<float>(),
+                h->cv_work.as<float>(), s));
+  ck(cv_backward(h->cv_ptmp.as<float>(), h->cv_bx.as<float>(), m, h->cv_bt.as<float>(),
+                 h->cv_bw.as<float>(), h->cv_act.as<float>(), h->cv_grad.as<float>(),
+                 h->cv_loss.as<float>(), h->cv_work.as<float>(), s));
+  ck(cudaMemcpyAsync(loss, h->cv_loss.p, sizeof(float), cudaMemcpyDeviceToHost, s));
+  ck(cudaMemcpyAsync(grad, h->cv_grad.p, pb, cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+  return map_err(e);
+}
+
 int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
   if (!h || !bytes) return RSSRI_ERR_INVALID_ARG;
   *bytes = 0;
@@ -831,6 +1249,8 @@ int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
     case RSSRI_BUF_GB:
     case RSSRI_BUF_SIGMA_DD:
     case RSSRI_BUF_SIGMA_RAW: *bytes = h->have_sigma ? nt * nn * d : 0; break;
+    case RSSRI_BUF_CV_PARAMS: *bytes = h->cv_ready ? CV_NPARAM * sizeof(float) : 0; break;
+    case RSSRI_BUF_CV_C: *bytes = h->cv_c_ready ? nt * nn * d : 0; break;
     default: return RSSRI_ERR_INVALID_ARG;
   }
   return *bytes ? RSSRI_OK : RSSRI_ERR_NOT_READY;
@@ -889,6 +1309,8 @@ int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_ki
     case RSSRI_BUF_GB: copy(dst, h->Gb.p, bytes); break;
     case RSSRI_BUF_SIGMA_DD: copy(dst, h->sdd.p, bytes); break;
     case RSSRI_BUF_SIGMA_RAW: copy(dst, h->sig_raw.p, bytes); break;
+    case RSSRI_BUF_CV_PARAMS: copy(dst, h->cv_params.p, bytes); break;
+    case RSSRI_BUF_CV_C: copy(dst, h->cv_c.p, bytes); break;
     default: return RSSRI_ERR_INVALID_ARG;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

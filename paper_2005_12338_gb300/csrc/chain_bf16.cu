@@ -1,0 +1,242 @@
+// Element-wise kernels of the reduced-precision chain (S8 in bf16 on tensor
+// cores), in the range-separated split of Eqs. 14-15: with R = R^L + R^S,
+//   C^L = R^L G R'^L,  dC = R^S G R' + R^L G R'^S,  C = C^L + dC,
+//   X = dC Gb,  Y = C^L Gb,  dt = Tr X,  t^L = Tr Y,
+//   F(R,R') - F(R^L,R'^L) = (2 dt I - X) C + (2 t^L I - Y) dC,
+//   Tr[(F - F^L) Gb] = 2 dt (2 t^L + dt) - Tr(X X) - 2 Tr(X Y).
+// Only the small R^S terms ever appear on their own, so the bf16 rounding of
+// every operand costs a relative error of order 2^-8 of the stochastic
+// remainder, not of the full self-energy.  Traces and energies are summed in
+// fp64.
+#include <cuda_bf16.h>
+
+#include "chain_bf16.cuh"
+
+namespace rssri {
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ double block_sum_d(double v) {
+  __shared__ double sh[32];
+  __syncthreads();
+  v = warp_sum_d(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double x = (l < nw) ? sh[l] : 0.0;
+    x = warp_sum_d(x);
+    if (l == 0) sh[0] = x;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+int grid_cap(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+}
+
+// fac = [set][kind][x][n][n] fp64 (kind 0: R, kind 1: R^L)
+__global__ void bf16_factors_kernel(const double *__restrict__ fac, int ns, int n, int ldp,
+                                    __nv_bfloat16 *__restrict__ xsl, __nv_bfloat16 *__restrict__ y3) {
+  const long long nn = (long long)n * n, mat = (long long)n * ldp;
+  const long long total = (long long)ns * n * ldp;
+  const double *r0 = fac, *rl0 = fac + ns * nn, *r1 = fac + 2 * ns * nn, *rl1 = fac + 3 * ns * nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long x = e / mat, r = e - x * mat;
+    const int i = (int)(r / ldp), j = (int)(r - (long long)i * ldp);
+    double a = 0, al = 0, b = 0, bl = 0;
+    if (j < n) {
+      const long long src = x * nn + (long long)i * n + j;
+      a = r0[src];
+      al = rl0[src];
+      b = r1[src];
+      bl = rl1[src];
+    }
+    xsl[e] = __double2bfloat16(a - al);             // R^S
+    xsl[ns * mat + e] = __double2bfloat16(al);      // R^L
+    y3[e] = __double2bfloat16(b);                   // R'
+    y3[ns * mat + e] = __double2bfloat16(b - bl);   // R'^S
+    y3[2 * ns * mat + e] = __double2bfloat16(bl);   // R'^L
+  }
+}
+
+__global__ void bf16_matrices_kernel(const double *__restrict__ src, int cnt, int n, int ldp,
+                                     __nv_bfloat16 *__restrict__ dst) {
+  const long long mat = (long long)n * ldp, total = (long long)cnt * mat;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long x = e / mat, r = e - x * mat;
+    const int i = (int)(r / ldp), j = (int)(r - (long long)i * ldp);
+    dst[e] = __double2bfloat16(j < n ? src[x * n * n + (long long)i * n + j] : 0.0);
+  }
+}
+
+// The fold works on 32 x 32 tiles staged in shared memory, so that every
+// global read and write is coalesced (including the transposes), in two
+// passes over a grid of (tile row, sample pair) blocks of 256 threads:
+//  1. partial sums of Tr X, Tr Y, Tr(X X) = sum X_ij X_ji, Tr(X Y) = sum Y_ij X_ji
+//     per tile row;
+//  2. the operands 2 dt I - X, 2 t^L I - Y, (C^L + dC)^T and dC^T of that tile
+//     row, after summing the partials of pass 1 in a fixed order; the block of
+//     tile row 0 adds the pair energy.
+__global__ void __launch_bounds__(256) fold_traces_kernel(const float *__restrict__ xy, int ns,
+                                                          int n, double *__restrict__ part) {
+  __shared__ float ta[32][33], tb[32][33], tc[32][33];
+  const int bi = blockIdx.x, x = blockIdx.y, nt = gridDim.x;
+  const long long nn = (long long)n * n;
+  const float *X = xy + x * nn, *Y = xy + (ns + x) * nn;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double dx = 0, dy = 0, sxx = 0, sxy = 0;
+  if (ty == 0) {
+    const int i = bi * 32 + tx;
+    if (i < n) {
+      dx = X[(long long)i * n + i];
+      dy = Y[(long long)i * n + i];
+    }
+  }
+  for (int bj = 0; bj < nt; ++bj) {
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = bi * 32 + r, j = bj * 32 + tx;
+      const int i2 = bj * 32 + r, j2 = bi * 32 + tx;
+      const bool in1 = i < n && j < n, in2 = i2 < n && j2 < n;
+      ta[r][tx] = in1 ? X[(long long)i * n + j] : 0.f;
+      tc[r][tx] = in1 ? Y[(long long)i * n + j] : 0.f;
+      tb[r][tx] = in2 ? X[(long long)i2 * n + j2] : 0.f;  // block (bj, bi) of X
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const double xt = tb[tx][r];  // X_ji, i = bi*32 + r, j = bj*32 + tx
+      sxx += (double)ta[r][tx] * xt;
+      sxy += (double)tc[r][tx] * xt;
+    }
+  }
+  const double v0 = block_sum_d(dx), v1 = block_sum_d(dy), v2 = block_sum_d(sxx),
+               v3 = block_sum_d(sxy);
+  if (threadIdx.x == 0) {
+    double *o = part + ((long long)x * nt + bi) * 4;
+    o[0] = v0;
+    o[1] = v1;
+    o[2] = v2;
+    o[3] = v3;
+  }
+}
+
+__global__ void __launch_bounds__(256) fold_operands_kernel(
+    const float *__restrict__ xy, const float *__restrict__ dc, const float *__restrict__ cl, int ns,
+    int n, int ldp, const double *__restrict__ part, double w, double ne,
+    __nv_bfloat16 *__restrict__ a6, __nv_bfloat16 *__restrict__ ct, __nv_bfloat16 *__restrict__ dct,
+    double *__restrict__ e_st) {
+  __shared__ float ta[32][33], tb[32][33];
+  __shared__ double sums[4];
+  const int bi = blockIdx.x, x = blockIdx.y, nt = gridDim.x;
+  const long long nn = (long long)n * n, mat = (long long)n * ldp;
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int t = 0; t < nt; ++t) v += part[((long long)x * nt + t) * 4 + threadIdx.x];
+    sums[threadIdx.x] = v;
+  }
+  __syncthreads();
+  const double dt = sums[0], tl = sums[1];
+  const float *X = xy + x * nn, *Y = xy + (ns + x) * nn;
+  const float *DC = dc + x * nn, *CL = cl + x * nn;
+  __nv_bfloat16 *A = a6 + x * mat, *Ab = a6 + (ns + x) * mat;
+  __nv_bfloat16 *Ct = ct + x * mat, *Dt = dct + x * mat;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int ntp = (ldp + 31) / 32;
+  for (int bj = 0; bj < ntp; ++bj) {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = bi * 32 + r, j = bj * 32 + tx;
+      if (i < n && j < ldp) {
+        const long long o = (long long)i * ldp + j;
+        if (j < n) {
+          const long long s2 = (long long)i * n + j;
+          const double d = (i == j) ? 1.0 : 0.0;
+          A[o] = __double2bfloat16(2.0 * dt * d - (double)X[s2]);
+          Ab[o] = __double2bfloat16(2.0 * tl * d - (double)Y[s2]);
+        } else {
+          A[o] = Ab[o] = __double2bfloat16(0.0);
+        }
+      }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = bj * 32 + r, j = bi * 32 + tx;  // source (i, j) of C and dC
+      const bool in = i < n && j < n;
+      ta[r][tx] = in ? CL[(long long)i * n + j] + DC[(long long)i * n + j] : 0.f;
+      tb[r][tx] = in ? DC[(long long)i * n + j] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = bi * 32 + r, j = bj * 32 + tx;  // destination (i, j) = source (j, i)
+      if (i < n && j < ldp) {
+        const long long o = (long long)i * ldp + j;
+        Ct[o] = __float2bfloat16_rn(j < n ? ta[tx][r] : 0.f);
+        Dt[o] = __float2bfloat16_rn(j < n ? tb[tx][r] : 0.f);
+      }
+    }
+  }
+  if (bi == 0 && threadIdx.x == 0) {
+    const double de = 2.0 * dt * (2.0 * tl + dt) - sums[2] - 2.0 * sums[3];
+    e_st[x] += -w * de / ne;
+  }
+}
+
+__global__ void reduce_bf16_kernel(const float *__restrict__ part, int groups, long long nn,
+                                   const double *__restrict__ base, double ns,
+                                   double *__restrict__ sig) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int g = 0; g < groups; ++g) acc += (double)part[g * nn + e];
+    sig[e] = base[e] + acc / ns;
+  }
+}
+
+}  // namespace
+
+cudaError_t bf16_factors(const double *fac, int ns, int n, int ldp, __nv_bfloat16 *xsl,
+                         __nv_bfloat16 *y3, cudaStream_t s) {
+  bf16_factors_kernel<<<grid_cap((long long)ns * n * ldp, 256), 256, 0, s>>>(fac, ns, n, ldp, xsl,
+                                                                             y3);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t bf16_matrices(const double *src, int cnt, int n, int ldp, __nv_bfloat16 *dst,
+                          cudaStream_t s) {
+  bf16_matrices_kernel<<<grid_cap((long long)cnt * n * ldp, 256), 256, 0, s>>>(src, cnt, n, ldp,
+                                                                               dst);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t fold_bf16(const float *xy, const float *dc, const float *cl, int ns, int n, int ldp,
+                      double w, double ne, __nv_bfloat16 *a6, __nv_bfloat16 *ct,
+                      __nv_bfloat16 *dct, double *e_st, double *part, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, ns);
+  fold_traces_kernel<<<grid, 256, 0, s>>>(xy, ns, n, part);
+  ++launch_counter();
+  RS_TRY(cudaGetLastError());
+  fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne, a6, ct, dct,
+                                            e_st);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_bf16(const float *part, int groups, int n, const double *base, double ns,
+                        double *sig, cudaStream_t s) {
+  const long long nn = (long long)n * n;
+  reduce_bf16_kernel<<<grid_cap(nn, 256), 256, 0, s>>>(part, groups, nn, base, ns, sig);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+}  // namespace rssri

@@ -89,6 +89,36 @@ def make_system(n: int, n_occ: int, n_aux: int, n_tau: int, input_seed: int = 0,
                   mu=0.5 * (gap_lo + gap_hi), beta=beta, tau=tau, tau_w=tau_w)
 
 
+def mlp_init(seed: int = 0, zero_output: bool = True) -> np.ndarray:
+    """Initial parameters of the control-variate network as the flat float32
+    layout W0[256][10] b0[256] W1[256][256] b1 W2[256][256] b2 W3[1][256] b3[1]:
+    He-normal hidden weights, zero biases, and a zero output layer (so the
+    network starts at c = 1) unless zero_output is False."""
+    rng = np.random.default_rng(seed)
+    sizes = [10, 256, 256, 256, 1]
+    parts = []
+    for k in range(4):
+        w = rng.standard_normal((sizes[k + 1], sizes[k])) * np.sqrt(2.0 / sizes[k])
+        if k == 3 and zero_output:
+            w[:] = 0.0
+        parts += [w.ravel(), np.zeros(sizes[k + 1])]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_unflatten(flat: np.ndarray):
+    """The flat layout of mlp_init as [(W, b), ...] float64 arrays."""
+    sizes = [10, 256, 256, 256, 1]
+    out, o = [], 0
+    for k in range(4):
+        nw = sizes[k + 1] * sizes[k]
+        w = flat[o:o + nw].astype(np.float64).reshape(sizes[k + 1], sizes[k])
+        o += nw
+        b = flat[o:o + sizes[k + 1]].astype(np.float64)
+        o += sizes[k + 1]
+        out.append((w, b))
+    return out
+
+
 # The five workloads the method is exercised on (sizes only; eps is the K^L cut
 # of Eq. 13, eps_prime the (ij|A) screen of Eq. 11 at the paper's 0.02).
 CONFIGS = {

@@ -1,0 +1,112 @@
+"""The learned control variate on the GPU: gradients of its fitting loss
+against the oracle, the c-weighted estimator against the oracle, and the gain
+of training.  The network runs in fp32, so the estimator is compared with a
+tolerance that adds 1e-4 of the control-variate correction to the 1e-10 bar."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import cv
+from paper_2005_12338_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2005_12338_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def flat(grads):
+    return [np.concatenate([w.ravel(), b]) for w, b in grads]
+
+
+def test_loss_gradient_matches_oracle(B):
+    rng = np.random.default_rng(0)
+    p = synth.mlp_init(1, zero_output=False)
+    params = synth.mlp_unflatten(p)
+    m = 300
+    x = rng.standard_normal((m, cv.N_FEAT)).astype(np.float32)
+    t = (1.0 + 0.3 * rng.standard_normal(m)).astype(np.float32)
+    w = (rng.random(m) + 0.1).astype(np.float32)
+    h = B.Handle(0)
+    loss, grad = h.cv_loss_grad(x, t, w, p)
+    h.close()
+    lref, gref = cv.mlp_loss_grad(params, x.astype(np.float64), t.astype(np.float64),
+                                  w.astype(np.float64))
+    assert abs(loss - lref) < 1e-4 * abs(lref)
+    o = 0
+    for k, gk in enumerate(flat(gref)):
+        got = grad[o:o + gk.size]
+        o += gk.size
+        assert np.linalg.norm(got - gk) < 2e-3 * np.linalg.norm(gk), k
+
+
+def run(B, s, opts, params=None, train=None):
+    dev = [torch.from_numpy(a).cuda() for a in (s.eri3, s.metric, s.orb_e, s.orb_c, s.tau,
+                                                 s.tau_w)]
+    h = B.Handle(0)
+    h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=opts)
+    losses = None
+    if params is not None:
+        h.cv_set_params(params)
+    if train is not None:
+        losses = h.cv_train(*train)
+    sig = torch.empty((s.n_tau, s.n, s.n), dtype=torch.float64, device="cuda")
+    e, se, st = h.sigma(opts, sig)
+    out = dict(sigma=sig.cpu().numpy(), e=e, se=se, st=st, losses=losses)
+    if opts.cv:
+        out["c"] = h.export("CV_C").reshape(s.n_tau, s.n, s.n)
+    h.close()
+    return out
+
+
+def test_cv_estimator_against_oracle(B):
+    s = synth.make_system(40, 18, 100, 3, input_seed=3)
+    ns, seed, epsp, eps = 8, 5, 0.02, 0.1
+    p = synth.mlp_init(2, zero_output=False)
+    got = run(B, s, B.Handle.options(epsp, eps, ns, seed, cv=1), params=p)
+    w = O.metric_inv_sqrt(s.metric)
+    el, _, _ = O.screen(s.eri3, epsp)
+    kl, _ = O.large_factor(el, w, eps)
+    r0, rl0 = O.stochastic_factors(s.eri3, w, kl, O.rademacher(seed, 0, ns, s.n_aux))
+    r1, rl1 = O.stochastic_factors(s.eri3, w, kl, O.rademacher(seed, 1, ns, s.n_aux))
+    rn = np.sqrt((kl ** 2).sum(axis=(1, 2)))
+    net = synth.mlp_unflatten(p)
+    tr = []
+    for t in range(s.n_tau):
+        g, gb = O.green(s.orb_e, s.orb_c, s.n_occ, s.mu, s.tau[t])
+        sdd = O.sigma_from_factor(kl, g, gb)
+        f = np.array([O.factor_pair(r0[x], r1[x], g, gb)[0] for x in range(ns)])
+        fl = np.array([O.factor_pair(rl0[x], rl1[x], g, gb)[0] for x in range(ns)])
+        c = cv.mlp_forward(net, cv.features(sdd, g, gb, s.tau[t], s.beta, rn))[0]
+        c = c.reshape(s.n, s.n)
+        raw = cv.cv_sigma(f.sum(0), fl.sum(0), ns, sdd, c)
+        ref = 0.5 * (raw + raw.T)
+        corr = np.linalg.norm(fl.mean(0) - sdd)
+        assert np.abs(got["c"][t] - c).max() < 1e-4 * np.abs(c).max()
+        assert np.linalg.norm(got["sigma"][t] - ref) < 1e-10 * np.linalg.norm(ref) + 1e-4 * corr
+        tr.append(np.sum(ref * gb.T))
+    e_ref = -np.dot(s.tau_w, tr) / (2 * s.n_occ)
+    assert abs(got["e"] - e_ref) < 1e-6 * abs(e_ref)
+
+
+def test_training_reduces_the_variance_objective(B):
+    """Fit c on one run, apply it on an independent one: the weighted variance
+    objective falls, and the estimate stays consistent with the plain one."""
+    s = synth.make_system(48, 20, 120, 6, input_seed=4)
+    train_opts = B.Handle.options(0.02, 0.1, 96, 101)
+    eval_cv = B.Handle.options(0.02, 0.1, 96, 7, cv=1)
+    eval_plain = B.Handle.options(0.02, 0.1, 96, 7)
+    got = run(B, s, eval_cv, train=(train_opts, synth.mlp_init(0), 400, 2048, 1e-3))
+    before, after = got["losses"]
+    assert after < 0.9 * before, (before, after)
+    plain = run(B, s, eval_plain)
+    assert abs(got["e"] - plain["e"]) < 4 * (got["se"] ** 2 + plain["se"] ** 2) ** 0.5
+    print(f"cv fit loss {before:.4e} -> {after:.4e}; E stderr plain {plain['se']:.3e} "
+          f"learned {got['se']:.3e}")

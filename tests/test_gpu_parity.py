@@ -36,9 +36,10 @@ def rel(a, b):
 
 
 def run_gpu(B, s, eps_prime, eps, n_s, seed, host=False, estimator=0, xi_offset=0, pair_batch=0,
-            g=None, gb=None):
+            g=None, gb=None, dd_arith=0):
     h = B.Handle(0)
-    opts = B.Handle.options(eps_prime, eps, n_s, seed, xi_offset, estimator, pair_batch)
+    opts = B.Handle.options(eps_prime, eps, n_s, seed, xi_offset, estimator, pair_batch,
+                            dd_arith=dd_arith)
     arrs = [s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w]
     if host:
         sig = np.empty((s.n_tau, s.n, s.n))
@@ -115,6 +116,18 @@ def test_parity_all_steps(B, case):
     s = synth.make_system(*c["sys"], input_seed=1)
     ref = run_oracle(s, c["eps_prime"], c["eps"], c["n_s"], c["seed"])
     h, got = run_gpu(B, s, c["eps_prime"], c["eps"], c["n_s"], c["seed"])
+    compare_all(h, got, ref, s)
+    h.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_parity_double_float_deterministic_block(B, case):
+    """The exchange contraction in double-float (fp32 pairs) meets the same
+    1e-10 bar as the fp64 one."""
+    c = CASES[case]
+    s = synth.make_system(*c["sys"], input_seed=1)
+    ref = run_oracle(s, c["eps_prime"], c["eps"], c["n_s"], c["seed"])
+    h, got = run_gpu(B, s, c["eps_prime"], c["eps"], c["n_s"], c["seed"], dd_arith=1)
     compare_all(h, got, ref, s)
     h.close()
 
@@ -208,11 +221,11 @@ def test_errors_are_reported(B):
 
 
 # ---------------------------------------------------- the N = 200 workload ---
-@pytest.fixture(scope="module")
-def c2(B):
+@pytest.fixture(scope="module", params=[0, 1], ids=["dd_fp64", "dd_df64"])
+def c2(B, request):
     cfg = synth.CONFIGS["c2_n200"]
     s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
-    h, got = run_gpu(B, s, cfg["eps_prime"], cfg["eps"], cfg["n_s"], 0)
+    h, got = run_gpu(B, s, cfg["eps_prime"], cfg["eps"], cfg["n_s"], 0, dd_arith=request.param)
     yield cfg, s, h, got
     h.close()
 
