@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp64"],
-                    help="chain products: bf16 tensor cores (the chosen form) or fp64 (plain)")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp64"],
+                    help="chain products: bf16 tensor cores (the chosen form), tf32 tensor "
+                         "cores, or fp64 (plain)")
     ap.add_argument("--dd", default="df64", choices=["df64", "fp64"],
                     help="exchange contraction of the deterministic block: double-float on "
                          "the fp32 pipes (chosen) or IEEE fp64")
@@ -62,6 +63,9 @@ def parse():
     ap.add_argument("--cv", action="store_true",
                     help="also train the learned control variate on an independent run and "
                          "report its estimate (fp64 chain)")
+    ap.add_argument("--literal", action="store_true",
+                    help="also run the literal Eq. 25 estimator (fp64 chain, exact-D cross "
+                         "terms) on the first timed seed and report its cost and stderr")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -81,6 +85,19 @@ def measured_peaks():
             d = json.load(f)
         return d, "measured"
     return dict(FALLBACK_PEAKS), "fallback"
+
+
+def tensor_peak(peaks, precision):
+    """Dense tensor peak of the chain's operand type: the measured bf16 figure,
+    halved for tf32 (the nominal tf32 : bf16 ratio)."""
+    bf16 = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+    return bf16 / 2.0 if precision == "tf32" else bf16
+
+
+def tensor_peak_source(peak_src, precision):
+    if precision == "tf32":
+        return "bf16 dense tensor peak x 1/2 (nominal tf32 ratio), " + peak_src
+    return "bf16 dense tensor peak, " + peak_src
 
 
 # --------------------------------------------------------------- clocks ----
@@ -215,7 +232,8 @@ def time_to_target(results, ns, target):
     per_pair = float(np.mean([r[3] for r in results])) / 1e3 / ns
     sigma_pair = float(np.mean([r[1] for r in results])) * np.sqrt(ns)
     pairs = max(2.0, (sigma_pair / target) ** 2)
-    return {"seconds": fixed + per_pair * pairs, "fixed_s": fixed, "per_pair_s": per_pair,
+    return {"seconds": fixed + per_pair * pairs, "sampling_only_s": per_pair * pairs,
+            "fixed_s": fixed, "per_pair_s": per_pair,
             "pairs_needed": pairs, "sd_per_pair": sigma_pair, "target": target}
 
 
@@ -249,13 +267,14 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------- our arm -----
-def traffic_for(kernel_class):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+def traffic_for(key):
+    """Per-launch DRAM bytes of the dominant kernel (key: kernel class, with
+    "/df64" for the double-float deterministic block) from the committed ncu
     summary, or None if absent or taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path)).get(kernel_class)
+    d = json.load(open(path)).get(key)
     if not d:
         return None
     src = os.path.join(ROOT, "paper_2005_12338_gb300", "csrc", d["source"])
@@ -285,7 +304,9 @@ def our_arm(args):
     h = binding.Handle(local)
     stream = torch.cuda.current_stream(local)
 
-    prec = binding.RSSRI_PREC_BF16 if args.precision == "bf16" else binding.RSSRI_PREC_FP64
+    prec = {"bf16": binding.RSSRI_PREC_BF16, "tf32": binding.RSSRI_PREC_TF32,
+            "fp64": binding.RSSRI_PREC_FP64}[args.precision]
+    tensor_chain = args.precision in ("bf16", "tf32")
     dd = binding.RSSRI_DD_DF64 if args.dd == "df64" else binding.RSSRI_DD_FP64
 
     def step(seed, profile=0, precision=prec, dd_arith=dd, estimator=binding.RSSRI_EST_CV):
@@ -332,7 +353,7 @@ def our_arm(args):
     # the plain fp64 form on the same seed: throughput and the error of the chosen form
     compare = None
     plain = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=binding.RSSRI_DD_FP64)
-    if (args.precision == "bf16" or args.dd == "df64") and not args.no_fp64_compare:
+    if (tensor_chain or args.dd == "df64") and not args.no_fp64_compare:
         step(replicas.rank_seed(rank, 990_001), **plain)  # tunes the fp64 chain shapes
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -352,7 +373,7 @@ def our_arm(args):
                    "plain_fp64_sampling_ms_per_step": st64["t_sample_ms"],
                    "chosen_sampling_ms_per_step": float(np.mean([r[3] for r in results])),
                    "sampling_speedup": st64["t_sample_ms"] / float(np.mean([r[3] for r in results])),
-                   "bf16_vs_fp64_same_seed": {
+                   "chosen_vs_fp64_same_seed": {
                        "sigma_rel_fro": err_sigma,
                        "sigma_stochastic_part_rel_fro": err_st,
                        "e_corr_abs": abs(results[0][0] - e64),
@@ -388,6 +409,23 @@ def our_arm(args):
         cv_report = {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
                      "e_corr_plain": e_cv, "stderr_plain": se_cv, "e_corr_learned": e_l,
                      "stderr_learned": se_l, "stderr_ratio_plain_over_learned": se_cv / se_l}
+
+    # the literal reading of Eq. 25 on the same draws as the first timed step
+    literal_report = None
+    if args.literal:
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        e_lit, se_lit, st_lit = step(replicas.rank_seed(rank, 0),
+                                     precision=binding.RSSRI_PREC_FP64,
+                                     estimator=binding.RSSRI_EST_LITERAL)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        literal_report = {"e_corr_literal": e_lit, "stderr_literal": se_lit,
+                          "e_corr_cv": results[0][0], "stderr_cv": results[0][1],
+                          "stderr_ratio_literal_over_cv": se_lit / results[0][1],
+                          "ms_per_step": l0.elapsed_time(l1),
+                          "sampling_ms": st_lit["t_sample_ms"]}
 
     # end to end through the C ABI with host buffers (pinned), copies included
     e2e = None
@@ -428,26 +466,27 @@ def our_arm(args):
         peak = DF64_PEAK_TFLOPS
         psrc = ("derived: 152 SMs x 128 fp32 lanes x 2070 MHz / 12 fp32 instructions per "
                 "double-float multiply-add x 2 flop (fp64-equivalent)")
-    elif name == "chain_gemm" and args.precision == "bf16":
-        peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
-        psrc = "bf16 dense tensor peak, " + peak_src
+    elif name == "chain_gemm" and tensor_chain:
+        peak = tensor_peak(peaks, args.precision)
+        psrc = tensor_peak_source(peak_src, args.precision)
     else:
         peak = FP64_PEAK_TFLOPS
         psrc = "derived: 152 SMs x 2 fp64 FMA/clk/SM x 2 flop x 2070 MHz (fp64 DFMA pipe)"
-    roofline = {"bound": "tensor" if (name == "chain_gemm" and args.precision == "bf16") else "alu",
+    roofline = {"bound": "tensor" if (name == "chain_gemm" and tensor_chain) else "alu",
                 "kernel": name, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_for(name),
+                "traffic": traffic_for(name + ("/df64" if name in ("dd_spmm", "dd_gemm") and
+                                               args.dd == "df64" else "")),
                 "peak_source": psrc + "; HBM/bf16 peaks " + peak_src,
                 "gflop_per_launch": per_launch_gf, "launches": int(prof_l[dom]),
                 "share_of_step": float(prof_ms[dom] / max(prof_ms.sum(), 1e-9))}
     tensor = None
-    if args.precision == "bf16":
-        bf16_peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+    if tensor_chain:
+        tpk = tensor_peak(peaks, args.precision)
         tf = prof_gf[0] / (prof_ms[0] / 1e3) / 1e3
-        tensor = {"kernel": "chain_gemm (tcgen05 bf16)", "bound": "tensor", "achieved": tf,
-                  "peak": bf16_peak, "unit": "TFLOP/s", "frac": tf / bf16_peak,
-                  "peak_source": peak_src}
+        tensor = {"kernel": f"chain_gemm (tcgen05 {args.precision})", "bound": "tensor",
+                  "achieved": tf, "peak": tpk, "unit": "TFLOP/s", "frac": tf / tpk,
+                  "peak_source": tensor_peak_source(peak_src, args.precision)}
     classes = {binding.PROF_CLASSES[c]: {"ms_per_step": prof_ms[c] / args.steps,
                                          "gflop_per_step": prof_gf[c] / args.steps,
                                          "launches_per_step": int(prof_l[c]) // args.steps,
@@ -458,7 +497,7 @@ def our_arm(args):
             "value": value, "unit": "units/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": ("bf16+" if args.precision == "bf16" else "") +
+            "dtype": (args.precision + "+" if tensor_chain else "") +
                      ("df64+f64" if args.dd == "df64" else "f64"), "data": "synthetic",
             "config": {"workload": f"{args.workload}: N={n} n_occ={s.n_occ} N_aux={s.n_aux} "
                                    f"N_tau={nt} N_s={ns} eps={cfg['eps']} "
@@ -474,7 +513,8 @@ def our_arm(args):
                       "time_to_1mEh_s": time_to_target(results, ns, 1e-3),
                       "classes": classes, "tensor_roofline": tensor,
                       "chosen_vs_plain_fp64": compare, "rs_vs_sri_same_n_s": rs_vs_sri,
-                      "learned_control_variate": cv_report}}
+                      "learned_control_variate": cv_report,
+                      "literal_estimator": literal_report}}
     if not args.no_cpu_baseline and world == 1:
         cb = oracle_sample(s, cfg, 0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

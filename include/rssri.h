@@ -72,8 +72,14 @@ enum { RSSRI_PTR_DEVICE = 0, RSSRI_PTR_HOST = 1 };
  * D + <R R> - <R^L R^L>, and this form keeps D D exact while pairing sample
  * xi of theta with sample xi of theta'.
  * RSSRI_EST_SRI: [K]^L is taken as empty, which is the plain stochastic RI of
- * Eq. 10 (the eps -> 1 limit of Sec. II). */
-enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1 };
+ * Eq. 10 (the eps -> 1 limit of Sec. II).
+ * RSSRI_EST_LITERAL: Eq. 25 with the product of brackets expanded term by
+ * term, D exact inside every bracket: Sigma = Sigma_DD + Phi(D, S'_xi) +
+ * Phi(S_xi, D) + Phi(S_xi, S'_xi) averaged over xi, S_xi = R(x)R - R^L(x)R^L.
+ * The cross terms with D are built per sample from the pair-space v^L
+ * (exchange) and from [K]^L (direct), about 4 N_aux P + 8 P^2 flops per
+ * (pair, tau) unit on top of four chains; fp64 chain only. */
+enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1, RSSRI_EST_LITERAL = 2 };
 
 /* Arithmetic of the chain products of the stochastic part (S8).
  * RSSRI_PREC_FP64: every product in fp64 (the plain form).
@@ -83,8 +89,12 @@ enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1 };
  *   bf16 operands and fp32 accumulation on the tensor cores; V^{-1/2}, the
  *   deterministic block, traces and energies stay fp64.  Needs N >= 16 and a
  *   GPU with tcgen05 (sm_100 family); its error is of relative order 1e-3 of
- *   the stochastic remainder Sigma - Sigma_DD. */
-enum { RSSRI_PREC_FP64 = 0, RSSRI_PREC_BF16 = 1 };
+ *   the stochastic remainder Sigma - Sigma_DD.
+ * RSSRI_PREC_TF32: the same split with operands rounded to tf32 (10 stored
+ *   mantissa bits, kept in fp32 storage) and fp32 accumulation: about 8x
+ *   smaller operand rounding than bf16 at twice the operand bytes and half
+ *   the tensor-core rate. */
+enum { RSSRI_PREC_FP64 = 0, RSSRI_PREC_BF16 = 1, RSSRI_PREC_TF32 = 2 };
 
 typedef struct rssri_handle rssri_handle;
 
@@ -131,19 +141,23 @@ typedef struct {
  *              set, else +1 (SplitMix64: Steele, Lea and Flood, OOPSLA 2014).
  *   xi_offset  first sample index (resume: runs over [xi_offset, xi_offset+n_s)
  *              concatenate exactly), xi_offset + n_s < 2^40.
- *   estimator  RSSRI_EST_CV or RSSRI_EST_SRI.
- *   precision  RSSRI_PREC_FP64 or RSSRI_PREC_BF16 (chain products only).
+ *   estimator  RSSRI_EST_CV, RSSRI_EST_SRI or RSSRI_EST_LITERAL (the last
+ *              with precision RSSRI_PREC_FP64 and cv = 0).
+ *   precision  RSSRI_PREC_FP64, RSSRI_PREC_BF16 or RSSRI_PREC_TF32 (chain
+ *              products only).
  *   pair_batch sample pairs processed per group of launches (0 = all;
- *              fp64 chain only, the bf16 chain takes all pairs at once).
+ *              fp64 chain only, the tensor-core chains take all pairs at once).
  *   profile    1: time every kernel class with CUDA events on the handle's
  *              stream (rssri_stats.prof_*); 0: off.
  *   cv         1: weight the large-part control variate element-wise by the
  *              coefficients c_ij(tau) of the network trained by
  *              rssri_cv_train (fp64 chain and RSSRI_EST_CV only); 0: c = 1.
- *   dd_arith   arithmetic of the exchange contraction of the deterministic
- *              block: RSSRI_DD_FP64 (IEEE fp64 FMAs) or RSSRI_DD_DF64
- *              (double-float: each fp64 value as a pair of floats, error-free
- *              products and sums on the fp32 pipes, ~1e-13 relative). */
+ *   dd_arith   arithmetic of the deterministic block (its products and
+ *              exchange contraction): RSSRI_DD_FP64 (IEEE fp64 FMAs) or
+ *              RSSRI_DD_DF64 (double-float: each fp64 value as a pair of
+ *              floats, error-free products and sums on the fp32 pipes, ~1e-13
+ *              relative).  The value given to rssri_setup also sets how the
+ *              pair-space v^L is formed there. */
 typedef struct {
   double eps_prime, eps;
   int64_t n_s;

@@ -6,7 +6,7 @@
 #include <new>
 #include <vector>
 
-#include "chain_bf16.cuh"
+#include "chain_tc.cuh"
 #include "cv_mlp.cuh"
 #include "dd_df64.cuh"
 #include "kernels.cuh"
@@ -81,7 +81,9 @@ struct rssri_handle {
       cv_scr, cv_bx, cv_bt, cv_bw, cv_loss;
   bool cv_ready = false, cv_c_ready = false;
   // double-float copies for the exchange contraction
-  DevBuf Dhl, Ahl;
+  DevBuf Dhl, Ahl, KPhl, PGhl, APhl, Gamhl, GGhl;
+  // literal estimator: pair gathers / J, aux traces, pair form of the batch
+  DevBuf litMP, litT, litMhl;
   bool d_df64_ready = false;
   // bf16 chain buffers
   DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
@@ -189,8 +191,13 @@ int validate_options(const rssri_options *o, bool for_sigma) {
     if (o->n_s < 2 || o->n_s > (1LL << 30) || o->xi_offset < 0 ||
         o->xi_offset + o->n_s >= (1LL << 40))
       return RSSRI_ERR_INVALID_ARG;
-    if (o->estimator != RSSRI_EST_CV && o->estimator != RSSRI_EST_SRI) return RSSRI_ERR_INVALID_ARG;
-    if (o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_BF16)
+    if (o->estimator != RSSRI_EST_CV && o->estimator != RSSRI_EST_SRI &&
+        o->estimator != RSSRI_EST_LITERAL)
+      return RSSRI_ERR_INVALID_ARG;
+    if (o->estimator == RSSRI_EST_LITERAL && (o->precision != RSSRI_PREC_FP64 || o->cv != 0))
+      return RSSRI_ERR_INVALID_ARG;
+    if (o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_BF16 &&
+        o->precision != RSSRI_PREC_TF32)
       return RSSRI_ERR_INVALID_ARG;
     if (o->pair_batch < 0) return RSSRI_ERR_INVALID_ARG;
     if (o->dd_arith != RSSRI_DD_FP64 && o->dd_arith != RSSRI_DD_DF64) return RSSRI_ERR_INVALID_ARG;
@@ -228,15 +235,6 @@ cudaError_t gemm(rssri_handle *h, const GemmArgs &g) {
 cudaError_t gemm_p(rssri_handle *h, int cls, const GemmArgs &g) {
   SPAN(cls, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
   return gemm(h, g);
-}
-
-// The same in double-float arithmetic when `df64` (deterministic block).
-cudaError_t gemm_dd(rssri_handle *h, const GemmArgs &g, bool df64) {
-  if (!df64) return gemm_p(h, RSSRI_PROF_DD_GEMM, g);
-  SPAN(RSSRI_PROF_DD_GEMM, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
-  const size_t need = dgemm_work_elems(g) * sizeof(double);
-  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
-  return dgemm_df64(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
 }
 
 // ------------------------------------------------------------ S1: V^-1/2 --
@@ -364,7 +362,7 @@ void rssri_destroy(rssri_handle *h) {
                     &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
                     &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
                     &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
-                    &h->Ahl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
+                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
                     &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss};
   for (DevBuf *b : bufs) release(*b);
@@ -508,13 +506,31 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   if (P > 0) {
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_int(h->spairs.as<int>(), h->lidx.as<int>(), P, h->pij.as<int>(), s)); }
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_rows(h->KLs.as<double>(), h->lidx.as<int>(), P, na, h->KP.as<double>(), s)); }
-    // D[a][b] = sum_Q K_P[a][Q] K_P[b][Q] = v^L for the pair of pairs (Eq. 8 on [K]^L)
-    GemmArgs g;
-    g.M = P; g.N = P; g.K = na;
-    g.A = h->KP.as<double>(); g.lda = na;
-    g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1;
-    g.C = h->D.as<double>(); g.ldc = P;
-    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    // D[a][b] = sum_Q K_P[a][Q] K_P[b][Q] = v^L for the pair of pairs (Eq. 8 on [K]^L),
+    // in the arithmetic the deterministic block is asked to use
+    if (o->dd_arith == RSSRI_DD_DF64) {
+      RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
+      RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s)); }
+      {
+        SPAN(RSSRI_PROF_SETUP_GEMM, 2.0 * P * (double)P * na * 1e-9);
+        DfGemm g;
+        g.M = P; g.N = P; g.K = na;
+        g.A = h->KPhl.as<float2>(); g.lda = na;
+        g.B = h->KPhl.as<float2>(); g.ldb = na; g.transB = 1;
+        g.C64 = h->D.as<double>(); g.ldc = P;
+        RS_CK(df_gemm(g, nullptr, 0, s));
+      }
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s)); }
+      h->d_df64_ready = true;
+    } else {
+      GemmArgs g;
+      g.M = P; g.N = P; g.K = na;
+      g.A = h->KP.as<double>(); g.lda = na;
+      g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1;
+      g.C = h->D.as<double>(); g.ldc = P;
+      RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    }
   }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_csr(h->pij.as<int>(), P, n, h->rowptr.as<int>(), h->prow.as<int>(),
                  h->pcol.as<int>(), s)); }
@@ -559,8 +575,7 @@ cudaError_t build_green(rssri_handle *h) {
 // K = [K]^L.  With PG^Q = K^Q G, At^Q = Gb K^Q G, Gamma_QQ' = Tr(K^Q G K^Q' Gb),
 // L^Q = sum_Q' Gamma_QQ' K^Q' and T^Q = sum_Q' K^Q' At^Q K^Q' (built in pair
 // space from D = v^L):  Sigma_DD = sum_Q K^Q G (2 L^Q - T^Q).
-cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, double *out,
-                         bool df64) {
+cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, double *out) {
   cudaStream_t s = h->stream;
   const int n = h->n, na = h->n_aux, P = h->P;
   const long long nn = (long long)n * n;
@@ -576,21 +591,11 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = Gb; g.lda = n;
     g.B = PG; g.ldb = (long long)n * na;
     g.C = At; g.ldc = (long long)n * na;
-    RS_TRY(gemm_dd(h, g, df64));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // T[m][Q][j] = sum_{a in row m, b in row j} D[a][b] At[(col a, col b)][Q]
-  if (df64) {
-    {
-      SPAN(RSSRI_PROF_OTHER, 0.0);
-      RS_TRY(to_df64(At, nn * na, h->Ahl.as<float2>(), s));
-    }
-    SPAN(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9);
-    RS_TRY(dd_exchange_spmm_df64(h->rowptr.as<int>(), h->pcol.as<int>(), h->Dhl.as<float2>(), P,
-                                 h->Ahl.as<float2>(), n, na, T, s));
-  } else {
   { SPAN(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9); RS_TRY(dd_exchange_spmm(h->rowptr.as<int>(), h->pcol.as<int>(), h->D.as<double>(), P, At, n, na,
                           T, s)); }
-  }
   // Gamma = K_P^T At_P, At_P the rows of At at the kept pairs
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
   {
@@ -599,7 +604,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = h->KP.as<double>(); g.lda = na; g.transA = 1;
     g.B = h->AP.as<double>(); g.ldb = na;
     g.C = h->Gam.as<double>(); g.ldc = na;
-    RS_TRY(gemm_dd(h, g, df64));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
   {
@@ -608,7 +613,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.A = h->KP.as<double>(); g.lda = na;
     g.B = h->Gam.as<double>(); g.ldb = na; g.transB = 1;
     g.C = h->L.as<double>(); g.ldc = na;
-    RS_TRY(gemm_dd(h, g, df64));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s)); }
   // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n]
@@ -619,7 +624,84 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     g.B = T; g.ldb = n;
     g.C = out; g.ldc = n;
     g.alpha = -1.0;
-    RS_TRY(gemm_dd(h, g, df64));
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  return cudaSuccess;
+}
+
+// A double-float product counted under the deterministic-block GEMM class.
+cudaError_t df_gemm_p(rssri_handle *h, const DfGemm &g) {
+  SPAN(RSSRI_PROF_DD_GEMM, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
+  const size_t need = df_gemm_work(g) * sizeof(double);
+  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
+  return df_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
+}
+
+// The same block in double-float arithmetic (fp32 pairs, fp64 totals every 256
+// terms).  Operands are split into (hi, lo) pairs once: D and K_P at setup, G
+// and Gb for all tau before the loop (Ghl, Gbhl), PG and At by the products
+// that form them, Gamma and T after their fp64 reductions.
+cudaError_t sigma_dd_tau_df64(rssri_handle *h, const float2 *Ghl, const float2 *Gbhl,
+                              double *out) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, P = h->P;
+  const long long nn = (long long)n * n;
+  if (P == 0) return cudaMemsetAsync(out, 0, nn * sizeof(double), s);
+  float2 *PGhl = h->PGhl.as<float2>(), *Ahl = h->Ahl.as<float2>();
+  const float2 *KPhl = h->KPhl.as<float2>();
+  double *T = h->T.as<double>();
+  // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]
+  { SPAN(RSSRI_PROF_DD_GEMM, 2.0 * n * (double)na * P * 1e-9);
+    RS_TRY(df_gemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), Ghl, n, KPhl, na,
+                             PGhl, na, (long long)n * na, s)); }
+  // At[k][(l,Q)] = sum_m Gb[k][m] PG[m][(l,Q)], written as pairs
+  {
+    DfGemm g;
+    g.M = n; g.N = n * na; g.K = n;
+    g.A = Gbhl; g.lda = n;
+    g.B = PGhl; g.ldb = (long long)n * na;
+    g.C2 = Ahl; g.ldc = (long long)n * na;
+    RS_TRY(df_gemm_p(h, g));
+  }
+  // T[m][Q][j] = sum_{a in row m, b in row j} D[a][b] At[(col a, col b)][Q]
+  { SPAN(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9);
+    RS_TRY(dd_exchange_spmm_df64(h->rowptr.as<int>(), h->pcol.as<int>(), h->Dhl.as<float2>(), P,
+                                 Ahl, n, na, T, s)); }
+  // Gamma = K_P^T At_P, At_P the rows of At at the kept pairs
+  { SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_TRY(gather_rows_f2(Ahl, h->pij.as<int>(), P, na, h->APhl.as<float2>(), s)); }
+  {
+    DfGemm g;
+    g.M = na; g.N = na; g.K = P;
+    g.A = KPhl; g.lda = na; g.transA = 1;
+    g.B = h->APhl.as<float2>(); g.ldb = na;
+    g.C64 = h->Gam.as<double>(); g.ldc = na;
+    RS_TRY(df_gemm_p(h, g));
+  }
+  { SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_TRY(to_df64(h->Gam.as<double>(), (long long)na * na, h->Gamhl.as<float2>(), s)); }
+  // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
+  {
+    DfGemm g;
+    g.M = P; g.N = na; g.K = na;
+    g.A = KPhl; g.lda = na;
+    g.B = h->Gamhl.as<float2>(); g.ldb = na; g.transB = 1;
+    g.C64 = h->L.as<double>(); g.ldc = na;
+    RS_TRY(df_gemm_p(h, g));
+  }
+  { SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s));
+    // At is no longer needed: its pair buffer takes T
+    RS_TRY(to_df64(T, nn * na, Ahl, s)); }
+  // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n]
+  {
+    DfGemm g;
+    g.M = n; g.N = n; g.K = n * na;
+    g.A = PGhl; g.lda = (long long)n * na;
+    g.B = Ahl; g.ldb = n;
+    g.C64 = out; g.ldc = n;
+    g.alpha = -1.0;
+    RS_TRY(df_gemm_p(h, g));
   }
   return cudaSuccess;
 }
@@ -635,7 +717,8 @@ size_t dd_work_need(rssri_handle *h) {
   return w;
 }
 
-// S8 in bf16 on the tensor cores, all sample pairs at once, for every tau:
+// S8 on the tensor cores (bf16 or tf32 operands, fp32 accumulation), all
+// sample pairs at once, for every tau:
 //   P = [R^S; R^L] G,  dC = P_S R' + P_L R'^S,  C^L = P_L R'^L,
 //   [X; Y] = [dC; C^L] Gb,  fold (traces, energy, 2 dt I - X, 2 t^L I - Y, C^T, dC^T),
 //   sum_x (2 dt I - X) C + (2 t^L I - Y) dC  (one contraction over the pairs).
@@ -643,22 +726,26 @@ size_t dd_work_need(rssri_handle *h) {
 // The launches are issued into a CUDA graph once and the graph is replayed
 // while the shapes, buffers and tau weights stay the same.
 struct ChainBufs {
-  __nv_bfloat16 *xsl, *y3, *gh, *gbh, *P, *dcl16, *a6, *ct, *dct;
+  int kind;  // TcKind of the operands
+  size_t es;  // operand element size
+  void *xsl, *y3, *gh, *gbh, *P, *dcl, *a6, *ct, *dct;
   float *dc32, *cl32, *xy32, *part;
   double *fold;
   int bpc, groups;
 };
 
-cudaError_t issue_chain_bf16(rssri_handle *h, cudaStream_t s, int ns, const double *G,
-                             const double *Gb, double *sig, int *err, const ChainBufs &b) {
+cudaError_t issue_chain_tc(rssri_handle *h, cudaStream_t s, int ns, const double *G,
+                           const double *Gb, double *sig, int *err, const ChainBufs &b) {
   const int n = h->n, nt = h->n_tau;
   const int ldp = (n + 7) / 8 * 8;
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
-  RS_TRY(bf16_factors(h->fac.as<double>(), ns, n, ldp, b.xsl, b.y3, s));
-  RS_TRY(bf16_matrices(G, nt, n, ldp, b.gh, s));
-  RS_TRY(bf16_matrices(Gb, nt, n, ldp, b.gbh, s));
+  RS_TRY(chain_factors(b.kind, h->fac.as<double>(), ns, n, ldp, b.xsl, b.y3, s));
+  RS_TRY(chain_matrices(b.kind, G, nt, n, ldp, b.gh, s));
+  RS_TRY(chain_matrices(b.kind, Gb, nt, n, ldp, b.gbh, s));
   const double ne = 2.0 * h->n_occ;
-  auto op = [&](const __nv_bfloat16 *p, long long sb, int rows) {
+  // element offset e into operand buffer p
+  auto at = [&](void *p, long long e) { return static_cast<void *>(static_cast<char *>(p) + e * b.es); };
+  auto op = [&](void *p, long long sb, int rows) {
     TcOperand t;
     t.ptr = p;
     t.ld = ldp;
@@ -667,60 +754,67 @@ cudaError_t issue_chain_bf16(rssri_handle *h, cudaStream_t s, int ns, const doub
     return t;
   };
   for (int t = 0; t < nt; ++t) {
-    const __nv_bfloat16 *gt = b.gh + t * mat, *gbt = b.gbh + t * mat;
+    void *gt = at(b.gh, t * mat), *gbt = at(b.gbh, t * mat);
     {  // P = [R^S; R^L] G (stacked rows of all pairs)
       TcGemm g;
+      g.kind = b.kind;
       g.M = 2 * ns * n; g.N = n; g.K[0] = n;
       g.A[0] = op(b.xsl, 0, 2 * ns * n); g.B[0] = op(gt, 0, n);
-      g.c16 = b.P; g.ldc16 = ldp; g.err = err;
+      g.cop = b.P; g.ldcop = ldp; g.err = err;
       RS_TRY(tc_gemm(g, s));
     }
     {  // dC = P_S R' + P_L R'^S
       TcGemm g;
+      g.kind = b.kind;
       g.M = n; g.N = n; g.batch = ns; g.nseg = 2; g.K[0] = g.K[1] = n;
       g.A[0] = op(b.P, mat, n); g.B[0] = op(b.y3, mat, n);
-      g.A[1] = op(b.P + ns * mat, mat, n); g.B[1] = op(b.y3 + ns * mat, mat, n);
-      g.c32 = b.dc32; g.c16 = b.dcl16; g.ldc16 = ldp; g.err = err;
+      g.A[1] = op(at(b.P, ns * mat), mat, n); g.B[1] = op(at(b.y3, ns * mat), mat, n);
+      g.c32 = b.dc32; g.cop = b.dcl; g.ldcop = ldp; g.err = err;
       RS_TRY(tc_gemm(g, s));
     }
     {  // C^L = P_L R'^L
       TcGemm g;
+      g.kind = b.kind;
       g.M = n; g.N = n; g.batch = ns; g.K[0] = n;
-      g.A[0] = op(b.P + ns * mat, mat, n); g.B[0] = op(b.y3 + 2 * ns * mat, mat, n);
-      g.c32 = b.cl32; g.c16 = b.dcl16 + ns * mat; g.ldc16 = ldp; g.err = err;
+      g.A[0] = op(at(b.P, ns * mat), mat, n); g.B[0] = op(at(b.y3, 2 * ns * mat), mat, n);
+      g.c32 = b.cl32; g.cop = at(b.dcl, ns * mat); g.ldcop = ldp; g.err = err;
       RS_TRY(tc_gemm(g, s));
     }
     {  // [X; Y] = [dC; C^L] Gb
       TcGemm g;
+      g.kind = b.kind;
       g.M = 2 * ns * n; g.N = n; g.K[0] = n;
-      g.A[0] = op(b.dcl16, 0, 2 * ns * n); g.B[0] = op(gbt, 0, n);
+      g.A[0] = op(b.dcl, 0, 2 * ns * n); g.B[0] = op(gbt, 0, n);
       g.c32 = b.xy32; g.err = err;
       RS_TRY(tc_gemm(g, s));
     }
-    RS_TRY(fold_bf16(b.xy32, b.dc32, b.cl32, ns, n, ldp, h->h_tau_w[t], ne, b.a6, b.ct, b.dct,
-                     h->e_st.as<double>(), b.fold, s));
+    RS_TRY(fold_tc(b.kind, b.xy32, b.dc32, b.cl32, ns, n, ldp, h->h_tau_w[t], ne, b.a6, b.ct,
+                   b.dct, h->e_st.as<double>(), b.fold, s));
     {  // sum over pairs of (2 dt I - X) C + (2 t^L I - Y) dC
       TcGemm g;
+      g.kind = b.kind;
       g.M = n; g.N = n; g.batch = ns; g.bpc = b.bpc; g.nseg = 2; g.K[0] = g.K[1] = n;
       g.A[0] = op(b.a6, mat, n); g.B[0] = op(b.ct, mat, n);
-      g.A[1] = op(b.a6 + ns * mat, mat, n); g.B[1] = op(b.dct, mat, n);
+      g.A[1] = op(at(b.a6, ns * mat), mat, n); g.B[1] = op(b.dct, mat, n);
       g.c32 = b.part; g.err = err;
       RS_TRY(tc_gemm(g, s));
     }
-    RS_TRY(reduce_bf16(b.part, b.groups, n, h->sdd.as<double>() + t * nn, (double)ns,
+    RS_TRY(reduce_tc(b.part, b.groups, n, h->sdd.as<double>() + t * nn, (double)ns,
                        sig + t * nn, s));
   }
   return cudaSuccess;
 }
 
-cudaError_t chain_bf16(rssri_handle *h, int ns, const double *G, const double *Gb, double *sig,
-                       int *err) {
+cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const double *Gb,
+                     double *sig, int *err) {
   cudaStream_t s = h->stream;
   const int n = h->n, nt = h->n_tau;
   const int ldp = (n + 7) / 8 * 8;
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
-  const size_t b16 = sizeof(__nv_bfloat16);
   ChainBufs b;
+  b.kind = kind;
+  b.es = kind == TC_BF16 ? sizeof(__nv_bfloat16) : sizeof(float);
+  const size_t b16 = b.es;
   b.bpc = std::max(1, ceil_div(ns, 152));
   b.groups = ceil_div(ns, b.bpc);
   RS_TRY(ensure(h->hxsl, 2 * ns * mat * b16));
@@ -737,15 +831,14 @@ cudaError_t chain_bf16(rssri_handle *h, int ns, const double *G, const double *G
   RS_TRY(ensure(h->hdct, ns * mat * b16));
   RS_TRY(ensure(h->hpart, b.groups * nn * sizeof(float)));
   RS_TRY(ensure(h->hfold, (size_t)ns * ceil_div(n, 32) * 4 * sizeof(double)));
-  auto bf = [](DevBuf &x) { return x.as<__nv_bfloat16>(); };
-  b.xsl = bf(h->hxsl); b.y3 = bf(h->hy3); b.gh = bf(h->hg); b.gbh = bf(h->hgb); b.P = bf(h->hP);
-  b.dcl16 = bf(h->hdcl16); b.a6 = bf(h->ha6); b.ct = bf(h->hct); b.dct = bf(h->hdct);
+  b.xsl = h->hxsl.p; b.y3 = h->hy3.p; b.gh = h->hg.p; b.gbh = h->hgb.p; b.P = h->hP.p;
+  b.dcl = h->hdcl16.p; b.a6 = h->ha6.p; b.ct = h->hct.p; b.dct = h->hdct.p;
   b.dc32 = h->hdc32.as<float>(); b.cl32 = h->hcl32.as<float>(); b.xy32 = h->hxy32.as<float>();
   b.part = h->hpart.as<float>();
   b.fold = h->hfold.as<double>();
   RS_TRY(tc_prepare());
   // the graph is keyed on every pointer and value baked into its launches
-  std::vector<uintptr_t> key = {(uintptr_t)ns, (uintptr_t)n, (uintptr_t)nt, (uintptr_t)h->n_occ,
+  std::vector<uintptr_t> key = {(uintptr_t)kind, (uintptr_t)ns, (uintptr_t)n, (uintptr_t)nt, (uintptr_t)h->n_occ,
                                 (uintptr_t)G, (uintptr_t)Gb, (uintptr_t)sig, (uintptr_t)err,
                                 (uintptr_t)h->fac.p, (uintptr_t)h->e_st.p, (uintptr_t)h->sdd.p};
   for (DevBuf *d : {&h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32, &h->hdcl16,
@@ -758,7 +851,7 @@ cudaError_t chain_bf16(rssri_handle *h, int ns, const double *G, const double *G
     if (!h->cap_stream) RS_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     RS_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     const long long l0 = launch_counter();
-    const cudaError_t ei = issue_chain_bf16(h, h->cap_stream, ns, G, Gb, sig, err, b);
+    const cudaError_t ei = issue_chain_tc(h, h->cap_stream, ns, G, Gb, sig, err, b);
     const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
     const long long captured = launch_counter() - l0;
     launch_counter() = l0;  // captured, not yet run
@@ -814,6 +907,107 @@ cudaError_t cv_compute_c(rssri_handle *h, const double *G, const double *Gb) {
   return cudaSuccess;
 }
 
+// The cross terms of the literal estimator (Eq. 25 with D exact inside each
+// bracket) for one tau and one batch of cnt sample pairs.  Phi is bilinear,
+// so Phi(D, S') + Phi(S, D) = sum_{y = R', R'^L} (+-) sum_Q F(K^Q, y) +
+// sum_{x = R, R^L} (+-) sum_Q F(x, K^Q) with K^Q = [K^Q]^L, and
+//   sum_Q F(K^Q, y) = (2 J_y - X_y) G y,   M_y = G y Gb,
+//   sum_Q F(x, K^Q) = x G (2 J'_x - X'_x), M'_x = Gb x G,
+// where for a matrix M: J = sum_Q Tr(K^Q M) K^Q (direct; K^Q symmetric, so
+// Tr(K^Q M) = sum over kept pairs of K_P M) and X = sum_Q K^Q M K^Q, the
+// exchange build X_mj = sum_{a in row m, b in row j} v^L_ab M[col a][col b]
+// in pair space (the same contraction as the deterministic block's with the
+// aux index replaced by the batch of matrices).  The four sides are batched
+// as s = side * cnt + x; the result is added to the first chain slot of BC
+// and to the pair energies.  XG, Cc, Bm are free scratch here.
+cudaError_t literal_cross(rssri_handle *h, const rssri_options *o, int t, int x0, int cnt,
+                          const double *Gt, const double *Gbt, double *XG, double *Cc, double *Bm,
+                          double *BC) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, ns = (int)o->n_s, P = h->P;
+  const long long nn = (long long)n * n;
+  const int S = 4 * cnt;
+  const double *fac = h->fac.as<double>();
+  auto factor = [&](int set, int kind) { return fac + ((2LL * set + kind) * ns + x0) * nn; };
+  // sides: 0 = y R' (+), 1 = y R'^L (-), 2 = x R (+), 3 = x R^L (-)
+  double *M = Cc, *tmp = XG;
+  for (int side = 0; side < 4; ++side) {
+    const bool yside = side < 2;
+    const double *F = yside ? factor(1, side) : factor(0, side - 2);
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = n; g.batch = cnt;
+    g.lda = g.ldb = g.ldc = n;
+    double *tm = tmp + (long long)side * cnt * nn, *mm = M + (long long)side * cnt * nn;
+    // y side: M = G y Gb; x side: M = Gb x G
+    g.A = yside ? Gt : Gbt; g.sA = 0; g.B = F; g.sB = nn; g.C = tm; g.sC = nn;
+    RS_TRY(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
+    g.A = tm; g.sA = nn; g.B = yside ? Gbt : Gt; g.sB = 0; g.C = mm; g.sC = nn;
+    RS_TRY(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
+  }
+  double *Mt = Bm;  // [k][l][s]
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(lit_qfast(M, S, nn, Mt, s)); }
+  // direct: tQ = K_P^T M_P, J_P = K_P tQ
+  double *MP = h->litMP.as<double>(), *tQ = h->litT.as<double>();
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(Mt, h->pij.as<int>(), P, S, MP, s)); }
+  {
+    GemmArgs g;
+    g.M = na; g.N = S; g.K = P;
+    g.A = h->KP.as<double>(); g.lda = na; g.transA = 1;
+    g.B = MP; g.ldb = S;
+    g.C = tQ; g.ldc = S;
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  {
+    GemmArgs g;
+    g.M = P; g.N = S; g.K = na;
+    g.A = h->KP.as<double>(); g.lda = na;
+    g.B = tQ; g.ldb = S;
+    g.C = MP; g.ldc = S;  // J_P overwrites the gathered M_P
+    RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  // exchange: Tk[m][s][j] = sum_{a in row m, b in row j} D[a][b] Mt[(col a, col b)][s]
+  double *Tk = XG;
+  {
+    SPAN(RSSRI_PROF_DD_SPMM, 2.0 * S * (double)P * P * 1e-9);
+    if (o->dd_arith == RSSRI_DD_DF64) {
+      RS_TRY(to_df64(Mt, S * nn, h->litMhl.as<float2>(), s));
+      RS_TRY(dd_exchange_spmm_df64(h->rowptr.as<int>(), h->pcol.as<int>(), h->Dhl.as<float2>(), P,
+                                   h->litMhl.as<float2>(), n, S, Tk, s));
+    } else {
+      RS_TRY(dd_exchange_spmm(h->rowptr.as<int>(), h->pcol.as<int>(), h->D.as<double>(), P, Mt, n,
+                              S, Tk, s));
+    }
+  }
+  // W[s] = 2 J_s - X_s
+  double *W = Cc;
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(lit_w(Tk, S, n, MP, h->pij.as<int>(), P, W, s)); }
+  // Z: y side (W G) y, x side (x G) W
+  double *Z = XG;
+  for (int side = 0; side < 4; ++side) {
+    const bool yside = side < 2;
+    const double *F = yside ? factor(1, side) : factor(0, side - 2);
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = n; g.batch = cnt;
+    g.lda = g.ldb = g.ldc = n;
+    double *tm = Bm + (long long)side * cnt * nn, *zz = Z + (long long)side * cnt * nn;
+    const double *ww = W + (long long)side * cnt * nn;
+    if (yside) {
+      g.A = ww; g.sA = nn; g.B = Gt; g.sB = 0; g.C = tm; g.sC = nn;
+      RS_TRY(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
+      g.A = tm; g.sA = nn; g.B = F; g.sB = nn; g.C = zz; g.sC = nn;
+      RS_TRY(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
+    } else {
+      g.A = F; g.sA = nn; g.B = Gt; g.sB = 0; g.C = tm; g.sC = nn;
+      RS_TRY(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
+      g.A = tm; g.sA = nn; g.B = ww; g.sB = nn; g.C = zz; g.sC = nn;
+      RS_TRY(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
+    }
+  }
+  SPAN(RSSRI_PROF_OTHER, 0.0);
+  return lit_add(Z, cnt, n, Gbt, h->h_tau_w[t], 2.0 * h->n_occ, BC,
+                 h->e_st.as<double>() + x0, s);
+}
+
 int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const double *gb_in,
               double *sigma, double *e_pair, double *e_corr, double *e_stderr, rssri_stats *st,
               bool collect_stats = false) {
@@ -834,11 +1028,17 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   const int ns = (int)o->n_s;
   const long long nn = (long long)n * n;
   const bool sri = o->estimator == RSSRI_EST_SRI;
+  const bool literal = o->estimator == RSSRI_EST_LITERAL;
   const int P = sri ? 0 : h->P;
   const int nb = (o->pair_batch > 0) ? (int)std::min<long long>(o->pair_batch, ns) : ns;
   const int has_l = sri ? 0 : 1;
-  const int nbat2 = nb * (1 + has_l);
-  const bool bf16 = o->precision == RSSRI_PREC_BF16;
+  // chain kinds (X, Y): 0 = (R, R'), 1 = (R^L, R'^L); the literal estimator
+  // adds 2 = (R, R'^L) and 3 = (R^L, R'), which enter with a minus sign
+  const int nkind = literal ? 4 : 1 + has_l;
+  const int nbat2 = nb * nkind;
+  // tensor-core chain (bf16 or tf32 operands) instead of the fp64 one
+  const bool bf16 = o->precision == RSSRI_PREC_BF16 || o->precision == RSSRI_PREC_TF32;
+  const int tc_kind = o->precision == RSSRI_PREC_TF32 ? TC_TF32 : TC_BF16;
   if (bf16 && (n < 16 || !tc_available())) return RSSRI_ERR_INVALID_ARG;
   cudaError_t e;
 #define RS_CK(x)                                       \
@@ -878,6 +1078,11 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   RS_CK(ensure(h->sarr, nbat2 * sizeof(double)));
   RS_CK(ensure(h->e_st, ns * sizeof(double)));
   RS_CK(ensure(h->e_pair, ns * sizeof(double)));
+  if (literal && P > 0) {
+    RS_CK(ensure(h->litMP, (size_t)P * nbat2 * sizeof(double)));
+    RS_CK(ensure(h->litT, (size_t)na * nbat2 * sizeof(double)));
+    if (o->dd_arith == RSSRI_DD_DF64) RS_CK(ensure(h->litMhl, (size_t)nbat2 * nn * sizeof(float2)));
+  }
   if (P > 0) {
     RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
     RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
@@ -888,10 +1093,16 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));
     if (o->dd_arith == RSSRI_DD_DF64) {
       RS_CK(ensure(h->Ahl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->APhl, (size_t)P * na * sizeof(float2)));
+      RS_CK(ensure(h->Gamhl, (size_t)na * na * sizeof(float2)));
+      RS_CK(ensure(h->GGhl, (size_t)2 * nt * nn * sizeof(float2)));
       if (!h->d_df64_ready) {
         RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
+        RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
         SPAN(RSSRI_PROF_OTHER, 0.0);
         RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s));
+        RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s));
         h->d_df64_ready = true;
       }
     }
@@ -908,10 +1119,19 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     RS_CK(build_green(h));
   }
   // ---- S7: deterministic block per tau
+  const bool dd_df64 = !sri && P > 0 && o->dd_arith == RSSRI_DD_DF64;
+  if (dd_df64) {
+    SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_CK(to_df64(G, nt * nn, h->GGhl.as<float2>(), s));
+    RS_CK(to_df64(Gb, nt * nn, h->GGhl.as<float2>() + nt * nn, s));
+  }
   for (int t = 0; t < nt; ++t) {
     double *out = h->sdd.as<double>() + t * nn;
     if (sri) RS_CK(cudaMemsetAsync(out, 0, nn * sizeof(double), s));
-    else RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out, o->dd_arith == RSSRI_DD_DF64));
+    else if (dd_df64)
+      RS_CK(sigma_dd_tau_df64(h, h->GGhl.as<float2>() + t * nn,
+                              h->GGhl.as<float2>() + (nt + t) * nn, out));
+    else RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out));
   }
   RS_CK(cudaEventRecord(h->ev[3], s));
 
@@ -970,17 +1190,18 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   int *tc_err = h->flags.as<int>() + 4;
   if (bf16) {
     RS_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
-    RS_CK(chain_bf16(h, ns, G, Gb, h->sig_raw.as<double>(), tc_err));
+    RS_CK(chain_tc(h, tc_kind, ns, G, Gb, h->sig_raw.as<double>(), tc_err));
   }
   for (int t = 0; t < nt && !bf16; ++t) {
     const double *Gt = G + t * nn, *Gbt = Gb + t * nn;
     double *sig = h->sig_raw.as<double>() + t * nn;
     for (int x0 = 0; x0 < ns; x0 += nb) {
       const int cnt = std::min(nb, ns - x0);
-      // the batch is [kind][x] with kind 0 = (R, R'), kind 1 = (R^L, R'^L)
-      for (int kind = 0; kind <= has_l; ++kind) {
-        const double *X = fac + ((0LL * 2 + kind) * ns + x0) * nn;
-        const double *Y = fac + ((1LL * 2 + kind) * ns + x0) * nn;
+      // the batch is [kind][x]
+      for (int kind = 0; kind < nkind; ++kind) {
+        const int xk = (kind == 0 || kind == 2) ? 0 : 1, yk = (kind == 0 || kind == 3) ? 0 : 1;
+        const double *X = fac + ((0LL * 2 + xk) * ns + x0) * nn;
+        const double *Y = fac + ((1LL * 2 + yk) * ns + x0) * nn;
         double *xg = XG + (long long)kind * cnt * nn, *c = Cc + (long long)kind * cnt * nn,
                *bm = Bm + (long long)kind * cnt * nn;
         GemmArgs g;
@@ -993,9 +1214,9 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
         g.A = c; g.sA = nn; g.B = Gbt; g.sB = 0; g.C = bm; g.sC = nn;  // B = C Gb
         RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
       }
-      const int tot = cnt * (1 + has_l);
+      const int tot = cnt * nkind;
       // t = Tr B, s2 = Tr B B, B <- +-(2 t I - B)
-      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(chain_fold(Bm, tot, cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s)); }
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(chain_fold(Bm, tot, literal ? 2 * cnt : cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s)); }
       {
         GemmArgs g;
         g.M = n; g.N = n; g.K = n; g.batch = tot;
@@ -1003,6 +1224,8 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
         g.A = Bm; g.sA = nn; g.B = Cc; g.sB = nn; g.C = BC; g.sC = nn;  // (2tI - B) C
         RS_CK(gemm_p(h, RSSRI_PROF_CHAIN_GEMM, g));
       }
+      if (literal && P > 0)
+        RS_CK(literal_cross(h, o, t, x0, cnt, Gt, Gbt, XG, Cc, Bm, BC));
       if (collect_stats) {
         SPAN(RSSRI_PROF_OTHER, 0.0);
         RS_CK(cv_stats(BC, cnt, n, h->cv_stats.as<double>() + (long long)t * 5 * nn, s));
@@ -1015,9 +1238,9 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
         RS_CK(cv_pair_energy(BC, cnt, n, ct, Gbt, h->tarr.as<double>(), h->sarr.as<double>(),
                              h->h_tau_w[t], ne, h->e_st.as<double>() + x0, s));
       } else {
-        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, has_l, n, (double)ns, h->sdd.as<double>() + t * nn,
+        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, nkind, n, (double)ns, h->sdd.as<double>() + t * nn,
                                x0 == 0, sig, s)); }
-        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, has_l, h->h_tau_w[t], ne,
+        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, nkind, literal ? 2 : 1, h->h_tau_w[t], ne,
                           h->e_st.as<double>() + x0, s)); }
       }
     }

@@ -1,19 +1,29 @@
-// Element-wise kernels of the reduced-precision chain (S8 in bf16 on tensor
-// cores), in the range-separated split of Eqs. 14-15: with R = R^L + R^S,
+// Element-wise kernels of the reduced-precision chain (S8 on the tensor cores
+// with bf16 or tf32 operands), in the range-separated split of Eqs. 14-15:
+// with R = R^L + R^S,
 //   C^L = R^L G R'^L,  dC = R^S G R' + R^L G R'^S,  C = C^L + dC,
 //   X = dC Gb,  Y = C^L Gb,  dt = Tr X,  t^L = Tr Y,
 //   F(R,R') - F(R^L,R'^L) = (2 dt I - X) C + (2 t^L I - Y) dC,
 //   Tr[(F - F^L) Gb] = 2 dt (2 t^L + dt) - Tr(X X) - 2 Tr(X Y).
-// Only the small R^S terms ever appear on their own, so the bf16 rounding of
-// every operand costs a relative error of order 2^-8 of the stochastic
-// remainder, not of the full self-energy.  Traces and energies are summed in
-// fp64.
+// Only the small R^S terms ever appear on their own, so the rounding of every
+// operand (2^-8 relative for bf16, 2^-11 for tf32) costs an error of that
+// order of the stochastic remainder, not of the full self-energy.  Traces and
+// energies are summed in fp64.
 #include <cuda_bf16.h>
 
-#include "chain_bf16.cuh"
+#include "chain_tc.cuh"
+#include "tc_gemm.cuh"
 
 namespace rssri {
 namespace {
+
+// Operand storage: bf16, or fp32 holding a value rounded to tf32.
+__device__ __forceinline__ void put(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+__device__ __forceinline__ void put(float *p, double v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(__double2float_rn(v)));
+  *p = __uint_as_float(r);
+}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -42,8 +52,9 @@ int grid_cap(long long work, int threads) {
 }
 
 // fac = [set][kind][x][n][n] fp64 (kind 0: R, kind 1: R^L)
-__global__ void bf16_factors_kernel(const double *__restrict__ fac, int ns, int n, int ldp,
-                                    __nv_bfloat16 *__restrict__ xsl, __nv_bfloat16 *__restrict__ y3) {
+template <class T>
+__global__ void factors_kernel(const double *__restrict__ fac, int ns, int n, int ldp,
+                               T *__restrict__ xsl, T *__restrict__ y3) {
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
   const long long total = (long long)ns * n * ldp;
   const double *r0 = fac, *rl0 = fac + ns * nn, *r1 = fac + 2 * ns * nn, *rl1 = fac + 3 * ns * nn;
@@ -59,22 +70,23 @@ __global__ void bf16_factors_kernel(const double *__restrict__ fac, int ns, int 
       b = r1[src];
       bl = rl1[src];
     }
-    xsl[e] = __double2bfloat16(a - al);             // R^S
-    xsl[ns * mat + e] = __double2bfloat16(al);      // R^L
-    y3[e] = __double2bfloat16(b);                   // R'
-    y3[ns * mat + e] = __double2bfloat16(b - bl);   // R'^S
-    y3[2 * ns * mat + e] = __double2bfloat16(bl);   // R'^L
+    put(&xsl[e], a - al);            // R^S
+    put(&xsl[ns * mat + e], al);     // R^L
+    put(&y3[e], b);                  // R'
+    put(&y3[ns * mat + e], b - bl);  // R'^S
+    put(&y3[2 * ns * mat + e], bl);  // R'^L
   }
 }
 
-__global__ void bf16_matrices_kernel(const double *__restrict__ src, int cnt, int n, int ldp,
-                                     __nv_bfloat16 *__restrict__ dst) {
+template <class T>
+__global__ void matrices_kernel(const double *__restrict__ src, int cnt, int n, int ldp,
+                                T *__restrict__ dst) {
   const long long mat = (long long)n * ldp, total = (long long)cnt * mat;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long x = e / mat, r = e - x * mat;
     const int i = (int)(r / ldp), j = (int)(r - (long long)i * ldp);
-    dst[e] = __double2bfloat16(j < n ? src[x * n * n + (long long)i * n + j] : 0.0);
+    put(&dst[e], j < n ? src[x * n * n + (long long)i * n + j] : 0.0);
   }
 }
 
@@ -129,11 +141,11 @@ __global__ void __launch_bounds__(256) fold_traces_kernel(const float *__restric
   }
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) fold_operands_kernel(
     const float *__restrict__ xy, const float *__restrict__ dc, const float *__restrict__ cl, int ns,
-    int n, int ldp, const double *__restrict__ part, double w, double ne,
-    __nv_bfloat16 *__restrict__ a6, __nv_bfloat16 *__restrict__ ct, __nv_bfloat16 *__restrict__ dct,
-    double *__restrict__ e_st) {
+    int n, int ldp, const double *__restrict__ part, double w, double ne, T *__restrict__ a6,
+    T *__restrict__ ct, T *__restrict__ dct, double *__restrict__ e_st) {
   __shared__ float ta[32][33], tb[32][33];
   __shared__ double sums[4];
   const int bi = blockIdx.x, x = blockIdx.y, nt = gridDim.x;
@@ -147,8 +159,8 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
   const double dt = sums[0], tl = sums[1];
   const float *X = xy + x * nn, *Y = xy + (ns + x) * nn;
   const float *DC = dc + x * nn, *CL = cl + x * nn;
-  __nv_bfloat16 *A = a6 + x * mat, *Ab = a6 + (ns + x) * mat;
-  __nv_bfloat16 *Ct = ct + x * mat, *Dt = dct + x * mat;
+  T *A = a6 + x * mat, *Ab = a6 + (ns + x) * mat;
+  T *Ct = ct + x * mat, *Dt = dct + x * mat;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int ntp = (ldp + 31) / 32;
   for (int bj = 0; bj < ntp; ++bj) {
@@ -159,10 +171,11 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
         if (j < n) {
           const long long s2 = (long long)i * n + j;
           const double d = (i == j) ? 1.0 : 0.0;
-          A[o] = __double2bfloat16(2.0 * dt * d - (double)X[s2]);
-          Ab[o] = __double2bfloat16(2.0 * tl * d - (double)Y[s2]);
+          put(&A[o], 2.0 * dt * d - (double)X[s2]);
+          put(&Ab[o], 2.0 * tl * d - (double)Y[s2]);
         } else {
-          A[o] = Ab[o] = __double2bfloat16(0.0);
+          put(&A[o], 0.0);
+          put(&Ab[o], 0.0);
         }
       }
     }
@@ -178,8 +191,8 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
       const int i = bi * 32 + r, j = bj * 32 + tx;  // destination (i, j) = source (j, i)
       if (i < n && j < ldp) {
         const long long o = (long long)i * ldp + j;
-        Ct[o] = __float2bfloat16_rn(j < n ? ta[tx][r] : 0.f);
-        Dt[o] = __float2bfloat16_rn(j < n ? tb[tx][r] : 0.f);
+        put(&Ct[o], j < n ? (double)ta[tx][r] : 0.0);
+        put(&Dt[o], j < n ? (double)tb[tx][r] : 0.0);
       }
     }
   }
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
   }
 }
 
-__global__ void reduce_bf16_kernel(const float *__restrict__ part, int groups, long long nn,
+__global__ void reduce_tc_kernel(const float *__restrict__ part, int groups, long long nn,
                                    const double *__restrict__ base, double ns,
                                    double *__restrict__ sig) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
@@ -202,39 +215,54 @@ __global__ void reduce_bf16_kernel(const float *__restrict__ part, int groups, l
 
 }  // namespace
 
-cudaError_t bf16_factors(const double *fac, int ns, int n, int ldp, __nv_bfloat16 *xsl,
-                         __nv_bfloat16 *y3, cudaStream_t s) {
-  bf16_factors_kernel<<<grid_cap((long long)ns * n * ldp, 256), 256, 0, s>>>(fac, ns, n, ldp, xsl,
-                                                                             y3);
+cudaError_t chain_factors(int kind, const double *fac, int ns, int n, int ldp, void *xsl,
+                          void *y3, cudaStream_t s) {
+  const int grid = grid_cap((long long)ns * n * ldp, 256);
+  if (kind == TC_BF16)
+    factors_kernel<<<grid, 256, 0, s>>>(fac, ns, n, ldp, static_cast<__nv_bfloat16 *>(xsl),
+                                        static_cast<__nv_bfloat16 *>(y3));
+  else
+    factors_kernel<<<grid, 256, 0, s>>>(fac, ns, n, ldp, static_cast<float *>(xsl),
+                                        static_cast<float *>(y3));
   ++launch_counter();
   return cudaGetLastError();
 }
 
-cudaError_t bf16_matrices(const double *src, int cnt, int n, int ldp, __nv_bfloat16 *dst,
-                          cudaStream_t s) {
-  bf16_matrices_kernel<<<grid_cap((long long)cnt * n * ldp, 256), 256, 0, s>>>(src, cnt, n, ldp,
-                                                                               dst);
+cudaError_t chain_matrices(int kind, const double *src, int cnt, int n, int ldp, void *dst,
+                           cudaStream_t s) {
+  const int grid = grid_cap((long long)cnt * n * ldp, 256);
+  if (kind == TC_BF16)
+    matrices_kernel<<<grid, 256, 0, s>>>(src, cnt, n, ldp, static_cast<__nv_bfloat16 *>(dst));
+  else
+    matrices_kernel<<<grid, 256, 0, s>>>(src, cnt, n, ldp, static_cast<float *>(dst));
   ++launch_counter();
   return cudaGetLastError();
 }
 
-cudaError_t fold_bf16(const float *xy, const float *dc, const float *cl, int ns, int n, int ldp,
-                      double w, double ne, __nv_bfloat16 *a6, __nv_bfloat16 *ct,
-                      __nv_bfloat16 *dct, double *e_st, double *part, cudaStream_t s) {
+cudaError_t fold_tc(int kind, const float *xy, const float *dc, const float *cl, int ns, int n,
+                    int ldp, double w, double ne, void *a6, void *ct, void *dct, double *e_st,
+                    double *part, cudaStream_t s) {
   dim3 grid((n + 31) / 32, ns);
   fold_traces_kernel<<<grid, 256, 0, s>>>(xy, ns, n, part);
   ++launch_counter();
   RS_TRY(cudaGetLastError());
-  fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne, a6, ct, dct,
-                                            e_st);
+  if (kind == TC_BF16)
+    fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne,
+                                              static_cast<__nv_bfloat16 *>(a6),
+                                              static_cast<__nv_bfloat16 *>(ct),
+                                              static_cast<__nv_bfloat16 *>(dct), e_st);
+  else
+    fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne,
+                                              static_cast<float *>(a6), static_cast<float *>(ct),
+                                              static_cast<float *>(dct), e_st);
   ++launch_counter();
   return cudaGetLastError();
 }
 
-cudaError_t reduce_bf16(const float *part, int groups, int n, const double *base, double ns,
-                        double *sig, cudaStream_t s) {
+cudaError_t reduce_tc(const float *part, int groups, int n, const double *base, double ns,
+                      double *sig, cudaStream_t s) {
   const long long nn = (long long)n * n;
-  reduce_bf16_kernel<<<grid_cap(nn, 256), 256, 0, s>>>(part, groups, nn, base, ns, sig);
+  reduce_tc_kernel<<<grid_cap(nn, 256), 256, 0, s>>>(part, groups, nn, base, ns, sig);
   ++launch_counter();
   return cudaGetLastError();
 }

@@ -46,8 +46,6 @@ int dgemm_ksplit(const GemmArgs &g);
 // Scratch doubles needed by dgemm() for `g`.
 size_t dgemm_work_elems(const GemmArgs &g);
 cudaError_t dgemm(const GemmArgs &g, double *work, size_t work_elems, cudaStream_t s);
-// The same product in double-float arithmetic on the fp32 pipes (~1e-13).
-cudaError_t dgemm_df64(const GemmArgs &g, double *work, size_t work_elems, cudaStream_t s);
 // Edge of the tile the autotuner chose for this shape (-1 before first use).
 int dgemm_tile_edge(const GemmArgs &g);
 

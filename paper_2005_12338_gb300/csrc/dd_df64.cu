@@ -7,9 +7,13 @@
 // with error-free transformations: the product's rounding error comes from
 // one fma (TwoProduct), the sum's from Knuth's TwoSum, and the two error
 // streams are collected in a second float.  About a dozen fp32 operations
-// replace one DFMA; after each row of the sparse operand (~40 terms) the pair
-// is renormalised exactly (Fast2Sum) and every four rows it is added into an
-// fp64 total.  The result agrees with the fp64 contraction to ~1e-12 relative.
+// replace one DFMA; after each pair of the sparse operand's row (~40 terms)
+// the pair is renormalised exactly (Fast2Sum) and every four pairs it is
+// added into an fp64 total.  The result agrees with the fp64 contraction to
+// ~1e-12 relative.
+#include <climits>
+#include <algorithm>
+
 #include "dd_df64.cuh"
 
 namespace rssri {
@@ -30,65 +34,364 @@ __global__ void to_df64_kernel(const double *__restrict__ x, long long len, floa
 }
 
 // T[m][q][j] = sum_{a in row m} sum_{b in row j} D[a][b] At[(col a, col b)][q]
-template <int QC>
-__global__ void __launch_bounds__(128) dd_spmm_df64_kernel(
+//
+// One warp per (row m, group of 4 consecutive rows j, chunk of 64 aux
+// indices q; lane t owns q0 + 2t and q0 + 2t + 1).  For each pair a = (m, k)
+// of row m and each window of SLR = 64 columns l covering the group's pairs,
+// the warp writes its rows' v^L entries D[a][(j, l)] into a dense 4 x SLR table
+// in shared memory (zero where (j, l) is not a kept pair) and then runs over
+// the columns the group actually holds: per column one 16-byte load of
+// At[k][l][q-pair] feeds 8 multiply-adds (4 rows x 2 aux indices).  The D
+// entries of the next (pair, window) are loaded into registers before the
+// current one is computed and the table is double-buffered, so a warp never
+// waits on another warp and global latency hides behind the arithmetic.
+constexpr int SLR = 64, SQW = 64, SWARPS = 4, SREG = 6;  // SREG x 8 entries per row in registers
+
+__device__ __forceinline__ void df_mac2(float &S, float &E, float2 d, float xh, float xl) {
+  // TwoProduct of the high parts plus the cross terms, then TwoSum S + p
+  const float p = __fmul_rn(d.x, xh);
+  float e = __fmaf_rn(d.x, xh, -p);
+  e = __fmaf_rn(d.x, xl, e);
+  e = __fmaf_rn(d.y, xh, e);
+  const float s = __fadd_rn(S, p);
+  const float bp = __fsub_rn(s, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  S = s;
+  E = __fadd_rn(E, __fadd_rn(err, e));
+}
+
+// (TH, TL) += (S, E): double-float addition of two normalised pairs (TwoSum of
+// the high parts, low parts and error added, Fast2Sum).  All fp32: on this GPU
+// a few fp64 operations per output would cost as much as the products.
+__device__ __forceinline__ void df_acc(float &TH, float &TL, float S, float E) {
+  const float s = __fadd_rn(TH, S);
+  const float bp = __fsub_rn(s, TH);
+  const float err = __fadd_rn(__fsub_rn(TH, __fsub_rn(s, bp)), __fsub_rn(S, bp));
+  const float t = __fadd_rn(__fadd_rn(TL, E), err);
+  TH = __fadd_rn(s, t);
+  TL = __fsub_rn(t, __fsub_rn(TH, s));
+}
+
+__global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     const int *__restrict__ rowptr, const int *__restrict__ pcol, const float2 *__restrict__ D,
     int P, const float2 *__restrict__ At, int n, int naux, double *__restrict__ T) {
+  __shared__ float2 Dt[SWARPS][2][4][SLR];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 4 + warp;
-  const int m = blockIdx.y;
-  if (j >= n) return;
+  const int j0 = (blockIdx.x * SWARPS + warp) * 4, m = blockIdx.y, q0 = blockIdx.z * SQW;
+  if (j0 >= n) return;  // whole warp
+  const int j1 = min(n, j0 + 4);
   const int a0 = rowptr[m], a1 = rowptr[m + 1];
-  const int b0 = rowptr[j], b1 = rowptr[j + 1];
-  for (int q0 = 0; q0 < naux; q0 += 32 * QC) {
-    double tot[QC];
+  // column extent of the group's rows (columns are sorted within a row)
+  int lo = INT_MAX, hi = -1;
+  for (int j = j0; j < j1; ++j) {
+    const int b0 = rowptr[j], b1 = rowptr[j + 1];
+    if (b1 > b0) {
+      lo = min(lo, pcol[b0]);
+      hi = max(hi, pcol[b1 - 1]);
+    }
+  }
+  const int nwin = hi >= lo ? (hi - lo) / SLR + 1 : 0;
+  const int nstage = (a1 - a0) * nwin;
+  // lane -> (row of the group, sub-lane) for the table fill
+  const int r_fill = lane >> 3, sub = lane & 7;
+  const int j_fill = j0 + r_fill;
+  const int fb0 = j_fill < j1 ? rowptr[j_fill] : 0, fb1 = j_fill < j1 ? rowptr[j_fill + 1] : 0;
+  float2 dv[SREG];
+  int dc[SREG];
+  auto prefetch = [&](int st) {
+    const float2 *Drow = D + (long long)(a0 + st / nwin) * P;
 #pragma unroll
-    for (int c = 0; c < QC; ++c) tot[c] = 0.0;
-    const int qv = naux - q0 - lane;
-    float S[QC], E[QC];
+    for (int t = 0; t < SREG; ++t) {
+      const int b = fb0 + sub + 8 * t;
+      dc[t] = b < fb1 ? pcol[b] : -1;
+      dv[t] = b < fb1 ? Drow[b] : make_float2(0.f, 0.f);
+    }
+  };
+  auto fill = [&](int st, int buf) {
+    const int a = a0 + st / nwin, lc = lo + (st % nwin) * SLR;
+    float2 *row = &Dt[warp][buf][r_fill][0];
+    for (int c = sub; c < SLR; c += 8) row[c] = make_float2(0.f, 0.f);
+    __syncwarp();
 #pragma unroll
-    for (int c = 0; c < QC; ++c) S[c] = E[c] = 0.0f;
-    for (int a = a0; a < a1; ++a) {
-      const float2 *Drow = D + (long long)a * P;
-      const float2 *Ak = At + (long long)pcol[a] * n * naux + q0 + lane;
-      for (int b = b0; b < b1; ++b) {
-        const float2 d = Drow[b];
-        const float2 *ap = Ak + (long long)pcol[b] * naux;
+    for (int t = 0; t < SREG; ++t) {
+      const int c = dc[t] - lc;
+      if (dc[t] >= 0 && c >= 0 && c < SLR) row[c] = dv[t];
+    }
+    // rows longer than SREG x 8 entries: the rest straight from memory
+    const float2 *Drow = D + (long long)a * P;
+    for (int b = fb0 + sub + 8 * SREG; b < fb1; b += 8) {
+      const int c = pcol[b] - lc;
+      if (c >= 0 && c < SLR) row[c] = Drow[b];
+    }
+    __syncwarp();
+  };
+
+  float TH[4][2], TL[4][2], S[4][2], E[4][2];
 #pragma unroll
-        for (int c = 0; c < QC; ++c) {
-          if (32 * c < qv) {
-            const float2 x = ap[32 * c];
-            // TwoProduct of the high parts plus the cross terms
-            const float p = __fmul_rn(d.x, x.x);
-            float e = __fmaf_rn(d.x, x.x, -p);
-            e = __fmaf_rn(d.x, x.y, e);
-            e = __fmaf_rn(d.y, x.x, e);
-            // TwoSum S + p
-            const float s = __fadd_rn(S[c], p);
-            const float bp = __fsub_rn(s, S[c]);
-            const float err = __fadd_rn(__fsub_rn(S[c], __fsub_rn(s, bp)), __fsub_rn(p, bp));
-            S[c] = s;
-            E[c] = __fadd_rn(E[c], __fadd_rn(err, e));
-          }
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) TH[r][c] = TL[r][c] = S[r][c] = E[r][c] = 0.0f;
+  const int q = q0 + 2 * lane;
+  const bool q_ok0 = q < naux, q_ok1 = q + 1 < naux;
+  const bool vec = (naux % 2) == 0 && q_ok1;  // 16-byte aligned pair of pairs
+  if (nstage > 0) {
+    prefetch(0);
+    fill(0, 0);
+  }
+  for (int st = 0; st < nstage; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nstage) prefetch(st + 1);
+    const int a = a0 + st / nwin, lc = lo + (st % nwin) * SLR;
+    const int lb = max(lo, lc), le = min(hi, lc + SLR - 1);
+    const float2 *Ak = At + (long long)pcol[a] * n * naux + q;
+    const float2 *Dw = &Dt[warp][buf][0][0];
+    for (int l = lb; l <= le; ++l) {
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float2 *ap = Ak + (long long)l * naux;
+      if (vec) {
+        x = __ldg(reinterpret_cast<const float4 *>(ap));
+      } else {
+        if (q_ok0) {
+          const float2 v = __ldg(ap);
+          x.x = v.x;
+          x.y = v.y;
+        }
+        if (q_ok1) {
+          const float2 v = __ldg(ap + 1);
+          x.z = v.x;
+          x.w = v.y;
         }
       }
-      // exact renormalisation per row (Fast2Sum); fp64 fold every 4 rows
-      const bool fold = ((a - a0) & 3) == 3 || a + 1 == a1;
 #pragma unroll
-      for (int c = 0; c < QC; ++c) {
-        const float s = __fadd_rn(S[c], E[c]);
-        E[c] = __fsub_rn(E[c], __fsub_rn(s, S[c]));
-        S[c] = s;
-        if (fold) {
-          tot[c] += (double)S[c] + (double)E[c];
-          S[c] = E[c] = 0.0f;
+      for (int r = 0; r < 4; ++r) {
+        const float2 d = Dw[r * SLR + (l - lc)];
+        df_mac2(S[r][0], E[r][0], d, x.x, x.y);
+        df_mac2(S[r][1], E[r][1], d, x.z, x.w);
+      }
+    }
+    // after the last window of a pair: exact renormalisation (Fast2Sum);
+    // added into the pair totals every 4 pairs and at the end
+    if (st % nwin == nwin - 1) {
+      const int ia = st / nwin;
+      const bool fold = (ia & 3) == 3 || ia + 1 == a1 - a0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float sn = __fadd_rn(S[r][c], E[r][c]);
+          E[r][c] = __fsub_rn(E[r][c], __fsub_rn(sn, S[r][c]));
+          S[r][c] = sn;
+          if (fold) {
+            df_acc(TH[r][c], TL[r][c], S[r][c], E[r][c]);
+            S[r][c] = E[r][c] = 0.0f;
+          }
+        }
+    }
+    if (st + 1 < nstage) fill(st + 1, buf ^ 1);
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int qc = q + c;
+    if (qc >= naux) continue;
+    double *out = T + ((long long)m * naux + qc) * n;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int j = j0 + r;
+      if (j < j1) out[j] = (double)TH[r][c] + (double)TL[r][c];
+    }
+  }
+}
+
+// ------------------------------------------------- double-float products --
+// C = alpha op(A) op(B) with A, B already split into (hi, lo) float pairs.
+// MODE 0: strided operands; MODE 1: segmented (A(m,kk) = A[col[s0+kk]*lda + m],
+// B(kk,q) = B[(s0+kk)*ldb + q], s0 = seg[b]).  OUT 0: fp64 C (or raw fp64
+// partials of a K chunk); OUT 1: C written as (hi, lo) pairs.  Each thread
+// owns 4 x 4 outputs of a 64 x 64 tile; K goes in 16-deep slabs through
+// shared memory; the pairs are renormalised exactly after each slab and folded
+// into fp64 totals every 256 terms.
+constexpr int DBM = 64, DBN = 64, DBK = 16, DNT = 256;
+
+__device__ __forceinline__ void df_mac(float &S, float &E, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(S, p);
+  const float bp = __fsub_rn(s, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  S = s;
+  E = __fadd_rn(E, __fadd_rn(err, e));
+}
+
+template <int MODE, int TA, int TB, int OUT>
+__global__ void __launch_bounds__(DNT) df_gemm_kernel(
+    int M, int N, int K, int kchunk, int ksplit, const float2 *__restrict__ A, long long lda,
+    long long sA, const float2 *__restrict__ B, long long ldb, long long sB, void *__restrict__ Cv,
+    long long ldc, long long sC, double alpha, int partial, const int *__restrict__ seg,
+    const int *__restrict__ col) {
+  __shared__ float2 As[2][DBK][DBM + 1];
+  __shared__ float2 Bs[2][DBK][DBN + 1];
+  constexpr int LA = DBM * DBK / DNT, LB = DBN * DBK / DNT;
+  constexpr bool AK = (MODE == 0 && TA == 0), BKc = (MODE == 0 && TB == 1);
+  const int z = blockIdx.z;
+  const int b = z / ksplit, ks = z % ksplit;
+  int kbeg, kend;
+  long long s0 = 0;
+  if (MODE == 1) {
+    s0 = seg[b];
+    kbeg = 0;
+    kend = seg[b + 1] - seg[b];
+  } else {
+    kbeg = ks * kchunk;
+    kend = min(K, kbeg + kchunk);
+    A += (long long)b * sA;
+    B += (long long)b * sB;
+  }
+  const int row0 = blockIdx.y * DBM, col0 = blockIdx.x * DBN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j of the tile, so
+  // that a warp's shared-memory reads are one broadcast (A) and one run of 16
+  // consecutive pairs (B)
+  float TH[4][4], TL[4][4];
+  float S[4][4], E[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) TH[i][j] = TL[i][j] = S[i][j] = E[i][j] = 0.0f;
+  float2 ra[LA], rb[LB];
+  const float2 zero = make_float2(0.f, 0.f);
+  auto load = [&](int kt) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * DNT;
+      const int i = AK ? e / DBK : e % DBM, k = AK ? e % DBK : e / DBM;
+      const int gi = row0 + i, gk = kt + k;
+      float2 v = zero;
+      if (gi < M && gk < kend) {
+        if (MODE == 1) v = A[(long long)col[s0 + gk] * lda + gi];
+        else if (TA == 0) v = A[(long long)gi * lda + gk];
+        else v = A[(long long)gk * lda + gi];
+      }
+      ra[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * DNT;
+      const int j = BKc ? e / DBK : e % DBN, k = BKc ? e % DBK : e / DBN;
+      const int gj = col0 + j, gk = kt + k;
+      float2 v = zero;
+      if (gj < N && gk < kend) {
+        if (MODE == 1) v = B[(s0 + gk) * ldb + gj];
+        else if (TB == 0) v = B[(long long)gk * ldb + gj];
+        else v = B[(long long)gj * ldb + gk];
+      }
+      rb[r] = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * DNT;
+      const int i = AK ? e / DBK : e % DBM, k = AK ? e % DBK : e / DBM;
+      As[buf][k][i] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * DNT;
+      const int j = BKc ? e / DBK : e % DBN, k = BKc ? e % DBK : e / DBN;
+      Bs[buf][k][j] = rb[r];
+    }
+  };
+  constexpr int FOLD = 256 / DBK;
+  int slab = 0;
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int kt = kbeg; kt < kend; kt += DBK) {
+      const bool more = kt + DBK < kend;
+      if (more) load(kt + DBK);
+#pragma unroll
+      for (int kk = 0; kk < DBK; ++kk) {
+        float2 a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_mac(S[i][j], E[i][j], a[i], bb[j]);
+      }
+      ++slab;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float sn = __fadd_rn(S[i][j], E[i][j]);
+          E[i][j] = __fsub_rn(E[i][j], __fsub_rn(sn, S[i][j]));
+          S[i][j] = sn;
+          if (slab == FOLD || !more) {
+            df_acc(TH[i][j], TL[i][j], S[i][j], E[i][j]);
+            S[i][j] = E[i][j] = 0.0f;
+          }
+        }
+      if (slab == FOLD) slab = 0;
+      if (more) {
+        store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+  const bool neg = alpha == -1.0, unit = alpha == 1.0 || neg;
+  for (int i = 0; i < 4; ++i) {
+    const int gi = row0 + ty + 16 * i;
+    if (gi >= M) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int gj = col0 + tx + 16 * j;
+      if (gj >= N) continue;
+      const float h = TH[i][j], l = TL[i][j];
+      if (partial) {
+        static_cast<double *>(Cv)[(long long)z * M * N + (long long)gi * N + gj] =
+            (double)h + (double)l;
+      } else {
+        const long long o = (long long)b * sC + (long long)gi * ldc + gj;
+        if (OUT == 0) {
+          const double v = (double)h + (double)l;
+          static_cast<double *>(Cv)[o] = unit ? (neg ? -v : v) : alpha * v;
+        } else if (unit) {
+          static_cast<float2 *>(Cv)[o] = neg ? make_float2(-h, -l) : make_float2(h, l);
+        } else {
+          const double v = alpha * ((double)h + (double)l);
+          const float hi = __double2float_rn(v);
+          static_cast<float2 *>(Cv)[o] = make_float2(hi, __double2float_rn(v - (double)hi));
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < QC; ++c)
-      if (32 * c < qv) T[((long long)m * naux + q0 + lane + 32 * c) * n + j] = tot[c];
   }
+}
+
+__global__ void df_reduce_kernel(const double *__restrict__ part, int ks, int M, int N,
+                                 double *__restrict__ C, long long ldc, double alpha) {
+  const long long mn = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < ks; ++k) s += part[k * mn + e];
+    const long long i = e / N, j = e - i * N;
+    C[i * ldc + j] = alpha * s;
+  }
+}
+
+__global__ void gather_rows_f2_kernel(const float2 *__restrict__ src, const int *__restrict__ idx,
+                                      int ncols, float2 *__restrict__ dst) {
+  const int r = blockIdx.x;
+  const float2 *s = src + (long long)idx[r] * ncols;
+  float2 *d = dst + (long long)r * ncols;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) d[c] = s[c];
 }
 
 }  // namespace
@@ -102,29 +405,82 @@ cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s) {
 
 cudaError_t dd_exchange_spmm_df64(const int *rowptr, const int *pcol, const float2 *D, int P,
                                   const float2 *At, int n, int naux, double *T, cudaStream_t s) {
-  // at most 10 accumulator pairs per lane: more resident warps hide the
-  // latency of the dependent TwoSum chains better than longer rows do
-  static const int kQC[] = {1, 2, 3, 4, 5, 6, 8, 10};
-  int best = 8;
-  long long best_lanes = -1;
-  for (int qc : kQC) {
-    const long long passes = (naux + 32LL * qc - 1) / (32LL * qc);
-    const long long lanes = passes * 32 * qc + passes * 64;
-    if (best_lanes < 0 || lanes < best_lanes) {
-      best_lanes = lanes;
-      best = qc;
-    }
+  if (n <= 0 || naux <= 0) return cudaSuccess;
+  dim3 grid(ceil_div(n, 4 * SWARPS), n, ceil_div(naux, SQW));
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+  dd_spmm_warp_df64_kernel<<<grid, 32 * SWARPS, 0, s>>>(rowptr, pcol, D, P, At, n, naux, T);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if ((g.C64 == nullptr) == (g.C2 == nullptr)) return cudaErrorInvalidValue;
+  // split K (fp64 output only) when the output has few tiles and K is long
+  const long long tiles = (long long)ceil_div(g.M, DBM) * ceil_div(g.N, DBN) * g.batch;
+  int ks = 1;
+  if (g.C64 && g.batch == 1 && tiles < 2 * 152 && g.K >= 1024) {
+    ks = (int)std::min<long long>((4 * 152 + tiles - 1) / tiles, g.K / 256);
+    ks = std::max(1, std::min(ks, 256));
   }
-  dim3 grid(ceil_div(n, 4), n);
-#define RS_SPMM(QC)                                                                           \
-  case QC:                                                                                    \
-    dd_spmm_df64_kernel<QC><<<grid, 128, 0, s>>>(rowptr, pcol, D, P, At, n, naux, T); \
-    break;
-  switch (best) {
-    RS_SPMM(1) RS_SPMM(2) RS_SPMM(3) RS_SPMM(4) RS_SPMM(5) RS_SPMM(6) RS_SPMM(8) RS_SPMM(10)
-    default: return cudaErrorInvalidValue;
+  int kc = ((ceil_div(g.K, ks) + DBK - 1) / DBK) * DBK;
+  ks = std::max(1, ceil_div(g.K, kc));
+  if (ks > 1 && work_elems < (size_t)ks * g.M * g.N) return cudaErrorInvalidValue;
+  if (g.batch * ks > 65535) return cudaErrorInvalidValue;
+  dim3 grid(ceil_div(g.N, DBN), ceil_div(g.M, DBM), g.batch * ks);
+  void *out = ks > 1 ? (void *)work : (g.C64 ? (void *)g.C64 : (void *)g.C2);
+  const int part = ks > 1;
+#define RS_DF(TA, TB, OUT)                                                                      \
+  df_gemm_kernel<0, TA, TB, OUT><<<grid, DNT, 0, s>>>(g.M, g.N, g.K, kc, ks, g.A, g.lda, g.sA, \
+                                                     g.B, g.ldb, g.sB, out, g.ldc, g.sC,       \
+                                                     g.alpha, part, nullptr, nullptr)
+  const int o = g.C2 ? 1 : 0;
+  if (!g.transA && !g.transB) { if (o) RS_DF(0, 0, 1); else RS_DF(0, 0, 0); }
+  else if (!g.transA && g.transB) { if (o) RS_DF(0, 1, 1); else RS_DF(0, 1, 0); }
+  else if (g.transA && !g.transB) { if (o) RS_DF(1, 0, 1); else RS_DF(1, 0, 0); }
+  else { if (o) RS_DF(1, 1, 1); else RS_DF(1, 1, 0); }
+#undef RS_DF
+  ++launch_counter();
+  RS_TRY(cudaGetLastError());
+  if (part) {
+    const long long mn = (long long)g.M * g.N;
+    df_reduce_kernel<<<grid_cap(mn, 256), 256, 0, s>>>(work, ks, g.M, g.N, g.C64, g.ldc, g.alpha);
+    ++launch_counter();
+    RS_TRY(cudaGetLastError());
   }
-#undef RS_SPMM
+  return cudaSuccess;
+}
+
+size_t df_gemm_work(const DfGemm &g) {
+  const long long tiles = (long long)ceil_div(g.M, DBM) * ceil_div(g.N, DBN) * g.batch;
+  if (!(g.C64 && g.batch == 1 && tiles < 2 * 152 && g.K >= 1024)) return 0;
+  int ks = (int)std::min<long long>((4 * 152 + tiles - 1) / tiles, g.K / 256);
+  ks = std::max(1, std::min(ks, 256));
+  const int kc = ((ceil_div(g.K, ks) + DBK - 1) / DBK) * DBK;
+  ks = std::max(1, ceil_div(g.K, kc));
+  return ks > 1 ? (size_t)ks * g.M * g.N : 0;
+}
+
+cudaError_t df_gemm_segmented(int batch, int M, int N, const int *seg, const int *col,
+                              const float2 *A, long long lda, const float2 *B, long long ldb,
+                              float2 *C, long long ldc, long long sC, cudaStream_t s) {
+  if (batch <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  for (int b0 = 0; b0 < batch; b0 += 65535) {
+    const int nb = std::min(65535, batch - b0);
+    dim3 grid(ceil_div(N, DBN), ceil_div(M, DBM), nb);
+    df_gemm_kernel<1, 1, 0, 1><<<grid, DNT, 0, s>>>(M, N, 0, 0, 1, A, lda, 0, B, ldb, 0,
+                                                    C + (long long)b0 * sC, ldc, sC, 1.0, 0,
+                                                    seg + b0, col);
+    ++launch_counter();
+    RS_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+cudaError_t gather_rows_f2(const float2 *src, const int *idx, int P, int ncols, float2 *dst,
+                           cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  gather_rows_f2_kernel<<<P, 128, 0, s>>>(src, idx, ncols, dst);
   ++launch_counter();
   return cudaGetLastError();
 }

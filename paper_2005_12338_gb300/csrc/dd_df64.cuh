@@ -12,4 +12,26 @@ cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s);
 cudaError_t dd_exchange_spmm_df64(const int *rowptr, const int *pcol, const float2 *D, int P,
                                   const float2 *At, int n, int naux, double *T, cudaStream_t s);
 
+// Double-float product C = alpha op(A) op(B) on (hi, lo) float pairs; exactly
+// one of C64 (fp64) and C2 (pairs) is set.  Split K (fp64 output, batch 1)
+// uses `work` of df_gemm_work() doubles.
+struct DfGemm {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const float2 *A = nullptr, *B = nullptr;
+  long long lda = 0, ldb = 0, sA = 0, sB = 0;
+  int transA = 0, transB = 0;
+  double *C64 = nullptr;
+  float2 *C2 = nullptr;
+  long long ldc = 0, sC = 0;
+  double alpha = 1.0;
+};
+cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s);
+size_t df_gemm_work(const DfGemm &g);
+// C[b][m][q] = sum_{a in [seg[b], seg[b+1])} A[col[a]*lda + m] * B[a*ldb + q], pairs out.
+cudaError_t df_gemm_segmented(int batch, int M, int N, const int *seg, const int *col,
+                              const float2 *A, long long lda, const float2 *B, long long ldb,
+                              float2 *C, long long ldc, long long sC, cudaStream_t s);
+cudaError_t gather_rows_f2(const float2 *src, const int *idx, int P, int ncols, float2 *dst,
+                           cudaStream_t s);
+
 }  // namespace rssri

@@ -390,213 +390,4 @@ cudaError_t dgemm_segmented(int batch, int M, int N, const int *seg, const int *
   return cudaSuccess;
 }
 
-// ----------------------------------------------------- double-float GEMM --
-// The same products in double-float arithmetic on the fp32 pipes (used for
-// the deterministic block when its exchange contraction runs in double-float
-// too).  Operands are split on load into (hi, lo) float pairs; each
-// multiply-add is an error-free TwoProduct (fma) plus TwoSum with the error
-// terms collected in a second float; after every K slab the pair is
-// renormalised exactly (Fast2Sum) and about every 256 terms it is folded into
-// an fp64 total, so long K (split-K chunks of ~3e3 terms) stays accurate to
-// ~1e-12 relative while the fp64 pipe stays nearly idle.
-namespace {
-
-__device__ __forceinline__ float2 split_df(double v) {
-  const float hi = __double2float_rn(v);
-  return make_float2(hi, __double2float_rn(v - (double)hi));
-}
-
-template <class TL, int TA, int TB>
-__global__ void __launch_bounds__(TL::NT) dgemm_df64_kernel(
-    int M, int N, int K, int kchunk, int ksplit, const double *__restrict__ A, long long lda,
-    long long sA, const double *__restrict__ B, long long ldb, long long sB,
-    double *__restrict__ C, long long ldc, long long sC, double alpha, double beta, int partial) {
-  constexpr int BM = TL::BM, BN = TL::BN, BK = TL::BK, TM = TL::TM, TN = TL::TN, NT = TL::NT;
-  constexpr int LA = (BM * BK + NT - 1) / NT, LB = (BN * BK + NT - 1) / NT;
-  constexpr bool AK = (TA == 0), BKc = (TB == 1);
-  __shared__ float2 As[2][BK][BM + 1];
-  __shared__ float2 Bs[2][BK][BN + 1];
-  const int z = blockIdx.z;
-  const int b = z / ksplit, ks = z % ksplit;
-  const int kbeg = ks * kchunk, kend = min(K, kbeg + kchunk);
-  A += (long long)b * sA;
-  B += (long long)b * sB;
-  double *Cb = partial ? C + (long long)z * M * N : C + (long long)b * sC;
-  const long long ldcb = partial ? N : ldc;
-  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  const int tid = threadIdx.x, tx = tid % TL::TX, ty = tid / TL::TX;
-  double tot[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) tot[i][j] = 0.0;
-  // fold into the fp64 total about every 256 terms
-  constexpr int FOLD = (256 + BK - 1) / BK;
-  float S[TM][TN], E[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) S[i][j] = E[i][j] = 0.0f;
-  int slab = 0;
-  float2 ra[LA], rb[LB];
-  auto load = [&](int kt) {
-#pragma unroll
-    for (int r = 0; r < LA; ++r) {
-      const int e = tid + r * NT;
-      double v = 0.0;
-      if (e < BM * BK) {
-        const int i = AK ? e / BK : e % BM, k = AK ? e % BK : e / BM;
-        const int gi = row0 + i, gk = kt + k;
-        if (gi < M && gk < kend) v = TA == 0 ? A[(long long)gi * lda + gk] : A[(long long)gk * lda + gi];
-      }
-      ra[r] = split_df(v);
-    }
-#pragma unroll
-    for (int r = 0; r < LB; ++r) {
-      const int e = tid + r * NT;
-      double v = 0.0;
-      if (e < BN * BK) {
-        const int j = BKc ? e / BK : e % BN, k = BKc ? e % BK : e / BN;
-        const int gj = col0 + j, gk = kt + k;
-        if (gj < N && gk < kend) v = TB == 0 ? B[(long long)gk * ldb + gj] : B[(long long)gj * ldb + gk];
-      }
-      rb[r] = split_df(v);
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int r = 0; r < LA; ++r) {
-      const int e = tid + r * NT;
-      if (e < BM * BK) {
-        const int i = AK ? e / BK : e % BM, k = AK ? e % BK : e / BM;
-        As[buf][k][i] = ra[r];
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < LB; ++r) {
-      const int e = tid + r * NT;
-      if (e < BN * BK) {
-        const int j = BKc ? e / BK : e % BN, k = BKc ? e % BK : e / BN;
-        Bs[buf][k][j] = rb[r];
-      }
-    }
-  };
-  if (kbeg < kend) {
-    load(kbeg);
-    store(0);
-    __syncthreads();
-    int buf = 0;
-    for (int kt = kbeg; kt < kend; kt += BK) {
-      const bool more = kt + BK < kend;
-      if (more) load(kt + BK);
-#pragma unroll
-      for (int kk = 0; kk < BK; ++kk) {
-        float2 a[TM], bb[TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty * TM + i];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx * TN + j];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) {
-            const float p = __fmul_rn(a[i].x, bb[j].x);
-            float e = __fmaf_rn(a[i].x, bb[j].x, -p);
-            e = __fmaf_rn(a[i].x, bb[j].y, e);
-            e = __fmaf_rn(a[i].y, bb[j].x, e);
-            const float s = __fadd_rn(S[i][j], p);
-            const float bp = __fsub_rn(s, S[i][j]);
-            const float err = __fadd_rn(__fsub_rn(S[i][j], __fsub_rn(s, bp)), __fsub_rn(p, bp));
-            S[i][j] = s;
-            E[i][j] = __fadd_rn(E[i][j], __fadd_rn(err, e));
-          }
-      }
-      // exact renormalisation of each pair (Fast2Sum), and every FOLD slabs
-      // a fold into the fp64 total, so that the fp64 pipe stays idle
-      ++slab;
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-          const float s = __fadd_rn(S[i][j], E[i][j]);
-          E[i][j] = __fsub_rn(E[i][j], __fsub_rn(s, S[i][j]));
-          S[i][j] = s;
-          if (slab == FOLD || !more) {
-            tot[i][j] += (double)S[i][j] + (double)E[i][j];
-            S[i][j] = E[i][j] = 0.0f;
-          }
-        }
-      if (slab == FOLD) slab = 0;
-      if (more) {
-        store(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int gi = row0 + ty * TM + i;
-    if (gi >= M) continue;
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int gj = col0 + tx * TN + j;
-      if (gj >= N) continue;
-      double *p = Cb + (long long)gi * ldcb + gj;
-      if (partial) *p = tot[i][j];
-      else *p = (beta != 0.0) ? fma(alpha, tot[i][j], beta * *p) : alpha * tot[i][j];
-    }
-  }
-}
-
-template <class TL, int TA, int TB>
-cudaError_t launch_df64_t(const GemmArgs &g, int ksplit, int kchunk, int b0, int nb, double *work,
-                          cudaStream_t s) {
-  dim3 grid(ceil_div(g.N, TL::BN), ceil_div(g.M, TL::BM), nb * ksplit);
-  const bool part = ksplit > 1;
-  dgemm_df64_kernel<TL, TA, TB><<<grid, TL::NT, 0, s>>>(
-      g.M, g.N, g.K, kchunk, ksplit, g.A + (long long)b0 * g.sA, g.lda, g.sA,
-      g.B + (long long)b0 * g.sB, g.ldb, g.sB, part ? work : g.C + (long long)b0 * g.sC, g.ldc,
-      g.sC, g.alpha, g.beta, part ? 1 : 0);
-  ++launch_counter();
-  RS_TRY(cudaGetLastError());
-  if (part) {
-    const long long total = (long long)g.M * g.N * nb;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
-    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(g.M, g.N, nb, ksplit, work,
-                                                 g.C + (long long)b0 * g.sC, g.ldc, g.sC,
-                                                 g.alpha, g.beta);
-    ++launch_counter();
-    RS_TRY(cudaGetLastError());
-  }
-  return cudaSuccess;
-}
-
-template <class TL>
-cudaError_t launch_df64(const GemmArgs &g, int ks, int kc, int b0, int nb, double *work,
-                        cudaStream_t s) {
-  if (!g.transA && !g.transB) return launch_df64_t<TL, 0, 0>(g, ks, kc, b0, nb, work, s);
-  if (!g.transA && g.transB) return launch_df64_t<TL, 0, 1>(g, ks, kc, b0, nb, work, s);
-  if (g.transA && !g.transB) return launch_df64_t<TL, 1, 0>(g, ks, kc, b0, nb, work, s);
-  return launch_df64_t<TL, 1, 1>(g, ks, kc, b0, nb, work, s);
-}
-
-}  // namespace
-
-cudaError_t dgemm_df64(const GemmArgs &g, double *work, size_t work_elems, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  int ks, kc;
-  split_plan(g, &ks, &kc);
-  if (ks > 1 && work_elems < dgemm_work_elems(g)) return cudaErrorInvalidValue;
-  const int per = std::max(1, 65535 / ks);
-  // 64-wide tiles: each loaded element is split once per tile on the fp64
-  // pipe, so a wide tile keeps that pipe behind the fp32 one (wider 5x5-per-
-  // thread tiles would spill the float pairs and fp64 totals)
-  for (int b0 = 0; b0 < g.batch; b0 += per) {
-    const int nb = std::min(per, g.batch - b0);
-    RS_TRY(launch_df64<T64>(g, ks, kc, b0, nb, work, s));
-  }
-  return cudaSuccess;
-}
-
 }  // namespace rssri

@@ -490,7 +490,9 @@ __global__ void chain_fold_kernel(double *__restrict__ Bm, int npos, int n, doub
   }
 }
 
-__global__ void sigma_accumulate_kernel(const double *__restrict__ BC, int nh, int has_l, long long nn,
+// the kinds of one sample pair are summed first (they cancel to the small
+// stochastic part), then the pairs in order
+__global__ void sigma_accumulate_kernel(const double *__restrict__ BC, int nh, int nkind, long long nn,
                                         double ns_div, const double *__restrict__ base, int init,
                                         double *__restrict__ sig) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
@@ -498,7 +500,7 @@ __global__ void sigma_accumulate_kernel(const double *__restrict__ BC, int nh, i
     double acc = 0.0;
     for (int x = 0; x < nh; ++x) {
       double v = BC[(long long)x * nn + e];
-      if (has_l) v += BC[(long long)(nh + x) * nn + e];
+      for (int k = 1; k < nkind; ++k) v += BC[(long long)(k * nh + x) * nn + e];
       acc += v;
     }
     const double add = acc / ns_div;
@@ -506,13 +508,81 @@ __global__ void sigma_accumulate_kernel(const double *__restrict__ BC, int nh, i
   }
 }
 
+// kinds k < kpos enter with +, the others with -: Tr(F Gb) = 2 t^2 - Tr(B B)
 __global__ void pair_energy_kernel(const double *__restrict__ t, const double *__restrict__ s2,
-                                   int nh, int has_l, double w, double ne, double *__restrict__ e_st) {
+                                   int nh, int nkind, int kpos, double w, double ne,
+                                   double *__restrict__ e_st) {
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nh; x += gridDim.x * blockDim.x) {
-    double de = 2.0 * t[x] * t[x] - s2[x];
-    if (has_l) de -= 2.0 * t[nh + x] * t[nh + x] - s2[nh + x];
+    double de = 0.0;
+    for (int k = 0; k < nkind; ++k) {
+      const double v = 2.0 * t[k * nh + x] * t[k * nh + x] - s2[k * nh + x];
+      de += k < kpos ? v : -v;
+    }
     e_st[x] += -w * de / ne;
   }
+}
+
+// ------------------------------------------- literal estimator (Eq. 25) --
+// out[e][s] = in[s][e] for s < S, e < nn (32 x 32 tiles through shared memory)
+__global__ void lit_qfast_kernel(const double *__restrict__ in, int S, long long nn,
+                                 double *__restrict__ out) {
+  __shared__ double tile[32][33];
+  const long long e0 = (long long)blockIdx.x * 32;
+  const int s0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int sv = s0 + r;
+    const long long e = e0 + tx;
+    tile[r][tx] = (sv < S && e < nn) ? in[(long long)sv * nn + e] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const long long e = e0 + r;
+    const int sv = s0 + tx;
+    if (e < nn && sv < S) out[e * S + sv] = tile[tx][r];
+  }
+}
+
+// W[s][m][j] = -Tk[m][s][j]
+__global__ void lit_w_kernel(const double *__restrict__ Tk, int S, int n, double *__restrict__ W) {
+  const long long total = (long long)S * n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e % n, ms = e / n;  // ms = m * S + s
+    const long long m = ms / S, sv = ms - m * S;
+    W[(sv * n + m) * n + j] = -Tk[e];
+  }
+}
+
+// W[s][prow a][pcol a] += 2 JP[a][s] (each target is written by one thread)
+__global__ void lit_direct_kernel(const double *__restrict__ JP, const int *__restrict__ pij, int P,
+                                  int S, long long nn, double *__restrict__ W) {
+  const long long total = (long long)P * S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long a = e / S, sv = e - a * S;
+    W[sv * nn + pij[a]] += 2.0 * JP[e];
+  }
+}
+
+// Per sample x (one block): z = sum_side sgn(side) Z[side][x], added into the
+// first chain slot, and e_st[x] += -w Tr(z Gb) / ne.  Sides 0 and 2 enter
+// with +, sides 1 and 3 with -.
+__global__ void lit_add_kernel(const double *__restrict__ Z, int cnt, int n,
+                               const double *__restrict__ Gb, double w, double ne,
+                               double *__restrict__ F0, double *__restrict__ e_st) {
+  const int x = blockIdx.x;
+  const long long nn = (long long)n * n;
+  double part = 0.0;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+    const double z = Z[(0LL * cnt + x) * nn + e] - Z[(1LL * cnt + x) * nn + e] +
+                     Z[(2LL * cnt + x) * nn + e] - Z[(3LL * cnt + x) * nn + e];
+    F0[(long long)x * nn + e] += z;
+    const long long i = e / n, j = e - i * n;
+    part += z * Gb[j * n + i];
+  }
+  const double de = block_sum(part);
+  if (threadIdx.x == 0) e_st[x] += -w * de / ne;
 }
 
 // ------------------------------------------------------------------ S9 ----
@@ -787,18 +857,47 @@ cudaError_t chain_fold(double *Bm, int nb, int npos, int n, double *t, double *s
   return cudaSuccess;
 }
 
-cudaError_t sigma_accumulate(const double *BC, int nh, int has_l, int n, double ns_div,
+cudaError_t sigma_accumulate(const double *BC, int nh, int nkind, int n, double ns_div,
                              const double *base, int init, double *sig, cudaStream_t s) {
   const long long nn = (long long)n * n;
-  sigma_accumulate_kernel<<<grid_for(nn, 256), 256, 0, s>>>(BC, nh, has_l, nn, ns_div, base, init,
+  sigma_accumulate_kernel<<<grid_for(nn, 256), 256, 0, s>>>(BC, nh, nkind, nn, ns_div, base, init,
                                                              sig);
   RS_LAUNCHED();
   return cudaSuccess;
 }
 
-cudaError_t pair_energy(const double *t, const double *s2, int nh, int has_l, double w, double ne,
-                        double *e_st, cudaStream_t s) {
-  pair_energy_kernel<<<grid_for(nh, 256), 256, 0, s>>>(t, s2, nh, has_l, w, ne, e_st);
+cudaError_t pair_energy(const double *t, const double *s2, int nh, int nkind, int kpos, double w,
+                        double ne, double *e_st, cudaStream_t s) {
+  pair_energy_kernel<<<grid_for(nh, 256), 256, 0, s>>>(t, s2, nh, nkind, kpos, w, ne, e_st);
+  RS_LAUNCHED();
+  return cudaSuccess;
+}
+
+cudaError_t lit_qfast(const double *in, int S, long long nn, double *out, cudaStream_t s) {
+  if (S <= 0 || nn <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((nn + 31) / 32), (S + 31) / 32);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  lit_qfast_kernel<<<grid, 256, 0, s>>>(in, S, nn, out);
+  RS_LAUNCHED();
+  return cudaSuccess;
+}
+
+cudaError_t lit_w(const double *Tk, int S, int n, const double *JP, const int *pij, int P,
+                  double *W, cudaStream_t s) {
+  const long long total = (long long)S * n * n;
+  lit_w_kernel<<<grid_for(total, 256), 256, 0, s>>>(Tk, S, n, W);
+  RS_LAUNCHED();
+  if (P > 0) {
+    lit_direct_kernel<<<grid_for((long long)P * S, 256), 256, 0, s>>>(JP, pij, P, S,
+                                                                      (long long)n * n, W);
+    RS_LAUNCHED();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t lit_add(const double *Z, int cnt, int n, const double *Gb, double w, double ne,
+                    double *F0, double *e_st, cudaStream_t s) {
+  lit_add_kernel<<<cnt, 256, 0, s>>>(Z, cnt, n, Gb, w, ne, F0, e_st);
   RS_LAUNCHED();
   return cudaSuccess;
 }

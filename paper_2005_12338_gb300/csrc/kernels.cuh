@@ -76,13 +76,22 @@ cudaError_t dd_fold_direct(const int *prow, const int *pcol, const double *L, in
 // B <- sgn (2 t I - B) with sgn = +1 for b < npos, -1 otherwise.
 cudaError_t chain_fold(double *Bm, int nb, int npos, int n, double *t, double *s2,
                        cudaStream_t s);
-// sig[i][j] (+)= sum_x (BC[x][i][j] + BC[nh+x][i][j]) / ns_div (second term if has_l);
+// sig[i][j] (+)= sum_x sum_{k < nkind} BC[k nh + x][i][j] / ns_div;
 // init: sig = base + ..., else sig += ...
-cudaError_t sigma_accumulate(const double *BC, int nh, int has_l, int n, double ns_div,
+cudaError_t sigma_accumulate(const double *BC, int nh, int nkind, int n, double ns_div,
                              const double *base, int init, double *sig, cudaStream_t s);
 // e_st[x] += -w * ((2 t[x]^2 - s2[x]) - (2 t[nh+x]^2 - s2[nh+x])) / ne (second if has_l).
-cudaError_t pair_energy(const double *t, const double *s2, int nh, int has_l, double w, double ne,
-                        double *e_st, cudaStream_t s);
+// e_st[x] += -(w/ne) sum_k (+-)(2 t[k][x]^2 - s2[k][x]), kinds k < kpos with +.
+cudaError_t pair_energy(const double *t, const double *s2, int nh, int nkind, int kpos, double w,
+                        double ne, double *e_st, cudaStream_t s);
+// Literal estimator helpers.  out[e][s] = in[s][e] (e < nn, s < S).
+cudaError_t lit_qfast(const double *in, int S, long long nn, double *out, cudaStream_t s);
+// W[s][m][j] = -Tk[m][s][j] + 2 JP[a][s] at the kept pairs a = (m, j).
+cudaError_t lit_w(const double *Tk, int S, int n, const double *JP, const int *pij, int P,
+                  double *W, cudaStream_t s);
+// F0[x] += Z[0][x] - Z[1][x] + Z[2][x] - Z[3][x]; e_st[x] += -w Tr(that Gb) / ne.
+cudaError_t lit_add(const double *Z, int cnt, int n, const double *Gb, double w, double ne,
+                    double *F0, double *e_st, cudaStream_t s);
 
 // ---------------------------------------------------------------- S9 ------
 // out[t] = sum_ij X[t][i][j] Y[t][j][i]

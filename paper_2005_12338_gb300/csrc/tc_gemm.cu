@@ -1,10 +1,12 @@
-// BF16 x BF16 -> FP32 products on the 5th-generation tensor cores.
+// BF16 x BF16 -> FP32 and TF32 x TF32 -> FP32 products on the 5th-generation
+// tensor cores.
 //
 // One CTA computes a 128 x BN tile (BN <= 256, a multiple of 16) of one
-// output group: warp 0 lane 0 streams A and B slabs (64 bf16 of K per row,
-// 128-byte swizzled) into a ring of shared-memory stages with TMA, warp 1 lane
-// 0 issues tcgen05.mma (kind::f16, M = 128, N = BN, K = 16 per instruction)
-// into an fp32 accumulator in tensor memory and releases each stage with
+// output group: warp 0 lane 0 streams A and B slabs (128 bytes of K per row:
+// 64 bf16 or 32 tf32, 128-byte swizzled) into a ring of shared-memory stages
+// with TMA, warp 1 lane 0 issues tcgen05.mma (kind::f16 with K = 16, or
+// kind::tf32 with K = 8, per instruction: 32 bytes of K either way; M = 128,
+// N = BN) into an fp32 accumulator in tensor memory and releases each stage with
 // tcgen05.commit, and all four warps drain the accumulator with tcgen05.ld
 // (warp w owns TMEM lanes 32w..32w+31, i.e. output rows).  Several batch
 // entries and two K segments can feed one accumulator, which turns sums of
@@ -25,8 +27,17 @@
 namespace rssri {
 namespace {
 
-constexpr int TBM = 128, TBK = 64;  // rows per CTA tile; K per stage (128 B of bf16)
-constexpr int A_STAGE = TBM * TBK * 2;
+constexpr int TBM = 128, SLAB = 128;  // rows per CTA tile; bytes of K per stage and row
+constexpr int A_STAGE = TBM * SLAB;
+
+// Element size and K elements per stage / per instruction of each kind.
+template <int KIND> struct KindT;
+template <> struct KindT<TC_BF16> {
+  static constexpr int ES = 2, TBK = SLAB / 2, KMMA = 16;
+};
+template <> struct KindT<TC_TF32> {
+  static constexpr int ES = 4, TBK = SLAB / 4, KMMA = 8;
+};
 
 struct TcParams {
   CUtensorMap ta[2];
@@ -35,8 +46,8 @@ struct TcParams {
   int nseg, M, N, BN, stages, batch, bpc;
   uint32_t tmem_cols;
   float *c32;
-  __nv_bfloat16 *c16, *c16t;
-  long long ldc16;
+  void *cop;
+  long long ldcop;
   int *err;
 };
 
@@ -86,17 +97,29 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
-// Instruction descriptor: D fp32, A and B bf16, both K-major, M = 128, N = n.
+// Instruction descriptor: D fp32, A and B of the same type (bf16 = 1 under
+// kind::f16, tf32 = 2 under kind::tf32), both K-major, M = 128, N = n.
+template <int KIND>
 __device__ __forceinline__ uint32_t instr_desc(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+  constexpr uint32_t ab = KIND == TC_BF16 ? 1u : 2u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(TBM >> 4) << 24);
 }
 
+// fp32 rounded to the nearest tf32 (10 stored mantissa bits), kept in fp32.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int KIND>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  constexpr int TBK = KindT<KIND>::TBK, KMMA = KindT<KIND>::KMMA;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int BN = p.BN, S = p.stages;
-  const int B_STAGE = BN * TBK * 2;
+  const int B_STAGE = BN * SLAB;
   uint8_t *sA = smem;
   uint8_t *sB = smem + S * A_STAGE;
   uint64_t *full = (uint64_t *)(sB + S * B_STAGE);
@@ -144,7 +167,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
           tma_load3(sB + st * B_STAGE, &p.tb[s], &full[st], k0, n0, b);
         }
   } else if (threadIdx.x == 32) {
-    const uint32_t idesc = instr_desc(BN);
+    const uint32_t idesc = instr_desc<KIND>(BN);
     int it = 0;
     bool ok = true, first = true;
     for (int b = b_lo; b < b_hi && ok; ++b)
@@ -158,14 +181,22 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint64_t da = smem_desc(s_u32(sA + st * A_STAGE));
           const uint64_t db = smem_desc(s_u32(sB + st * B_STAGE));
-          const int nk = min(TBK / 16, (p.K[s] - k0 + 15) / 16);
+          // each instruction takes the next 32 bytes of K: +2 in the
+          // descriptor's 16-byte start-address units
+          const int nk = min(TBK / KMMA, (p.K[s] - k0 + KMMA - 1) / KMMA);
           for (int kk = 0; kk < nk; ++kk) {
             const uint32_t acc = first ? 0u : 1u;
             first = false;
-            asm volatile(
-                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}" ::"r"(tmem),
-                "l"(da + 2 * kk), "l"(db + 2 * kk), "r"(idesc), "r"(acc));
+            if (KIND == TC_BF16)
+              asm volatile(
+                  "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}" ::"r"(tmem),
+                  "l"(da + 2 * kk), "l"(db + 2 * kk), "r"(idesc), "r"(acc));
+            else
+              asm volatile(
+                  "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}" ::"r"(tmem),
+                  "l"(da + 2 * kk), "l"(db + 2 * kk), "r"(idesc), "r"(acc));
           }
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -213,9 +244,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
               if (col0 + j < p.N) dst[j] = __uint_as_float(r[j]);
           }
         }
-        if (p.c16) {
-          __nv_bfloat16 *dst = p.c16 + z * (long long)p.M * p.ldc16 + (long long)row * p.ldc16 + col0;
-          if (full16 && (p.ldc16 % 8) == 0) {
+        if (p.cop && KIND == TC_BF16) {
+          __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(p.cop) + z * (long long)p.M * p.ldcop +
+                               (long long)row * p.ldcop + col0;
+          if (full16 && (p.ldcop % 8) == 0) {
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
               uint4 q;
@@ -234,12 +266,20 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
               if (col0 + j < p.N) dst[j] = __float2bfloat16_rn(__uint_as_float(r[j]));
           }
         }
-        if (p.c16t) {
+        if (p.cop && KIND == TC_TF32) {
+          float *dst = static_cast<float *>(p.cop) + z * (long long)p.M * p.ldcop +
+                       (long long)row * p.ldcop + col0;
+          if (full16 && (p.ldcop % 4) == 0) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (col0 + j < p.N)
-              p.c16t[z * MN + (long long)(col0 + j) * p.M + row] =
-                  __float2bfloat16_rn(__uint_as_float(r[j]));
+            for (int v = 0; v < 4; ++v)
+              reinterpret_cast<float4 *>(dst)[v] = make_float4(
+                  round_tf32(__uint_as_float(r[4 * v])), round_tf32(__uint_as_float(r[4 * v + 1])),
+                  round_tf32(__uint_as_float(r[4 * v + 2])), round_tf32(__uint_as_float(r[4 * v + 3])));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (col0 + j < p.N) dst[j] = round_tf32(__uint_as_float(r[j]));
+          }
         }
       }
     }
@@ -263,15 +303,20 @@ void load_encode() {
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
 }
 
-cudaError_t make_map(CUtensorMap *m, const TcOperand &op, int K, int batch, int box_rows) {
+cudaError_t make_map(CUtensorMap *m, int kind, const TcOperand &op, int K, int batch,
+                     int box_rows) {
   if (!g_encode) return cudaErrorNotSupported;
-  if ((op.ld % 8) || (op.sb % 8) || ((uintptr_t)op.ptr % 16)) return cudaErrorInvalidValue;
+  const int es_bytes = kind == TC_BF16 ? 2 : 4;
+  const int per16 = 16 / es_bytes;  // elements per 16 bytes
+  if ((op.ld % per16) || (op.sb % per16) || ((uintptr_t)op.ptr % 16)) return cudaErrorInvalidValue;
   const long long sb = op.sb ? op.sb : op.ld * op.rows;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)op.rows, (cuuint64_t)batch};
-  cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)sb * 2};
-  cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)op.ld * es_bytes, (cuuint64_t)sb * es_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)(SLAB / es_bytes), (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(op.ptr),
+  const CUresult r = g_encode(m, kind == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              3, const_cast<void *>(op.ptr),
                               dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -295,9 +340,11 @@ cudaError_t tc_prepare() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
   if (!done[dev]) {
-    const int smem = 1024 + 4 * (A_STAGE + 256 * TBK * 2) + 256;
-    RS_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem));
+    const int smem = 1024 + 4 * (A_STAGE + 256 * SLAB) + 256;
+    RS_TRY(cudaFuncSetAttribute(tc_gemm_kernel<TC_BF16>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RS_TRY(cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     done[dev] = true;
   }
   return cudaSuccess;
@@ -305,8 +352,10 @@ cudaError_t tc_prepare() {
 
 cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s) {
   if (!tc_available()) return cudaErrorNotSupported;
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0 || g.nseg < 1 || g.nseg > 2 || g.bpc < 1)
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0 || g.nseg < 1 || g.nseg > 2 || g.bpc < 1 ||
+      (g.kind != TC_BF16 && g.kind != TC_TF32))
     return cudaErrorInvalidValue;
+  const int tbk = g.kind == TC_BF16 ? KindT<TC_BF16>::TBK : KindT<TC_TF32>::TBK;
   TcParams p;
   std::memset(&p, 0, sizeof(p));
   // N tile: <= 256, a multiple of 16, with the least padding
@@ -315,10 +364,10 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s) {
   long long iters = 0;
   for (int s2 = 0; s2 < g.nseg; ++s2) {
     if (g.K[s2] <= 0) return cudaErrorInvalidValue;
-    RS_TRY(make_map(&p.ta[s2], g.A[s2], g.K[s2], g.batch, TBM));
-    RS_TRY(make_map(&p.tb[s2], g.B[s2], g.K[s2], g.batch, BN));
+    RS_TRY(make_map(&p.ta[s2], g.kind, g.A[s2], g.K[s2], g.batch, TBM));
+    RS_TRY(make_map(&p.tb[s2], g.kind, g.B[s2], g.K[s2], g.batch, BN));
     p.K[s2] = g.K[s2];
-    iters += ceil_div(g.K[s2], TBK);
+    iters += ceil_div(g.K[s2], tbk);
   }
   iters *= g.bpc;
   p.nseg = g.nseg;
@@ -331,11 +380,10 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s) {
   p.bpc = g.bpc;
   p.tmem_cols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   p.c32 = g.c32;
-  p.c16 = g.c16;
-  p.c16t = g.c16t;
-  p.ldc16 = g.ldc16 ? g.ldc16 : g.N;
+  p.cop = g.cop;
+  p.ldcop = g.ldcop ? g.ldcop : g.N;
   p.err = g.err;
-  size_t smem = 1024 + (size_t)p.stages * (A_STAGE + BN * TBK * 2) + 256;
+  size_t smem = 1024 + (size_t)p.stages * (A_STAGE + BN * SLAB) + 256;
   // at most two CTAs per SM, so that their tensor memory (<= 2 x 256 columns) always fits
   smem = std::max<size_t>(smem, 80 * 1024);
   RS_TRY(tc_prepare());
@@ -345,7 +393,8 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s) {
     const int nz = std::min(65535, groups - z0);
     if (z0 > 0) return cudaErrorInvalidValue;  // not needed by the path's shapes
     dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, TBM), nz);
-    tc_gemm_kernel<<<grid, 128, smem, s>>>(p);
+    if (g.kind == TC_BF16) tc_gemm_kernel<TC_BF16><<<grid, 128, smem, s>>>(p);
+    else tc_gemm_kernel<TC_TF32><<<grid, 128, smem, s>>>(p);
     ++launch_counter();
     RS_TRY(cudaGetLastError());
   }

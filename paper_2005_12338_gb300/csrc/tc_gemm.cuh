@@ -1,5 +1,6 @@
-// BF16 tensor-core products (tcgen05, TMA, TMEM) for the reduced-precision
-// chain of the stochastic part (Sec. III, Eq. 25 split by Eqs. 14-15).
+// BF16 and TF32 tensor-core products (tcgen05, TMA, TMEM) for the
+// reduced-precision chain of the stochastic part (Sec. III, Eq. 25 split by
+// Eqs. 14-15).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -8,27 +9,34 @@
 
 namespace rssri {
 
-// One K segment of a product: A[b] is M x K and B[b] is N x K, both bf16
-// with K contiguous (row stride ld, batch stride sb, in elements; strides must
-// be multiples of 8 elements so that every TMA row starts on 16 bytes).
+// Operand kinds: bf16 (kind::f16) or fp32 storage read as tf32 (kind::tf32;
+// values should already be rounded to tf32, the tensor core drops the low
+// mantissa bits).
+enum TcKind { TC_BF16 = 0, TC_TF32 = 1 };
+
+// One K segment of a product: A[b] is M x K and B[b] is N x K, both of the
+// product's kind with K contiguous (row stride ld, batch stride sb, in
+// elements; strides must be multiples of 16 bytes so that every TMA row starts
+// on a 16-byte boundary).
 struct TcOperand {
-  const __nv_bfloat16 *ptr = nullptr;
+  const void *ptr = nullptr;
   long long ld = 0, sb = 0;
   int rows = 0;
 };
 
 // out[z] = sum_{b in group z} sum_{s < nseg} A_s[b] B_s[b]^T, where the batch
 // entries are taken bpc at a time (one group per z, reduced in the tensor
-// memory accumulator in a fixed order).  Outputs (any may be null):
-//   c32 [z][M][N] fp32 (ld = N, stride M*N), c16 [z][M][ldc16] bf16
-//   (ldc16 = 0 means N), c16t [z][N][M] bf16 (the transpose).
+// memory accumulator in a fixed order).  Outputs (either may be null):
+//   c32 [z][M][N] fp32 (ld = N, stride M*N); cop [z][M][ldcop] in the operand
+//   type (bf16, or fp32 rounded to tf32), ldcop = 0 meaning N.
 struct TcGemm {
+  int kind = TC_BF16;
   int M = 0, N = 0, batch = 1, bpc = 1, nseg = 1;
   TcOperand A[2], B[2];
   int K[2] = {0, 0};
   float *c32 = nullptr;
-  __nv_bfloat16 *c16 = nullptr, *c16t = nullptr;
-  long long ldc16 = 0;
+  void *cop = nullptr;
+  long long ldcop = 0;
   int *err = nullptr;  // device flag, set non-zero if a bounded wait gives up
 };
 
