@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--eps", type=float, default=None,
                     help="override the K^L cut eps of the workload (e.g. the paper's 0.1)")
+    ap.add_argument("--n-tau", type=int, default=None,
+                    help="override the number of tau points of the workload (for one-off "
+                         "measurements on the largest workload; not the benchmark line)")
     ap.add_argument("--cv", action="store_true",
                     help="also train the learned control variate on an independent run and "
                          "report its estimate (fp64 chain)")
@@ -295,6 +298,8 @@ def our_arm(args):
     cfg = dict(synth.CONFIGS[args.workload])
     if args.eps is not None:
         cfg["eps"] = args.eps
+    if args.n_tau is not None:
+        cfg["n_tau"] = args.n_tau
     s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
     n, nt, ns = s.n, s.n_tau, cfg["n_s"]
     host = [s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w]

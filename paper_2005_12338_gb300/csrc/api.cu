@@ -1084,10 +1084,12 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     if (o->dd_arith == RSSRI_DD_DF64) RS_CK(ensure(h->litMhl, (size_t)nbat2 * nn * sizeof(float2)));
   }
   if (P > 0) {
-    RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
-    RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
+    if (o->dd_arith != RSSRI_DD_DF64) {  // the double-float block keeps these as pairs
+      RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
+    }
     RS_CK(ensure(h->T, (size_t)nn * na * sizeof(double)));
-    RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
     RS_CK(ensure(h->L, (size_t)P * na * sizeof(double)));
     RS_CK(ensure(h->Gam, (size_t)na * na * sizeof(double)));
     RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));

@@ -35,17 +35,17 @@ __global__ void to_df64_kernel(const double *__restrict__ x, long long len, floa
 
 // T[m][q][j] = sum_{a in row m} sum_{b in row j} D[a][b] At[(col a, col b)][q]
 //
-// One warp per (row m, group of 4 consecutive rows j, chunk of 64 aux
-// indices q; lane t owns q0 + 2t and q0 + 2t + 1).  For each pair a = (m, k)
+// One warp per (row m, group of 4 consecutive rows j, chunk of 128 aux
+// indices q; lane t owns q0 + 4t .. q0 + 4t + 3).  For each pair a = (m, k)
 // of row m and each window of SLR = 64 columns l covering the group's pairs,
 // the warp writes its rows' v^L entries D[a][(j, l)] into a dense 4 x SLR table
 // in shared memory (zero where (j, l) is not a kept pair) and then runs over
-// the columns the group actually holds: per column one 16-byte load of
-// At[k][l][q-pair] feeds 8 multiply-adds (4 rows x 2 aux indices).  The D
-// entries of the next (pair, window) are loaded into registers before the
-// current one is computed and the table is double-buffered, so a warp never
-// waits on another warp and global latency hides behind the arithmetic.
-constexpr int SLR = 64, SQW = 64, SWARPS = 4, SREG = 6;  // SREG x 8 entries per row in registers
+// the columns the group actually holds, two at a time: per column two 16-byte
+// loads of At[k][l][4 aux] feed 16 multiply-adds (4 rows x 4 aux indices).
+// The D entries of the next (pair, window) are loaded into registers before
+// the current one is computed and the table is double-buffered, so a warp
+// never waits on another warp and global latency hides behind the arithmetic.
+constexpr int SLR = 64, SQW = 128, SWARPS = 4, SREG = 6;  // SREG x 8 entries per row in registers
 
 __device__ __forceinline__ void df_mac2(float &S, float &E, float2 d, float xh, float xl) {
   // TwoProduct of the high parts plus the cross terms, then TwoSum S + p
@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     const int *__restrict__ rowptr, const int *__restrict__ pcol, const float2 *__restrict__ D,
     int P, const float2 *__restrict__ At, int n, int naux, double *__restrict__ T) {
   __shared__ float2 Dt[SWARPS][2][4][SLR];
+  // running pair totals (TH, TL) of the 16 outputs of each thread, touched
+  // once every 4 pairs: kept in shared memory ([output][thread], conflict-free)
+  __shared__ float2 Tot[16][32 * SWARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j0 = (blockIdx.x * SWARPS + warp) * 4, m = blockIdx.y, q0 = blockIdx.z * SQW;
   if (j0 >= n) return;  // whole warp
@@ -126,14 +129,30 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     __syncwarp();
   };
 
-  float TH[4][2], TL[4][2], S[4][2], E[4][2];
+  float S[4][4], E[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) TH[r][c] = TL[r][c] = S[r][c] = E[r][c] = 0.0f;
-  const int q = q0 + 2 * lane;
-  const bool q_ok0 = q < naux, q_ok1 = q + 1 < naux;
-  const bool vec = (naux % 2) == 0 && q_ok1;  // 16-byte aligned pair of pairs
+    for (int c = 0; c < 4; ++c) {
+      S[r][c] = E[r][c] = 0.0f;
+      Tot[r * 4 + c][threadIdx.x] = make_float2(0.f, 0.f);
+    }
+  const int q = q0 + 4 * lane;
+  const int nq = max(0, min(4, naux - q));  // valid aux indices of this lane
+  const bool vec = (naux % 2) == 0 && nq == 4;  // two 16-byte aligned loads
+  auto load4 = [&](const float2 *ap, float2 (&x)[4]) {
+    if (vec) {
+      const float4 u = __ldg(reinterpret_cast<const float4 *>(ap));
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(ap + 2));
+      x[0] = make_float2(u.x, u.y);
+      x[1] = make_float2(u.z, u.w);
+      x[2] = make_float2(v.x, v.y);
+      x[3] = make_float2(v.z, v.w);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = c < nq ? __ldg(ap + c) : make_float2(0.f, 0.f);
+    }
+  };
   if (nstage > 0) {
     prefetch(0);
     fill(0, 0);
@@ -143,30 +162,32 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     if (st + 1 < nstage) prefetch(st + 1);
     const int a = a0 + st / nwin, lc = lo + (st % nwin) * SLR;
     const int lb = max(lo, lc), le = min(hi, lc + SLR - 1);
-    const float2 *Ak = At + (long long)pcol[a] * n * naux + q;
+    // local column index li = l - lc in [0, SLR)
+    const float2 *Ak = At + ((long long)pcol[a] * n + lc) * naux + q;
     const float2 *Dw = &Dt[warp][buf][0][0];
-    for (int l = lb; l <= le; ++l) {
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float2 *ap = Ak + (long long)l * naux;
-      if (vec) {
-        x = __ldg(reinterpret_cast<const float4 *>(ap));
-      } else {
-        if (q_ok0) {
-          const float2 v = __ldg(ap);
-          x.x = v.x;
-          x.y = v.y;
-        }
-        if (q_ok1) {
-          const float2 v = __ldg(ap + 1);
-          x.z = v.x;
-          x.w = v.y;
-        }
-      }
+    const int le_i = le - lc;
+    int li = lb - lc;
+    for (; li < le_i; li += 2) {
+      float2 xa[4], xb[4];
+      load4(Ak + (long long)li * naux, xa);
+      load4(Ak + (long long)(li + 1) * naux, xb);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const float2 d = Dw[r * SLR + (l - lc)];
-        df_mac2(S[r][0], E[r][0], d, x.x, x.y);
-        df_mac2(S[r][1], E[r][1], d, x.z, x.w);
+        const float2 da = Dw[r * SLR + li], db = Dw[r * SLR + li + 1];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], da, xa[c].x, xa[c].y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], db, xb[c].x, xb[c].y);
+      }
+    }
+    if (li == le_i) {
+      float2 xa[4];
+      load4(Ak + (long long)li * naux, xa);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float2 da = Dw[r * SLR + li];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], da, xa[c].x, xa[c].y);
       }
     }
     // after the last window of a pair: exact renormalisation (Fast2Sum);
@@ -177,12 +198,14 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < 4; ++c) {
           const float sn = __fadd_rn(S[r][c], E[r][c]);
           E[r][c] = __fsub_rn(E[r][c], __fsub_rn(sn, S[r][c]));
           S[r][c] = sn;
           if (fold) {
-            df_acc(TH[r][c], TL[r][c], S[r][c], E[r][c]);
+            float2 t = Tot[r * 4 + c][threadIdx.x];
+            df_acc(t.x, t.y, S[r][c], E[r][c]);
+            Tot[r * 4 + c][threadIdx.x] = t;
             S[r][c] = E[r][c] = 0.0f;
           }
         }
@@ -190,14 +213,15 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     if (st + 1 < nstage) fill(st + 1, buf ^ 1);
   }
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < 4; ++c) {
     const int qc = q + c;
     if (qc >= naux) continue;
     double *out = T + ((long long)m * naux + qc) * n;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int j = j0 + r;
-      if (j < j1) out[j] = (double)TH[r][c] + (double)TL[r][c];
+      const float2 t = Tot[r * 4 + c][threadIdx.x];
+      if (j < j1) out[j] = (double)t.x + (double)t.y;
     }
   }
 }

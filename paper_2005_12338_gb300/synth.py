@@ -73,7 +73,8 @@ def make_system(n: int, n_occ: int, n_aux: int, n_tau: int, input_seed: int = 0,
     g[ju, iu, :] = g[iu, ju, :]
     idx = np.arange(n)
     damp = np.exp(-np.abs(idx[:, None] - idx[None, :]) / decay) / np.sqrt(n_aux)
-    eri3 = np.ascontiguousarray(g * damp[:, :, None])
+    g *= damp[:, :, None]  # in place: one [n][n][n_aux] array on the host at a time
+    eri3 = g
     # SPD metric
     b = rng.standard_normal((n_aux, n_aux))
     metric = b @ b.T / n_aux + 0.5 * np.eye(n_aux)
