@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--literal", action="store_true",
                     help="also run the literal Eq. 25 estimator (fp64 chain, exact-D cross "
                          "terms) on the first timed seed and report its cost and stderr")
+    ap.add_argument("--many", type=int, default=0,
+                    help="also time K independent chains of uneven size (N from 64 to 256) "
+                         "one by one and batched on K streams (rssri_sigma_batch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -285,6 +288,52 @@ def traffic_for(key):
     return d["bytes_per_launch"] if sha == d.get("source_sha") else None
 
 
+def many_systems(args, binding, torch, prec, dd):
+    """K independent chains of uneven size, each with its own handle and
+    stream: the sampling calls (S4-S10) timed one after another and then all
+    enqueued at once through rssri_sigma_batch.  Setups are done beforehand."""
+    m = dict(synth.MANY, k=args.many)
+    sizes = synth.many_sizes(m["k"], m["n_min"], m["n_max"])
+    hs, outs, units = [], [], 0
+    opts = binding.Handle.options(m["eps_prime"], m["eps"], m["n_s"], 5, precision=prec,
+                                  dd_arith=dd)
+    for k, n in enumerate(sizes):
+        s = synth.make_system(n, n // 2, 3 * n, m["n_tau"], input_seed=k)
+        st = torch.cuda.Stream()
+        h = binding.Handle(torch.cuda.current_device(), stream=st.cuda_stream)
+        dev = [torch.from_numpy(a).cuda() for a in (s.eri3, s.metric, s.orb_e, s.orb_c, s.tau,
+                                                     s.tau_w)]
+        torch.cuda.synchronize()
+        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=opts)
+        hs.append((h, dev, st))
+        outs.append(torch.empty((m["n_tau"], n, n), dtype=torch.float64, device="cuda"))
+        units += m["n_s"] * m["n_tau"]
+
+    def one_by_one():
+        for (h, _, _), o in zip(hs, outs):
+            h.sigma(opts, o)
+
+    def batched():
+        binding.sigma_batch([x[0] for x in hs], opts, outs)
+
+    res = {}
+    for name, fn in (("one_by_one", one_by_one), ("batched", batched)):
+        fn()  # warm-up: autotuning, graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        res[name] = {"s_per_pass": dt, "units_per_s": units / dt}
+    for h, _, _ in hs:
+        h.close()
+    return {"chains": len(sizes), "n": sizes, "n_tau": m["n_tau"], "n_s": m["n_s"],
+            "timed": "rssri_sigma (S4-S10) of every chain, host wall clock, setups excluded",
+            **res, "speedup": res["one_by_one"]["s_per_pass"] / res["batched"]["s_per_pass"]}
+
+
 def our_arm(args):
     import torch
     import torch.distributed as dist
@@ -314,9 +363,11 @@ def our_arm(args):
     tensor_chain = args.precision in ("bf16", "tf32")
     dd = binding.RSSRI_DD_DF64 if args.dd == "df64" else binding.RSSRI_DD_FP64
 
-    def step(seed, profile=0, precision=prec, dd_arith=dd, estimator=binding.RSSRI_EST_CV):
+    def step(seed, profile=0, precision=prec, dd_arith=dd, estimator=binding.RSSRI_EST_CV,
+             pair_batch=0):
         o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, profile=profile,
-                                   precision=precision, dd_arith=dd_arith, estimator=estimator)
+                                   precision=precision, dd_arith=dd_arith, estimator=estimator,
+                                   pair_batch=pair_batch)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
         return h.sigma(o, sig, ep)
 
@@ -357,7 +408,10 @@ def our_arm(args):
 
     # the plain fp64 form on the same seed: throughput and the error of the chosen form
     compare = None
-    plain = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=binding.RSSRI_DD_FP64)
+    # (on the largest workloads the fp64 chain takes its pairs 100 at a time to
+    # bound its scratch; the sums are the same up to rounding order)
+    plain = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=binding.RSSRI_DD_FP64,
+                 pair_batch=100 if n >= 500 else 0)
     if (tensor_chain or args.dd == "df64") and not args.no_fp64_compare:
         step(replicas.rank_seed(rank, 990_001), **plain)  # tunes the fp64 chain shapes
         torch.cuda.synchronize()
@@ -414,6 +468,8 @@ def our_arm(args):
         cv_report = {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
                      "e_corr_plain": e_cv, "stderr_plain": se_cv, "e_corr_learned": e_l,
                      "stderr_learned": se_l, "stderr_ratio_plain_over_learned": se_cv / se_l}
+
+    many_report = many_systems(args, binding, torch, prec, dd) if args.many > 0 else None
 
     # the literal reading of Eq. 25 on the same draws as the first timed step
     literal_report = None
@@ -519,7 +575,8 @@ def our_arm(args):
                       "classes": classes, "tensor_roofline": tensor,
                       "chosen_vs_plain_fp64": compare, "rs_vs_sri_same_n_s": rs_vs_sri,
                       "learned_control_variate": cv_report,
-                      "literal_estimator": literal_report}}
+                      "literal_estimator": literal_report,
+                      "many_systems": many_report}}
     if not args.no_cpu_baseline and world == 1:
         cb = oracle_sample(s, cfg, 0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -269,6 +269,28 @@ RSSRI_API int rssri_sigma_from_g(rssri_handle *h, const rssri_options *o,
                        double *e_pair, double *e_corr, double *e_stderr,
                        rssri_stats *st);
 
+/* Asynchronous form of rssri_sigma: enqueues the same work on the handle's
+ * stream and returns without waiting for it.  sigma (required) and e_pair
+ * (optional) must stay valid until rssri_sigma_wait returns; host arrays are
+ * copied asynchronously only if they are pinned.  At most one call may be
+ * pending per handle; until it has been waited for, the handle accepts no
+ * other call except rssri_destroy (which waits).  The energies, statistics
+ * and any error of the enqueued work are returned by rssri_sigma_wait. */
+RSSRI_API int rssri_sigma_async(rssri_handle *h, const rssri_options *o, double *sigma,
+                                double *e_pair);
+RSSRI_API int rssri_sigma_wait(rssri_handle *h, double *e_corr, double *e_stderr,
+                               rssri_stats *st);
+
+/* Many independent systems at once: rssri_sigma on count distinct handles
+ * (each set up beforehand, each on its own stream so that their work can
+ * overlap on the device) with the same options.  All calls are enqueued
+ * before any is waited for.  sigma[i], e_pair[i] (e_pair may be NULL),
+ * e_corr[i] and e_stderr[i] (either may be NULL) belong to hs[i].  Returns
+ * the first error; every call that was enqueued is waited for. */
+RSSRI_API int rssri_sigma_batch(rssri_handle *const *hs, int count, const rssri_options *o,
+                                double *const *sigma, double *const *e_pair, double *e_corr,
+                                double *e_stderr);
+
 /* ------------------------------------------------------- intermediates */
 
 /* Intermediates kept on the device after setup / sigma, for inspection. */

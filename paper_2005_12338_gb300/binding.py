@@ -78,6 +78,13 @@ SIGNATURES = {
                                      C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(rssri_stats)]),
+    "rssri_sigma_async": (C.c_int, [C.c_void_p, C.POINTER(rssri_options), C.c_void_p,
+                                    C.c_void_p]),
+    "rssri_sigma_wait": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(rssri_stats)]),
+    "rssri_sigma_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(rssri_options),
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "rssri_buffer_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
     "rssri_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
     "rssri_energy_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
@@ -148,6 +155,7 @@ class Handle:
         self.device = device
         check(lib().rssri_create(C.byref(self._h), device, C.c_void_p(stream)), "rssri_create")
         self._keep = None
+        self._pending = None
         self.kind = RSSRI_PTR_DEVICE
         self.n = self.n_tau = self.n_aux = 0
 
@@ -201,6 +209,20 @@ class Handle:
             check(rc, "rssri_sigma_from_g")
         return e.value, se.value, st.as_dict()
 
+    def sigma_async(self, opts: rssri_options, sigma_out, e_pair_out=None):
+        """rssri_sigma_async: enqueue and return; keep the outputs alive until sigma_wait."""
+        self._pending = (opts, sigma_out, e_pair_out)
+        check(lib().rssri_sigma_async(self._h, C.byref(opts), _ptr(sigma_out),
+                                      _ptr(e_pair_out)), "rssri_sigma_async")
+
+    def sigma_wait(self):
+        """rssri_sigma_wait; returns (e_corr, e_stderr, stats dict)."""
+        e, se, st = C.c_double(), C.c_double(), rssri_stats()
+        rc = lib().rssri_sigma_wait(self._h, C.byref(e), C.byref(se), C.byref(st))
+        self._pending = None
+        check(rc, "rssri_sigma_wait")
+        return e.value, se.value, st.as_dict()
+
     def cv_train(self, opts: rssri_options, init_params: np.ndarray, steps: int, batch: int,
                  lr: float):
         """rssri_cv_train; returns (loss_before, loss_after)."""
@@ -246,3 +268,16 @@ class Handle:
         check(lib().rssri_export(self._h, which, out.ctypes.data, nb.value, RSSRI_PTR_HOST),
               "rssri_export")
         return out
+
+
+def sigma_batch(handles, opts: rssri_options, sigmas, e_pairs=None):
+    """rssri_sigma_batch over handles (each set up, each on its own stream);
+    returns ([e_corr], [e_stderr])."""
+    k = len(handles)
+    hs = (C.c_void_p * k)(*[h._h.value for h in handles])
+    sg = (C.c_void_p * k)(*[_ptr(x) for x in sigmas])
+    ep = (C.c_void_p * k)(*[_ptr(x) for x in e_pairs]) if e_pairs is not None else None
+    e = (C.c_double * k)()
+    se = (C.c_double * k)()
+    check(lib().rssri_sigma_batch(hs, k, C.byref(opts), sg, ep, e, se), "rssri_sigma_batch")
+    return list(e), list(se)

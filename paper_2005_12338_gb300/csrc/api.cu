@@ -51,6 +51,11 @@ struct rssri_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev[6] = {};
+  // results of an enqueued sigma call, copied into pinned host memory:
+  // [0..3] the energy scalars, then the tensor-core timeout flag
+  double *host_res = nullptr;
+  bool pending = false, pending_tc = false;
+  int pending_ns = 0;
   bool ready = false;
   bool broken = false;
 
@@ -84,6 +89,8 @@ struct rssri_handle {
   DevBuf Dhl, Ahl, KPhl, PGhl, APhl, Gamhl, GGhl;
   // literal estimator: pair gathers / J, aux traces, pair form of the batch
   DevBuf litMP, litT, litMhl;
+  // pairs of (ij|A) and of U^T / theta for the double-float factor products
+  DevBuf eri_hl, ut_hl;
   bool d_df64_ready = false;
   // bf16 chain buffers
   DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
@@ -340,6 +347,7 @@ int rssri_create(rssri_handle **out, int device, void *stream) {
   cudaError_t e = ensure(h->scal, 64 * sizeof(double));
   if (e == cudaSuccess) e = ensure(h->part, 8192 * sizeof(double));
   if (e == cudaSuccess) e = ensure(h->flags, 16 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->host_res, 8 * sizeof(double));
   if (e != cudaSuccess) {
     rssri_destroy(h);
     return map_err(e);
@@ -362,7 +370,7 @@ void rssri_destroy(rssri_handle *h) {
                     &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
                     &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
                     &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
-                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
+                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
                     &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss};
   for (DevBuf *b : bufs) release(*b);
@@ -371,11 +379,12 @@ void rssri_destroy(rssri_handle *h) {
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->chain_graph) cudaGraphExecDestroy(h->chain_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->host_res) cudaFreeHost(h->host_res);
   delete h;
 }
 
 int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o) {
-  if (!h) return RSSRI_ERR_INVALID_ARG;
+  if (!h || h->pending) return RSSRI_ERR_INVALID_ARG;
   if (h->broken) return RSSRI_ERR_CUDA;
   int rc = validate_problem(p);
   if (rc) return rc;
@@ -1008,12 +1017,14 @@ cudaError_t literal_cross(rssri_handle *h, const rssri_options *o, int t, int x0
                  h->e_st.as<double>() + x0, s);
 }
 
-int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const double *gb_in,
-              double *sigma, double *e_pair, double *e_corr, double *e_stderr, rssri_stats *st,
-              bool collect_stats = false) {
+// Enqueues S4-S10 on the handle's stream; the energies and the tensor-core
+// flag are copied into the handle's pinned host buffer, read by finish_sigma.
+int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const double *gb_in,
+                double *sigma, double *e_pair, bool collect_stats) {
   if (!h) return RSSRI_ERR_INVALID_ARG;
   if (h->broken) return RSSRI_ERR_CUDA;
   if (!h->ready) return RSSRI_ERR_NOT_READY;
+  if (h->pending) return RSSRI_ERR_INVALID_ARG;  // one enqueued call per handle
   int rc = validate_options(o, true);
   if (rc) return rc;
   if (!sigma && !collect_stats) return RSSRI_ERR_INVALID_ARG;
@@ -1150,7 +1161,24 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     RS_CK(gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
   }
   // ---- S5: R[set][xi][ij] = sum_A U^T[xi][A] (ij|A); R^L from the kept pairs
-  {
+  // (in double-float when the block is: the operands split into pairs first)
+  const bool fac_df64 = o->dd_arith == RSSRI_DD_DF64;
+  if (fac_df64) {
+    RS_CK(ensure(h->eri_hl, (size_t)nn * na * sizeof(float2)));
+    RS_CK(ensure(h->ut_hl, (size_t)2 * ns * na * sizeof(float2)));
+    {
+      SPAN(RSSRI_PROF_OTHER, 0.0);
+      RS_CK(to_df64(h->eri3, nn * na, h->eri_hl.as<float2>(), s));
+      RS_CK(to_df64(Ut, 2LL * ns * na, h->ut_hl.as<float2>(), s));
+    }
+    SPAN(RSSRI_PROF_FACTOR_GEMM, 2.0 * 2 * ns * (double)nn * na * 1e-9);
+    DfGemm g;
+    g.M = ns; g.N = (int)nn; g.K = na; g.batch = 2;
+    g.A = h->ut_hl.as<float2>(); g.lda = na; g.sA = (long long)ns * na;
+    g.B = h->eri_hl.as<float2>(); g.ldb = na; g.transB = 1; g.sB = 0;
+    g.C64 = fac; g.ldc = nn; g.sC = 2LL * ns * nn;  // kind 0 of each set
+    RS_CK(df_gemm(g, nullptr, 0, s));
+  } else {
     GemmArgs g;
     g.M = ns; g.N = (int)nn; g.K = na; g.batch = 2;
     g.A = Ut; g.lda = na; g.sA = (long long)ns * na;
@@ -1162,13 +1190,25 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
     double *rl = fac + (2LL * set + 1) * ns * nn;
     RS_CK(cudaMemsetAsync(rl, 0, (size_t)ns * nn * sizeof(double), s));
   }
-  if (P > 0) {
+  if (P > 0 && fac_df64) {
+    // theta is +-1, exact as a pair; K_P was split at setup
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(theta, 2LL * ns * na, h->ut_hl.as<float2>(), s)); }
+    SPAN(RSSRI_PROF_FACTOR_GEMM, 2.0 * 2 * ns * (double)P * na * 1e-9);
+    DfGemm g;
+    g.M = ns; g.N = P; g.K = na; g.batch = 2;
+    g.A = h->ut_hl.as<float2>(); g.lda = na; g.sA = (long long)ns * na;
+    g.B = h->KPhl.as<float2>(); g.ldb = na; g.transB = 1; g.sB = 0;
+    g.C64 = h->RLp.as<double>(); g.ldc = P; g.sC = (long long)ns * P;
+    RS_CK(df_gemm(g, nullptr, 0, s));
+  } else if (P > 0) {
     GemmArgs g;
     g.M = ns; g.N = P; g.K = na; g.batch = 2;
     g.A = theta; g.lda = na; g.sA = (long long)ns * na;
     g.B = h->KP.as<double>(); g.ldb = na; g.transB = 1; g.sB = 0;
     g.C = h->RLp.as<double>(); g.ldc = P; g.sC = (long long)ns * P;
     RS_CK(gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
+  }
+  if (P > 0) {
     for (int set = 0; set < 2; ++set)
       { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(scatter_pairs(h->RLp.as<double>() + (long long)set * ns * P, ns, P, h->pij.as<int>(),
                           nn, nn, fac + (2LL * set + 1) * ns * nn, s)); }
@@ -1265,13 +1305,32 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   if (sigma) RS_CK(cudaMemcpyAsync(sigma, h->sig_out.p, nt * nn * sizeof(double), dk, s));
   if (e_pair) RS_CK(cudaMemcpyAsync(e_pair, h->e_pair.p, ns * sizeof(double), dk, s));
   RS_CK(cudaEventRecord(h->ev[4], s));
-  double res[4];
-  int tc_flag = 0;
-  RS_CK(cudaMemcpyAsync(res, h->res.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  RS_CK(cudaMemcpyAsync(&tc_flag, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  RS_CK(cudaStreamSynchronize(s));
-  if (bf16 && tc_flag) return RSSRI_ERR_TIMEOUT;
-  h->last_ns = ns;
+  RS_CK(cudaMemcpyAsync(h->host_res, h->res.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RS_CK(cudaMemcpyAsync(reinterpret_cast<int *>(h->host_res + 4), tc_err, sizeof(int),
+                        cudaMemcpyDeviceToHost, s));
+  RS_CK(cudaEventRecord(h->ev[5], s));
+  h->pending = true;
+  h->pending_tc = bf16;
+  h->pending_ns = ns;
+  return RSSRI_OK;
+#undef RS_CK
+}
+
+// Waits for the enqueued call and returns its energies and statistics.
+int finish_sigma(rssri_handle *h, double *e_corr, double *e_stderr, rssri_stats *st) {
+  if (!h || !h->pending) return RSSRI_ERR_INVALID_ARG;
+  h->pending = false;
+  if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  const cudaError_t e = cudaEventSynchronize(h->ev[5]);
+  if (e != cudaSuccess) {
+    const int r = map_err(e);
+    if (r == RSSRI_ERR_CUDA) h->broken = true;
+    return r;
+  }
+  const double *res = h->host_res;
+  const int tc_flag = *reinterpret_cast<const int *>(h->host_res + 4);
+  if (h->pending_tc && tc_flag) return RSSRI_ERR_TIMEOUT;
+  h->last_ns = h->pending_ns;
   h->have_sigma = true;
   float t_dd = 0, t_samp = 0;
   cudaEventElapsedTime(&t_dd, h->ev[2], h->ev[3]);
@@ -1305,7 +1364,14 @@ int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const
   if (st) *st = S;
   if (!std::isfinite(res[1]) || !std::isfinite(res[3])) return RSSRI_ERR_NONFINITE;
   return RSSRI_OK;
-#undef RS_CK
+}
+
+int run_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, const double *gb_in,
+              double *sigma, double *e_pair, double *e_corr, double *e_stderr, rssri_stats *st,
+              bool collect_stats = false) {
+  const int rc = issue_sigma(h, o, g_in, gb_in, sigma, e_pair, collect_stats);
+  if (rc) return rc;
+  return finish_sigma(h, e_corr, e_stderr, st);
 }
 
 }  // namespace
@@ -1324,9 +1390,44 @@ int rssri_sigma_from_g(rssri_handle *h, const rssri_options *o, const double *g,
   return run_sigma(h, o, g, gb, sigma, e_pair, e_corr, e_stderr, st);
 }
 
+int rssri_sigma_async(rssri_handle *h, const rssri_options *o, double *sigma, double *e_pair) {
+  if (!sigma) return RSSRI_ERR_INVALID_ARG;
+  return issue_sigma(h, o, nullptr, nullptr, sigma, e_pair, false);
+}
+
+int rssri_sigma_wait(rssri_handle *h, double *e_corr, double *e_stderr, rssri_stats *st) {
+  return finish_sigma(h, e_corr, e_stderr, st);
+}
+
+int rssri_sigma_batch(rssri_handle *const *hs, int count, const rssri_options *o,
+                      double *const *sigma, double *const *e_pair, double *e_corr,
+                      double *e_stderr) {
+  if (count < 0 || (count > 0 && (!hs || !sigma))) return RSSRI_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < i; ++j)
+      if (hs[i] == hs[j]) return RSSRI_ERR_INVALID_ARG;
+  int first = RSSRI_OK, issued = 0;
+  for (; issued < count; ++issued) {
+    const int rc = issue_sigma(hs[issued], o, nullptr, nullptr, sigma[issued],
+                               e_pair ? e_pair[issued] : nullptr, false);
+    if (rc) {
+      first = rc;
+      break;
+    }
+  }
+  // every enqueued call is waited for, also after a failure
+  for (int i = 0; i < issued; ++i) {
+    const int rc = finish_sigma(hs[i], e_corr ? e_corr + i : nullptr,
+                                e_stderr ? e_stderr + i : nullptr, nullptr);
+    if (rc && first == RSSRI_OK) first = rc;
+  }
+  return first;
+}
+
 int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_params, int steps,
                    int batch, float lr, double *loss_before, double *loss_after) {
-  if (!h || !o || !init_params || steps < 0 || batch < 1 || batch > CV_CHUNK || !(lr > 0.f))
+  if (!h || h->pending || !o || !init_params || steps < 0 || batch < 1 || batch > CV_CHUNK ||
+      !(lr > 0.f))
     return RSSRI_ERR_INVALID_ARG;
   if (h->broken) return RSSRI_ERR_CUDA;
   if (!h->ready) return RSSRI_ERR_NOT_READY;
@@ -1408,7 +1509,7 @@ int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_pa
 }
 
 int rssri_cv_set_params(rssri_handle *h, const float *params) {
-  if (!h || !params) return RSSRI_ERR_INVALID_ARG;
+  if (!h || h->pending || !params) return RSSRI_ERR_INVALID_ARG;
   if (h->broken) return RSSRI_ERR_CUDA;
   if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
   cudaError_t e = ensure(h->cv_params, CV_NPARAM * sizeof(float));
@@ -1422,7 +1523,8 @@ int rssri_cv_set_params(rssri_handle *h, const float *params) {
 
 int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, const float *weight,
                        int m, const float *params, float *loss, float *grad) {
-  if (!h || !x || !target || !weight || !params || !loss || !grad || m < 1 || m > CV_CHUNK)
+  if (!h || h->pending || !x || !target || !weight || !params || !loss || !grad || m < 1 ||
+      m > CV_CHUNK)
     return RSSRI_ERR_INVALID_ARG;
   if (h->broken) return RSSRI_ERR_CUDA;
   if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
@@ -1457,7 +1559,7 @@ int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, con
 }
 
 int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
-  if (!h || !bytes) return RSSRI_ERR_INVALID_ARG;
+  if (!h || h->pending || !bytes) return RSSRI_ERR_INVALID_ARG;
   *bytes = 0;
   if (!h->ready) return RSSRI_ERR_NOT_READY;
   const size_t d = sizeof(double);

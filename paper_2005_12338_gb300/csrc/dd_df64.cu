@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
   // once every 4 pairs: kept in shared memory ([output][thread], conflict-free)
   __shared__ float2 Tot[16][32 * SWARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = (blockIdx.x * SWARPS + warp) * 4, m = blockIdx.y, q0 = blockIdx.z * SQW;
+  // aux chunks vary fastest in the launch order, so the blocks that read the
+  // same rows of D run together and share them through L2
+  const int q0 = blockIdx.x * SQW, j0 = (blockIdx.y * SWARPS + warp) * 4, m = blockIdx.z;
   if (j0 >= n) return;  // whole warp
   const int j1 = min(n, j0 + 4);
   const int a0 = rowptr[m], a1 = rowptr[m + 1];
@@ -167,10 +169,15 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     const float2 *Dw = &Dt[warp][buf][0][0];
     const int le_i = le - lc;
     int li = lb - lc;
+    // software pipeline: the next two columns are loaded while the current
+    // two are multiplied
+    float2 xa[4] = {}, xb[4] = {};
+    if (li <= le_i) load4(Ak + (long long)li * naux, xa);
+    if (li + 1 <= le_i) load4(Ak + (long long)(li + 1) * naux, xb);
     for (; li < le_i; li += 2) {
-      float2 xa[4], xb[4];
-      load4(Ak + (long long)li * naux, xa);
-      load4(Ak + (long long)(li + 1) * naux, xb);
+      float2 na[4] = {}, nb[4] = {};
+      if (li + 2 <= le_i) load4(Ak + (long long)(li + 2) * naux, na);
+      if (li + 3 <= le_i) load4(Ak + (long long)(li + 3) * naux, nb);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const float2 da = Dw[r * SLR + li], db = Dw[r * SLR + li + 1];
@@ -179,10 +186,13 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
 #pragma unroll
         for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], db, xb[c].x, xb[c].y);
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        xa[c] = na[c];
+        xb[c] = nb[c];
+      }
     }
     if (li == le_i) {
-      float2 xa[4];
-      load4(Ak + (long long)li * naux, xa);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const float2 da = Dw[r * SLR + li];
@@ -234,7 +244,18 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
 // owns 4 x 4 outputs of a 64 x 64 tile; K goes in 16-deep slabs through
 // shared memory; the pairs are renormalised exactly after each slab and folded
 // into fp64 totals every 256 terms.
-constexpr int DBM = 64, DBN = 64, DBK = 16, DNT = 256;
+// Tile geometries: TY x TX threads, each owning TI x TJ outputs at strides
+// TY and TX; K in slabs of BK; MINB resident CTAs per SM asked of the
+// compiler.  G64: 64 x 64 tiles (256 threads); G40: 40 x 40 tiles (64
+// threads, 25 outputs each), for shapes such as N = 200 and N_aux = 600 that
+// 64-wide tiles would pad by up to 64%.
+template <int TY_, int TX_, int TI_, int TJ_, int BK_, int MINB_>
+struct DfGeo {
+  static constexpr int TY = TY_, TX = TX_, TI = TI_, TJ = TJ_, BK = BK_, MINB = MINB_;
+  static constexpr int BM = TY * TI, BN = TX * TJ, NT = TY * TX;
+};
+using G64 = DfGeo<16, 16, 4, 4, 16, 2>;
+using G40 = DfGeo<8, 8, 5, 5, 8, 6>;
 
 __device__ __forceinline__ void df_mac(float &S, float &E, float2 a, float2 b) {
   const float p = __fmul_rn(a.x, b.x);
@@ -248,15 +269,18 @@ __device__ __forceinline__ void df_mac(float &S, float &E, float2 a, float2 b) {
   E = __fadd_rn(E, __fadd_rn(err, e));
 }
 
-template <int MODE, int TA, int TB, int OUT>
-__global__ void __launch_bounds__(DNT) df_gemm_kernel(
+template <class GEO, int MODE, int TA, int TB, int OUT>
+__global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
     int M, int N, int K, int kchunk, int ksplit, const float2 *__restrict__ A, long long lda,
     long long sA, const float2 *__restrict__ B, long long ldb, long long sB, void *__restrict__ Cv,
     long long ldc, long long sC, double alpha, int partial, const int *__restrict__ seg,
     const int *__restrict__ col) {
+  constexpr int DBM = GEO::BM, DBN = GEO::BN, DBK = GEO::BK, DNT = GEO::NT;
+  constexpr int TY = GEO::TY, TX = GEO::TX, TI = GEO::TI, TJ = GEO::TJ;
   __shared__ float2 As[2][DBK][DBM + 1];
   __shared__ float2 Bs[2][DBK][DBN + 1];
   constexpr int LA = DBM * DBK / DNT, LB = DBN * DBK / DNT;
+  static_assert(LA * DNT == DBM * DBK && LB * DNT == DBN * DBK, "tile loads");
   constexpr bool AK = (MODE == 0 && TA == 0), BKc = (MODE == 0 && TB == 1);
   const int z = blockIdx.z;
   const int b = z / ksplit, ks = z % ksplit;
@@ -273,16 +297,16 @@ __global__ void __launch_bounds__(DNT) df_gemm_kernel(
     B += (long long)b * sB;
   }
   const int row0 = blockIdx.y * DBM, col0 = blockIdx.x * DBN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  // thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j of the tile, so
-  // that a warp's shared-memory reads are one broadcast (A) and one run of 16
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  // thread (tx, ty) owns rows ty + TY i and columns tx + TX j of the tile, so
+  // that a warp's shared-memory reads are a broadcast or two (A) and runs of
   // consecutive pairs (B)
-  float TH[4][4], TL[4][4];
-  float S[4][4], E[4][4];
+  float TH[TI][TJ], TL[TI][TJ];
+  float S[TI][TJ], E[TI][TJ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) TH[i][j] = TL[i][j] = S[i][j] = E[i][j] = 0.0f;
+    for (int j = 0; j < TJ; ++j) TH[i][j] = TL[i][j] = S[i][j] = E[i][j] = 0.0f;
   float2 ra[LA], rb[LB];
   const float2 zero = make_float2(0.f, 0.f);
   auto load = [&](int kt) {
@@ -339,21 +363,21 @@ __global__ void __launch_bounds__(DNT) df_gemm_kernel(
       if (more) load(kt + DBK);
 #pragma unroll
       for (int kk = 0; kk < DBK; ++kk) {
-        float2 a[4], bb[4];
+        float2 a[TI], bb[TJ];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+        for (int i = 0; i < TI; ++i) a[i] = As[buf][kk][ty + TY * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bb[j] = Bs[buf][kk][tx + 16 * j];
+        for (int j = 0; j < TJ; ++j) bb[j] = Bs[buf][kk][tx + TX * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TI; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) df_mac(S[i][j], E[i][j], a[i], bb[j]);
+          for (int j = 0; j < TJ; ++j) df_mac(S[i][j], E[i][j], a[i], bb[j]);
       }
       ++slab;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TJ; ++j) {
           const float sn = __fadd_rn(S[i][j], E[i][j]);
           E[i][j] = __fsub_rn(E[i][j], __fsub_rn(sn, S[i][j]));
           S[i][j] = sn;
@@ -371,11 +395,11 @@ __global__ void __launch_bounds__(DNT) df_gemm_kernel(
     }
   }
   const bool neg = alpha == -1.0, unit = alpha == 1.0 || neg;
-  for (int i = 0; i < 4; ++i) {
-    const int gi = row0 + ty + 16 * i;
+  for (int i = 0; i < TI; ++i) {
+    const int gi = row0 + ty + TY * i;
     if (gi >= M) continue;
-    for (int j = 0; j < 4; ++j) {
-      const int gj = col0 + tx + 16 * j;
+    for (int j = 0; j < TJ; ++j) {
+      const int gj = col0 + tx + TX * j;
       if (gj >= N) continue;
       const float h = TH[i][j], l = TL[i][j];
       if (partial) {
@@ -430,34 +454,52 @@ cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s) {
 cudaError_t dd_exchange_spmm_df64(const int *rowptr, const int *pcol, const float2 *D, int P,
                                   const float2 *At, int n, int naux, double *T, cudaStream_t s) {
   if (n <= 0 || naux <= 0) return cudaSuccess;
-  dim3 grid(ceil_div(n, 4 * SWARPS), n, ceil_div(naux, SQW));
+  dim3 grid(ceil_div(naux, SQW), ceil_div(n, 4 * SWARPS), n);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   dd_spmm_warp_df64_kernel<<<grid, 32 * SWARPS, 0, s>>>(rowptr, pcol, D, P, At, n, naux, T);
   ++launch_counter();
   return cudaGetLastError();
 }
 
-cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  if ((g.C64 == nullptr) == (g.C2 == nullptr)) return cudaErrorInvalidValue;
-  // split K (fp64 output only) when the output has few tiles and K is long
-  const long long tiles = (long long)ceil_div(g.M, DBM) * ceil_div(g.N, DBN) * g.batch;
+namespace {
+
+// 40-wide tiles only where 64-wide ones would pad the output by more than 30%
+// more: a 64-wide CTA issues better (16 warps per SM against 12, measured
+// 73% against 51-55% of the FMA pipe), so it wins unless it wastes more.
+bool use_g40(int M, int N) {
+  const long long a64 = (long long)ceil_div(M, 64) * 64 * ceil_div(N, 64) * 64;
+  const long long a40 = (long long)ceil_div(M, 40) * 40 * ceil_div(N, 40) * 40;
+  return 10 * a64 > 13 * a40;
+}
+
+// Split of K (fp64 output, batch 1, few tiles, long K) into ks chunks of kc.
+template <class GEO>
+void df_plan(const DfGemm &g, int *ks_out, int *kc_out) {
+  const long long tiles = (long long)ceil_div(g.M, GEO::BM) * ceil_div(g.N, GEO::BN) * g.batch;
+  const long long target = 2LL * GEO::MINB * 152;  // resident CTAs x 2 waves
   int ks = 1;
-  if (g.C64 && g.batch == 1 && tiles < 2 * 152 && g.K >= 1024) {
-    ks = (int)std::min<long long>((4 * 152 + tiles - 1) / tiles, g.K / 256);
+  if (g.C64 && g.batch == 1 && tiles < target / 2 && g.K >= 1024) {
+    ks = (int)std::min<long long>((target + tiles - 1) / tiles, g.K / 256);
     ks = std::max(1, std::min(ks, 256));
   }
-  int kc = ((ceil_div(g.K, ks) + DBK - 1) / DBK) * DBK;
-  ks = std::max(1, ceil_div(g.K, kc));
+  const int kc = ((ceil_div(g.K, ks) + GEO::BK - 1) / GEO::BK) * GEO::BK;
+  *kc_out = kc;
+  *ks_out = std::max(1, ceil_div(g.K, kc));
+}
+
+template <class GEO>
+cudaError_t df_gemm_geo(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s) {
+  int ks, kc;
+  df_plan<GEO>(g, &ks, &kc);
   if (ks > 1 && work_elems < (size_t)ks * g.M * g.N) return cudaErrorInvalidValue;
   if (g.batch * ks > 65535) return cudaErrorInvalidValue;
-  dim3 grid(ceil_div(g.N, DBN), ceil_div(g.M, DBM), g.batch * ks);
+  dim3 grid(ceil_div(g.N, GEO::BN), ceil_div(g.M, GEO::BM), g.batch * ks);
   void *out = ks > 1 ? (void *)work : (g.C64 ? (void *)g.C64 : (void *)g.C2);
   const int part = ks > 1;
-#define RS_DF(TA, TB, OUT)                                                                      \
-  df_gemm_kernel<0, TA, TB, OUT><<<grid, DNT, 0, s>>>(g.M, g.N, g.K, kc, ks, g.A, g.lda, g.sA, \
-                                                     g.B, g.ldb, g.sB, out, g.ldc, g.sC,       \
-                                                     g.alpha, part, nullptr, nullptr)
+#define RS_DF(TA, TB, OUT)                                                                \
+  df_gemm_kernel<GEO, 0, TA, TB, OUT><<<grid, GEO::NT, 0, s>>>(                           \
+      g.M, g.N, g.K, kc, ks, g.A, g.lda, g.sA, g.B, g.ldb, g.sB, out, g.ldc, g.sC, g.alpha, \
+      part, nullptr, nullptr)
   const int o = g.C2 ? 1 : 0;
   if (!g.transA && !g.transB) { if (o) RS_DF(0, 0, 1); else RS_DF(0, 0, 0); }
   else if (!g.transA && g.transB) { if (o) RS_DF(0, 1, 1); else RS_DF(0, 1, 0); }
@@ -475,13 +517,19 @@ cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream
   return cudaSuccess;
 }
 
+}  // namespace
+
+cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if ((g.C64 == nullptr) == (g.C2 == nullptr)) return cudaErrorInvalidValue;
+  return use_g40(g.M, g.N) ? df_gemm_geo<G40>(g, work, work_elems, s)
+                           : df_gemm_geo<G64>(g, work, work_elems, s);
+}
+
 size_t df_gemm_work(const DfGemm &g) {
-  const long long tiles = (long long)ceil_div(g.M, DBM) * ceil_div(g.N, DBN) * g.batch;
-  if (!(g.C64 && g.batch == 1 && tiles < 2 * 152 && g.K >= 1024)) return 0;
-  int ks = (int)std::min<long long>((4 * 152 + tiles - 1) / tiles, g.K / 256);
-  ks = std::max(1, std::min(ks, 256));
-  const int kc = ((ceil_div(g.K, ks) + DBK - 1) / DBK) * DBK;
-  ks = std::max(1, ceil_div(g.K, kc));
+  int ks, kc;
+  if (use_g40(g.M, g.N)) df_plan<G40>(g, &ks, &kc);
+  else df_plan<G64>(g, &ks, &kc);
   return ks > 1 ? (size_t)ks * g.M * g.N : 0;
 }
 
@@ -489,12 +537,20 @@ cudaError_t df_gemm_segmented(int batch, int M, int N, const int *seg, const int
                               const float2 *A, long long lda, const float2 *B, long long ldb,
                               float2 *C, long long ldc, long long sC, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  const bool g40 = use_g40(M, N);
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     const int nb = std::min(65535, batch - b0);
-    dim3 grid(ceil_div(N, DBN), ceil_div(M, DBM), nb);
-    df_gemm_kernel<1, 1, 0, 1><<<grid, DNT, 0, s>>>(M, N, 0, 0, 1, A, lda, 0, B, ldb, 0,
-                                                    C + (long long)b0 * sC, ldc, sC, 1.0, 0,
-                                                    seg + b0, col);
+    if (g40) {
+      dim3 grid(ceil_div(N, G40::BN), ceil_div(M, G40::BM), nb);
+      df_gemm_kernel<G40, 1, 1, 0, 1><<<grid, G40::NT, 0, s>>>(
+          M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C + (long long)b0 * sC, ldc, sC, 1.0, 0,
+          seg + b0, col);
+    } else {
+      dim3 grid(ceil_div(N, G64::BN), ceil_div(M, G64::BM), nb);
+      df_gemm_kernel<G64, 1, 1, 0, 1><<<grid, G64::NT, 0, s>>>(
+          M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C + (long long)b0 * sC, ldc, sC, 1.0, 0,
+          seg + b0, col);
+    }
     ++launch_counter();
     RS_TRY(cudaGetLastError());
   }

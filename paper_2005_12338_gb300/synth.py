@@ -27,7 +27,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["System", "make_system", "tau_grid", "CONFIGS"]
+__all__ = ["System", "make_system", "tau_grid", "CONFIGS", "MANY", "many_sizes"]
 
 
 @dataclass
@@ -130,3 +130,16 @@ CONFIGS = {
     "c3_n1000": dict(n=1000, n_occ=500, n_aux=3000, n_tau=128, n_s=500, eps=1e-3,
                      eps_prime=0.02, seeds=(0,)),
 }
+
+# Many independent chains of uneven size (a reduced form of the 64-chain
+# batch, N from 100 to 800, whose deterministic blocks alone would take tens
+# of minutes): K chains with N_k spread evenly over [n_min, n_max], N_aux = 3N,
+# n_occ = N/2, input seed k.
+MANY = dict(k=16, n_min=64, n_max=256, n_tau=16, n_s=64, eps=1e-3, eps_prime=0.02)
+
+
+def many_sizes(k: int, n_min: int, n_max: int):
+    """N_k = n_min + round((n_max - n_min) k / (K - 1)), k = 0..K-1."""
+    if k == 1:
+        return [n_min]
+    return [n_min + int(round((n_max - n_min) * i / (k - 1))) for i in range(k)]
