@@ -702,7 +702,8 @@ cudaError_t sigma_dd_tau_df64(rssri_handle *h, const float2 *Ghl, const float2 *
     RS_TRY(dd_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s));
     // At is no longer needed: its pair buffer takes T
     RS_TRY(to_df64(T, nn * na, Ahl, s)); }
-  // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n]
+  // Sigma_DD = -PG_view [n x (n na)] * T_view [(n na) x n], symmetric (G, Gb
+  // and every K^Q are): the tiles below the diagonal are mirrored
   {
     DfGemm g;
     g.M = n; g.N = n; g.K = n * na;
@@ -710,6 +711,7 @@ cudaError_t sigma_dd_tau_df64(rssri_handle *h, const float2 *Ghl, const float2 *
     g.B = Ahl; g.ldb = n;
     g.C64 = out; g.ldc = n;
     g.alpha = -1.0;
+    g.sym = 1;
     RS_TRY(df_gemm_p(h, g));
   }
   return cudaSuccess;

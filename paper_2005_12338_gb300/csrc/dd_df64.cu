@@ -169,37 +169,37 @@ __global__ void __launch_bounds__(32 * SWARPS) dd_spmm_warp_df64_kernel(
     const float2 *Dw = &Dt[warp][buf][0][0];
     const int le_i = le - lc;
     int li = lb - lc;
-    // software pipeline: the next two columns are loaded while the current
-    // two are multiplied
-    float2 xa[4] = {}, xb[4] = {};
-    if (li <= le_i) load4(Ak + (long long)li * naux, xa);
-    if (li + 1 <= le_i) load4(Ak + (long long)(li + 1) * naux, xb);
-    for (; li < le_i; li += 2) {
-      float2 na[4] = {}, nb[4] = {};
-      if (li + 2 <= le_i) load4(Ak + (long long)(li + 2) * naux, na);
-      if (li + 3 <= le_i) load4(Ak + (long long)(li + 3) * naux, nb);
+    // software pipeline over pairs of columns: two register sets alternate,
+    // so the loads of columns li+2, li+3 fly while li, li+1 are multiplied
+    float2 xa[4] = {}, xb[4] = {}, na[4] = {}, nb[4] = {};
+    auto ld = [&](int c, float2 (&x)[4]) {
+      if (c <= le_i) load4(Ak + (long long)c * naux, x);
+    };
+    auto mac = [&](int c, const float2 (&x)[4]) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const float2 da = Dw[r * SLR + li], db = Dw[r * SLR + li + 1];
+        const float2 d = Dw[r * SLR + c];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], da, xa[c].x, xa[c].y);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], db, xb[c].x, xb[c].y);
+        for (int cc = 0; cc < 4; ++cc) df_mac2(S[r][cc], E[r][cc], d, x[cc].x, x[cc].y);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        xa[c] = na[c];
-        xb[c] = nb[c];
-      }
+    };
+    ld(li, xa);
+    ld(li + 1, xb);
+    for (; li + 3 <= le_i; li += 4) {
+      ld(li + 2, na);
+      ld(li + 3, nb);
+      mac(li, xa);
+      mac(li + 1, xb);
+      ld(li + 4, xa);
+      ld(li + 5, xb);
+      mac(li + 2, na);
+      mac(li + 3, nb);
     }
-    if (li == le_i) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const float2 da = Dw[r * SLR + li];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) df_mac2(S[r][c], E[r][c], da, xa[c].x, xa[c].y);
-      }
-    }
+    // 0 to 3 columns left; xa, xb hold li and li + 1 where those exist
+    if (li + 2 <= le_i) ld(li + 2, na);
+    if (li <= le_i) mac(li, xa);
+    if (li + 1 <= le_i) mac(li + 1, xb);
+    if (li + 2 <= le_i) mac(li + 2, na);
     // after the last window of a pair: exact renormalisation (Fast2Sum);
     // added into the pair totals every 4 pairs and at the end
     if (st % nwin == nwin - 1) {
@@ -273,7 +273,7 @@ template <class GEO, int MODE, int TA, int TB, int OUT>
 __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
     int M, int N, int K, int kchunk, int ksplit, const float2 *__restrict__ A, long long lda,
     long long sA, const float2 *__restrict__ B, long long ldb, long long sB, void *__restrict__ Cv,
-    long long ldc, long long sC, double alpha, int partial, const int *__restrict__ seg,
+    long long ldc, long long sC, double alpha, int partial, int sym, const int *__restrict__ seg,
     const int *__restrict__ col) {
   constexpr int DBM = GEO::BM, DBN = GEO::BN, DBK = GEO::BK, DNT = GEO::NT;
   constexpr int TY = GEO::TY, TX = GEO::TX, TI = GEO::TI, TJ = GEO::TJ;
@@ -282,6 +282,8 @@ __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
   constexpr int LA = DBM * DBK / DNT, LB = DBN * DBK / DNT;
   static_assert(LA * DNT == DBM * DBK && LB * DNT == DBN * DBK, "tile loads");
   constexpr bool AK = (MODE == 0 && TA == 0), BKc = (MODE == 0 && TB == 1);
+  // symmetric result: only the tiles on and above the diagonal are computed
+  if (sym && blockIdx.y > blockIdx.x) return;
   const int z = blockIdx.z;
   const int b = z / ksplit, ks = z % ksplit;
   int kbeg, kend;
@@ -422,15 +424,30 @@ __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
   }
 }
 
+// C = alpha * (sum of the ks partial products); with sym (M == N, square tiles
+// of edge tile), elements of tiles below the diagonal take the transposed
+// position's partials (only tiles on and above the diagonal were computed).
 __global__ void df_reduce_kernel(const double *__restrict__ part, int ks, int M, int N,
-                                 double *__restrict__ C, long long ldc, double alpha) {
+                                 double *__restrict__ C, long long ldc, double alpha, int sym,
+                                 int tile) {
   const long long mn = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn;
        e += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < ks; ++k) s += part[k * mn + e];
     const long long i = e / N, j = e - i * N;
+    const long long src = (sym && i / tile > j / tile) ? j * N + i : e;
+    double s = 0.0;
+    for (int k = 0; k < ks; ++k) s += part[k * mn + src];
     C[i * ldc + j] = alpha * s;
+  }
+}
+
+// C[i][j] = C[j][i] for the elements of tiles below the diagonal (sym, no split).
+__global__ void df_mirror_kernel(double *__restrict__ C, long long ldc, int M, int tile) {
+  const long long mm = (long long)M * M;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / M, j = e - i * M;
+    if (i / tile > j / tile) C[i * ldc + j] = C[j * ldc + i];
   }
 }
 
@@ -499,7 +516,7 @@ cudaError_t df_gemm_geo(const DfGemm &g, double *work, size_t work_elems, cudaSt
 #define RS_DF(TA, TB, OUT)                                                                \
   df_gemm_kernel<GEO, 0, TA, TB, OUT><<<grid, GEO::NT, 0, s>>>(                           \
       g.M, g.N, g.K, kc, ks, g.A, g.lda, g.sA, g.B, g.ldb, g.sB, out, g.ldc, g.sC, g.alpha, \
-      part, nullptr, nullptr)
+      part, g.sym, nullptr, nullptr)
   const int o = g.C2 ? 1 : 0;
   if (!g.transA && !g.transB) { if (o) RS_DF(0, 0, 1); else RS_DF(0, 0, 0); }
   else if (!g.transA && g.transB) { if (o) RS_DF(0, 1, 1); else RS_DF(0, 1, 0); }
@@ -510,7 +527,13 @@ cudaError_t df_gemm_geo(const DfGemm &g, double *work, size_t work_elems, cudaSt
   RS_TRY(cudaGetLastError());
   if (part) {
     const long long mn = (long long)g.M * g.N;
-    df_reduce_kernel<<<grid_cap(mn, 256), 256, 0, s>>>(work, ks, g.M, g.N, g.C64, g.ldc, g.alpha);
+    df_reduce_kernel<<<grid_cap(mn, 256), 256, 0, s>>>(work, ks, g.M, g.N, g.C64, g.ldc, g.alpha,
+                                                      g.sym, GEO::BM);
+    ++launch_counter();
+    RS_TRY(cudaGetLastError());
+  } else if (g.sym) {
+    df_mirror_kernel<<<grid_cap((long long)g.M * g.M, 256), 256, 0, s>>>(g.C64, g.ldc, g.M,
+                                                                         GEO::BM);
     ++launch_counter();
     RS_TRY(cudaGetLastError());
   }
@@ -522,6 +545,7 @@ cudaError_t df_gemm_geo(const DfGemm &g, double *work, size_t work_elems, cudaSt
 cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if ((g.C64 == nullptr) == (g.C2 == nullptr)) return cudaErrorInvalidValue;
+  if (g.sym && (g.M != g.N || !g.C64 || g.batch != 1)) return cudaErrorInvalidValue;
   return use_g40(g.M, g.N) ? df_gemm_geo<G40>(g, work, work_elems, s)
                            : df_gemm_geo<G64>(g, work, work_elems, s);
 }
@@ -543,12 +567,12 @@ cudaError_t df_gemm_segmented(int batch, int M, int N, const int *seg, const int
     if (g40) {
       dim3 grid(ceil_div(N, G40::BN), ceil_div(M, G40::BM), nb);
       df_gemm_kernel<G40, 1, 1, 0, 1><<<grid, G40::NT, 0, s>>>(
-          M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C + (long long)b0 * sC, ldc, sC, 1.0, 0,
+          M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C + (long long)b0 * sC, ldc, sC, 1.0, 0, 0,
           seg + b0, col);
     } else {
       dim3 grid(ceil_div(N, G64::BN), ceil_div(M, G64::BM), nb);
       df_gemm_kernel<G64, 1, 1, 0, 1><<<grid, G64::NT, 0, s>>>(
-          M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C + (long long)b0 * sC, ldc, sC, 1.0, 0,
+          M, N, 0, 0, 1, A, lda, 0, B, ldb, 0, C + (long long)b0 * sC, ldc, sC, 1.0, 0, 0,
           seg + b0, col);
     }
     ++launch_counter();

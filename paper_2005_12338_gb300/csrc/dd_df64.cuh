@@ -24,6 +24,9 @@ struct DfGemm {
   float2 *C2 = nullptr;
   long long ldc = 0, sC = 0;
   double alpha = 1.0;
+  // the product is known to be symmetric (M == N, fp64 output, batch 1):
+  // only tiles on and above the diagonal are computed, the rest mirrored
+  int sym = 0;
 };
 cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s);
 size_t df_gemm_work(const DfGemm &g);

@@ -107,6 +107,10 @@ CASES = {
     "n20": dict(sys=(20, 10, 60, 32), eps_prime=0.02, eps=1e-2, n_s=64, seed=0),
     # ragged: two 64-wide tiles plus a tail, odd sample count, several tau
     "n72_ragged": dict(sys=(72, 31, 150, 5), eps_prime=0.02, eps=1e-2, n_s=7, seed=12345),
+    # odd N and odd N_aux: unaligned rows everywhere (scalar paths of the vector loads)
+    "n37_odd": dict(sys=(37, 16, 45, 3), eps_prime=0.02, eps=1e-2, n_s=5, seed=99),
+    # short contractions (N N_aux < 1024): no split over K anywhere
+    "n16_short": dict(sys=(16, 7, 40, 3), eps_prime=0.02, eps=1e-2, n_s=4, seed=5),
 }
 
 

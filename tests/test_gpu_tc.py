@@ -78,6 +78,20 @@ def test_tc_chain_against_oracle(B, n72, pname):
     assert abs(got["e"] - ref.e_corr) < 0.1 * ref.e_stderr
 
 
+@pytest.mark.parametrize("pname", PRECS)
+def test_tc_chain_odd_size(B, pname):
+    """N = 37: operand rows padded to 40 elements for the TMA descriptors, a
+    ragged last tile in every product."""
+    s = synth.make_system(37, 16, 45, 3, input_seed=8)
+    ref = O.rs_sri(s.eri3, s.metric, s.orb_e, s.orb_c, s.n_occ, s.mu, s.tau, s.tau_w, 0.02, 1e-2,
+                   5, 99)
+    got = run(B, s, 0.02, 1e-2, 5, 99, prec(B, pname))
+    for t in range(s.n_tau):
+        st_ref = ref.sigma[t] - 0.5 * (ref.sigma_dd[t] + ref.sigma_dd[t].T)
+        st_got = got["sigma"][t] - 0.5 * (got["sdd"][t] + got["sdd"][t].T)
+        assert np.linalg.norm(st_got - st_ref) / np.linalg.norm(st_ref) < TOL[pname], t
+
+
 def test_tf32_closer_than_bf16(B, n72):
     """The tf32 operands carry 3 more bits: its remainder error must be well
     below the bf16 one on the same draws."""
