@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librssri.so")
-SOURCES = ["api.cu", "gemm_f64.cu", "kernels.cu", "static_energy.cu", "tc_gemm.cu", "chain_tc.cu", "dd_df64.cu", "cv_mlp.cu"]
+SOURCES = ["api.cu", "gemm_f64.cu", "kernels.cu", "static_energy.cu", "tc_gemm.cu", "chain_tc.cu", "dd_df64.cu", "dd_spmm_df64.cu", "cv_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -91,6 +91,8 @@ struct rssri_handle {
   DevBuf litMP, litT, litMhl;
   // pairs of (ij|A) and of U^T / theta for the double-float factor products
   DevBuf eri_hl, ut_hl;
+  // pair copies of the Newton-Schulz operands (double-float metric root)
+  DevBuf nsA2, nsB2;
   bool d_df64_ready = false;
   // bf16 chain buffers
   DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
@@ -251,7 +253,7 @@ cudaError_t gemm_p(rssri_handle *h, int cls, const GemmArgs &g) {
 // spectrum of V/c lies in (0, 1] (c = max row sum of |V| guarantees this for
 // an SPD V).  Stops one step after max |Z Y - I| < 1e-8; a non-SPD metric
 // never converges and is reported as NOT_SPD.
-int metric_inv_sqrt(rssri_handle *h, int *rc) {
+int metric_inv_sqrt(rssri_handle *h, int *rc, bool df64) {
   cudaStream_t s = h->stream;
   const int na = h->n_aux;
   const size_t bytes = (size_t)na * na * sizeof(double);
@@ -272,25 +274,45 @@ int metric_inv_sqrt(rssri_handle *h, int *rc) {
          *Z2 = h->nsZ2.as<double>(), *Pm = h->nsP.as<double>(), *Tm = h->nsT.as<double>();
   double *scal = h->scal.as<double>(), *part = h->part.as<double>();
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(ns_init(h->metric, na, Y, Z, scal, part, s)); }
-  GemmArgs g;
-  g.M = g.N = g.K = na;
-  g.lda = g.ldb = g.ldc = na;
+  if (df64) {
+    RS_CK(ensure(h->nsA2, (size_t)na * na * sizeof(float2)));
+    RS_CK(ensure(h->nsB2, (size_t)na * na * sizeof(float2)));
+  }
+  // C = A B (na x na), in fp64 or in double-float on split copies
+  auto mm = [&](const double *A, const double *B, double *C) -> cudaError_t {
+    if (!df64) {
+      GemmArgs g;
+      g.M = g.N = g.K = na;
+      g.lda = g.ldb = g.ldc = na;
+      g.A = A; g.B = B; g.C = C;
+      return gemm_p(h, RSSRI_PROF_SETUP_GEMM, g);
+    }
+    {
+      SPAN(RSSRI_PROF_OTHER, 0.0);
+      RS_TRY(to_df64(A, (long long)na * na, h->nsA2.as<float2>(), s));
+      RS_TRY(to_df64(B, (long long)na * na, h->nsB2.as<float2>(), s));
+    }
+    SPAN(RSSRI_PROF_SETUP_GEMM, 2.0 * na * (double)na * na * 1e-9);
+    DfGemm g;
+    g.M = g.N = g.K = na;
+    g.A = h->nsA2.as<float2>(); g.lda = na;
+    g.B = h->nsB2.as<float2>(); g.ldb = na;
+    g.C64 = C; g.ldc = na;
+    return df_gemm(g, nullptr, 0, s);
+  };
   const int max_it = 100;
   double resid = 0;
   bool final_step = false;
   int it = 0;
   for (; it < max_it; ++it) {
-    g.A = Z; g.B = Y; g.C = Pm;
-    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    RS_CK(mm(Z, Y, Pm));
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(ns_tbuild(Pm, na, Tm, scal, part, s)); }
     RS_CK(fetch(&resid, scal + 1, s));
     if (!std::isfinite(resid) || resid > 1e6) break;
     if (final_step) break;
     if (resid < 1e-8) final_step = true;
-    g.A = Y; g.B = Tm; g.C = Y2;
-    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
-    g.A = Tm; g.B = Z; g.C = Z2;
-    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    RS_CK(mm(Y, Tm, Y2));
+    RS_CK(mm(Tm, Z, Z2));
     std::swap(Y, Y2);
     std::swap(Z, Z2);
   }
@@ -370,7 +392,7 @@ void rssri_destroy(rssri_handle *h) {
                     &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
                     &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
                     &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
-                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
+                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
                     &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss};
   for (DevBuf *b : bufs) release(*b);
@@ -455,7 +477,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
 
   // S1
   int ns_rc = RSSRI_OK;
-  rc = metric_inv_sqrt(h, &ns_rc);
+  rc = metric_inv_sqrt(h, &ns_rc, o->dd_arith == RSSRI_DD_DF64);
   if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
   if (ns_rc) return ns_rc;
 
