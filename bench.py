@@ -51,9 +51,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp64"],
-                    help="chain products: bf16 tensor cores (the chosen form), tf32 tensor "
-                         "cores, or fp64 (plain)")
+    ap.add_argument("--precision", default="df64", choices=["df64", "bf16", "tf32", "fp64"],
+                    help="chain products: double-float on the fp32 pipes (fp64-accurate, the "
+                         "benchmark line), bf16 or tf32 tensor cores (reduced precision), or "
+                         "IEEE fp64 (plain)")
+    ap.add_argument("--reduced", default="bf16", choices=["bf16", "tf32", "none"],
+                    help="also time this reduced-precision tensor-core form and report its "
+                         "error against the IEEE fp64 form on the same draws")
     ap.add_argument("--dd", default="df64", choices=["df64", "fp64"],
                     help="exchange contraction of the deterministic block: double-float on "
                          "the fp32 pipes (chosen) or IEEE fp64")
@@ -358,8 +362,9 @@ def our_arm(args):
     h = binding.Handle(local)
     stream = torch.cuda.current_stream(local)
 
-    prec = {"bf16": binding.RSSRI_PREC_BF16, "tf32": binding.RSSRI_PREC_TF32,
-            "fp64": binding.RSSRI_PREC_FP64}[args.precision]
+    prec_code = {"bf16": binding.RSSRI_PREC_BF16, "tf32": binding.RSSRI_PREC_TF32,
+                 "fp64": binding.RSSRI_PREC_FP64, "df64": binding.RSSRI_PREC_DF64}
+    prec = prec_code[args.precision]
     tensor_chain = args.precision in ("bf16", "tf32")
     dd = binding.RSSRI_DD_DF64 if args.dd == "df64" else binding.RSSRI_DD_FP64
 
@@ -412,7 +417,9 @@ def our_arm(args):
     # bound its scratch; the sums are the same up to rounding order)
     plain = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=binding.RSSRI_DD_FP64,
                  pair_batch=100 if n >= 500 else 0)
-    if (tensor_chain or args.dd == "df64") and not args.no_fp64_compare:
+    sig64 = None
+    if (tensor_chain or args.dd == "df64" or args.precision == "df64") and \
+            not args.no_fp64_compare:
         step(replicas.rank_seed(rank, 990_001), **plain)  # tunes the fp64 chain shapes
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -426,6 +433,7 @@ def our_arm(args):
         st_ref = sig - 0.5 * (sdd + sdd.transpose(1, 2))
         err_sigma = float(torch.linalg.norm(sig_first - sig) / torch.linalg.norm(sig))
         err_st = float(torch.linalg.norm(sig_first - sig) / torch.linalg.norm(st_ref))
+        sig64, st_ref64 = sig.clone(), st_ref.clone()
         res64 = [(e64, se64, st64["t_setup_ms"] + st64["t_green_dd_ms"], st64["t_sample_ms"])]
         compare = {"plain_fp64_units_per_s": ns * nt / (ms64 / 1e3),
                    "plain_fp64_ms_per_step": ms64,
@@ -440,6 +448,37 @@ def our_arm(args):
                        "e_stderr": se64},
                    "time_to_1mEh_plain_fp64_s": time_to_target(res64, ns, 1e-3)}
 
+    # the reduced-precision tensor-core form: throughput, and its error against
+    # the IEEE fp64 form on the same draws
+    reduced = None
+    if args.reduced != "none" and not tensor_chain and sig64 is not None:
+        rp = prec_code[args.reduced]
+        er, ser, _ = step(replicas.rank_seed(rank, 0), precision=rp)  # graph capture + error
+        torch.cuda.synchronize()
+        d = sig - sig64
+        err = {"sigma_rel_fro": float(torch.linalg.norm(d) / torch.linalg.norm(sig64)),
+               "sigma_stochastic_part_rel_fro": float(torch.linalg.norm(d) /
+                                                      torch.linalg.norm(st_ref64)),
+               "e_corr_abs": abs(er - e64), "e_corr_rel": abs(er - e64) / abs(e64),
+               "e_stderr": se64}
+        step(replicas.rank_seed(rank, 990_002), precision=rp)
+        torch.cuda.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        rres = []
+        r0.record(stream)
+        for k in range(args.steps):
+            e_, se_, st_ = step(replicas.rank_seed(rank, k), precision=rp)
+            rres.append((e_, se_, st_["t_setup_ms"] + st_["t_green_dd_ms"], st_["t_sample_ms"]))
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rms = r0.elapsed_time(r1) / args.steps
+        reduced = {"precision": args.reduced, "units_per_s": ns * nt / (rms / 1e3),
+                   "ms_per_step": rms,
+                   "sampling_ms_per_step": float(np.mean([r[3] for r in rres])),
+                   "vs_fp64_same_seed": err,
+                   "time_to_1mEh_s": time_to_target(rres, ns, 1e-3)}
+
     # Sec. IV: the range-separated estimator against plain stochastic RI at the
     # same number of sample pairs and the same seed
     e_sri, se_sri, _ = step(replicas.rank_seed(rank, 0), estimator=binding.RSSRI_EST_SRI)
@@ -452,17 +491,19 @@ def our_arm(args):
     # estimate with it on the first timed seed, next to the plain estimate
     cv_report = None
     if args.cv:
+        # the control variate needs F and F^L separately: fp64 or double-float chain
+        cvp = prec if args.precision in ("fp64", "df64") else binding.RSSRI_PREC_FP64
         tr = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 777),
-                                    dd_arith=dd)
+                                    dd_arith=dd, precision=cvp)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=tr)
         c0 = time.perf_counter()
         lb, la = h.cv_train(tr, synth.mlp_init(0), 400, 4096, 1e-3)
         t_train = time.perf_counter() - c0
-        ev = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=dd)
+        ev = dict(precision=cvp, dd_arith=dd)
         e_cv, se_cv, st_cv = step(replicas.rank_seed(rank, 0), **ev,
                                   estimator=binding.RSSRI_EST_CV)
         o_cv = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 0),
-                                      dd_arith=dd, cv=1)
+                                      dd_arith=dd, cv=1, precision=cvp)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o_cv)
         e_l, se_l, st_l = h.sigma(o_cv, sig, ep)
         cv_report = {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
@@ -523,7 +564,10 @@ def our_arm(args):
     name = binding.PROF_CLASSES[dom]
     per_launch_gf = prof_gf[dom] / max(prof_l[dom], 1)
     achieved = prof_gf[dom] / (prof_ms[dom] / 1e3) / 1e3  # TFLOP/s
-    if name in ("dd_spmm", "dd_gemm") and args.dd == "df64":
+    df64_class = ((name in ("dd_spmm", "dd_gemm") and args.dd == "df64") or
+                  (name in ("chain_gemm", "factor_gemm", "setup_gemm") and
+                   args.precision == "df64"))
+    if df64_class:
         peak = DF64_PEAK_TFLOPS
         psrc = ("derived: 152 SMs x 128 fp32 lanes x 2070 MHz / 12 fp32 instructions per "
                 "double-float multiply-add x 2 flop (fp64-equivalent)")
@@ -558,8 +602,9 @@ def our_arm(args):
             "value": value, "unit": "units/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": (args.precision + "+" if tensor_chain else "") +
-                     ("df64+f64" if args.dd == "df64" else "f64"), "data": "synthetic",
+            "dtype": "+".join(([args.precision] if tensor_chain else []) +
+                              (["df64"] if "df64" in (args.precision, args.dd) else []) +
+                              ["f64"]), "data": "synthetic",
             "config": {"workload": f"{args.workload}: N={n} n_occ={s.n_occ} N_aux={s.n_aux} "
                                    f"N_tau={nt} N_s={ns} eps={cfg['eps']} "
                                    f"eps'={cfg['eps_prime']}, whole path per step",
@@ -574,6 +619,7 @@ def our_arm(args):
                       "time_to_1mEh_s": time_to_target(results, ns, 1e-3),
                       "classes": classes, "tensor_roofline": tensor,
                       "chosen_vs_plain_fp64": compare, "rs_vs_sri_same_n_s": rs_vs_sri,
+                      "reduced_precision_form": reduced,
                       "learned_control_variate": cv_report,
                       "literal_estimator": literal_report,
                       "many_systems": many_report}}

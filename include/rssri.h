@@ -93,8 +93,13 @@ enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1, RSSRI_EST_LITERAL = 2 };
  * RSSRI_PREC_TF32: the same split with operands rounded to tf32 (10 stored
  *   mantissa bits, kept in fp32 storage) and fp32 accumulation: about 8x
  *   smaller operand rounding than bf16 at twice the operand bytes and half
- *   the tensor-core rate. */
-enum { RSSRI_PREC_FP64 = 0, RSSRI_PREC_BF16 = 1, RSSRI_PREC_TF32 = 2 };
+ *   the tensor-core rate.
+ * RSSRI_PREC_DF64: the plain form's products in double-float arithmetic on
+ *   the fp32 pipes (each fp64 value as a pair of floats, error-free products
+ *   and sums, ~1e-13 relative): fp64-accurate, within the same 1e-10 of the
+ *   fp64 form, and several times faster on GPUs whose fp64 rate is a small
+ *   fraction of their fp32 rate. */
+enum { RSSRI_PREC_FP64 = 0, RSSRI_PREC_BF16 = 1, RSSRI_PREC_TF32 = 2, RSSRI_PREC_DF64 = 3 };
 
 typedef struct rssri_handle rssri_handle;
 
@@ -143,8 +148,8 @@ typedef struct {
  *              concatenate exactly), xi_offset + n_s < 2^40.
  *   estimator  RSSRI_EST_CV, RSSRI_EST_SRI or RSSRI_EST_LITERAL (the last
  *              with precision RSSRI_PREC_FP64 and cv = 0).
- *   precision  RSSRI_PREC_FP64, RSSRI_PREC_BF16 or RSSRI_PREC_TF32 (chain
- *              products only).
+ *   precision  RSSRI_PREC_FP64, RSSRI_PREC_BF16, RSSRI_PREC_TF32 or
+ *              RSSRI_PREC_DF64 (chain products only).
  *   pair_batch sample pairs processed per group of launches (0 = all;
  *              fp64 chain only, the tensor-core chains take all pairs at once).
  *   profile    1: time every kernel class with CUDA events on the handle's

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "librssri.so")
 
 RSSRI_PTR_DEVICE, RSSRI_PTR_HOST = 0, 1
 RSSRI_EST_CV, RSSRI_EST_SRI, RSSRI_EST_LITERAL = 0, 1, 2
-RSSRI_PREC_FP64, RSSRI_PREC_BF16, RSSRI_PREC_TF32 = 0, 1, 2
+RSSRI_PREC_FP64, RSSRI_PREC_BF16, RSSRI_PREC_TF32, RSSRI_PREC_DF64 = 0, 1, 2, 3
 RSSRI_DD_FP64, RSSRI_DD_DF64 = 0, 1
 BUF = dict(W=0, COLMAX=1, ERI_L=2, K_L=3, THETA=4, R=5, R_L=6, G=7, GB=8, SIGMA_DD=9,
            SIGMA_RAW=10, CV_PARAMS=11, CV_C=12)

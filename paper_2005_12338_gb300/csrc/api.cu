@@ -93,6 +93,8 @@ struct rssri_handle {
   DevBuf eri_hl, ut_hl;
   // pair copies of the Newton-Schulz operands (double-float metric root)
   DevBuf nsA2, nsB2;
+  // double-float chain: factor pairs, X G and C pairs, (2tI - B) pairs
+  DevBuf facHl, xgHl, cHl, bHl;
   bool d_df64_ready = false;
   // bf16 chain buffers
   DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
@@ -206,7 +208,7 @@ int validate_options(const rssri_options *o, bool for_sigma) {
     if (o->estimator == RSSRI_EST_LITERAL && (o->precision != RSSRI_PREC_FP64 || o->cv != 0))
       return RSSRI_ERR_INVALID_ARG;
     if (o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_BF16 &&
-        o->precision != RSSRI_PREC_TF32)
+        o->precision != RSSRI_PREC_TF32 && o->precision != RSSRI_PREC_DF64)
       return RSSRI_ERR_INVALID_ARG;
     if (o->pair_batch < 0) return RSSRI_ERR_INVALID_ARG;
     if (o->dd_arith != RSSRI_DD_FP64 && o->dd_arith != RSSRI_DD_DF64) return RSSRI_ERR_INVALID_ARG;
@@ -392,7 +394,7 @@ void rssri_destroy(rssri_handle *h) {
                     &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
                     &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
                     &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
-                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
+                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->facHl, &h->xgHl, &h->cHl, &h->bHl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
                     &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss};
   for (DevBuf *b : bufs) release(*b);
@@ -658,6 +660,14 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   return cudaSuccess;
+}
+
+// A double-float product counted under kernel class `cls`.
+cudaError_t df_gemm_c(rssri_handle *h, int cls, const DfGemm &g) {
+  SPAN(cls, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
+  const size_t need = df_gemm_work(g) * sizeof(double);
+  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
+  return df_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
 }
 
 // A double-float product counted under the deterministic-block GEMM class.
@@ -1054,7 +1064,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   if (!sigma && !collect_stats) return RSSRI_ERR_INVALID_ARG;
   const bool use_cv = o->cv != 0;
   if ((use_cv || collect_stats) &&
-      (o->precision != RSSRI_PREC_FP64 || o->estimator != RSSRI_EST_CV))
+      ((o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_DF64) ||
+       o->estimator != RSSRI_EST_CV))
     return RSSRI_ERR_INVALID_ARG;
   if (use_cv && !h->cv_ready) return RSSRI_ERR_NOT_READY;
   if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
@@ -1075,6 +1086,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   const bool bf16 = o->precision == RSSRI_PREC_BF16 || o->precision == RSSRI_PREC_TF32;
   const int tc_kind = o->precision == RSSRI_PREC_TF32 ? TC_TF32 : TC_BF16;
   if (bf16 && (n < 16 || !tc_available())) return RSSRI_ERR_INVALID_ARG;
+  // the chain in double-float (fp64-accurate) instead of IEEE fp64
+  const bool chain_df64 = o->precision == RSSRI_PREC_DF64;
   cudaError_t e;
 #define RS_CK(x)                                       \
   do {                                                 \
@@ -1104,8 +1117,15 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   RS_CK(ensure(h->fac, (size_t)4 * ns * nn * sizeof(double)));  // [set][kind][xi][n][n]
   RS_CK(ensure(h->RLp, (size_t)2 * ns * std::max(h->P, 1) * sizeof(double)));
   if (!bf16) {
-    RS_CK(ensure(h->XG, (size_t)nbat2 * nn * sizeof(double)));
-    RS_CK(ensure(h->Cc, (size_t)nbat2 * nn * sizeof(double)));
+    if (chain_df64) {
+      RS_CK(ensure(h->facHl, (size_t)4 * ns * nn * sizeof(float2)));
+      RS_CK(ensure(h->xgHl, (size_t)nbat2 * nn * sizeof(float2)));
+      RS_CK(ensure(h->cHl, (size_t)nbat2 * nn * sizeof(float2)));
+      RS_CK(ensure(h->bHl, (size_t)nbat2 * nn * sizeof(float2)));
+    } else {
+      RS_CK(ensure(h->XG, (size_t)nbat2 * nn * sizeof(double)));
+      RS_CK(ensure(h->Cc, (size_t)nbat2 * nn * sizeof(double)));
+    }
     RS_CK(ensure(h->Bm, (size_t)nbat2 * nn * sizeof(double)));
     RS_CK(ensure(h->BC, (size_t)nbat2 * nn * sizeof(double)));
   }
@@ -1157,7 +1177,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   }
   // ---- S7: deterministic block per tau
   const bool dd_df64 = !sri && P > 0 && o->dd_arith == RSSRI_DD_DF64;
-  if (dd_df64) {
+  if (dd_df64 || chain_df64) {
+    RS_CK(ensure(h->GGhl, (size_t)2 * nt * nn * sizeof(float2)));
     SPAN(RSSRI_PROF_OTHER, 0.0);
     RS_CK(to_df64(G, nt * nn, h->GGhl.as<float2>(), s));
     RS_CK(to_df64(Gb, nt * nn, h->GGhl.as<float2>() + nt * nn, s));
@@ -1238,6 +1259,11 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
                           nn, nn, fac + (2LL * set + 1) * ns * nn, s)); }
   }
 
+  if (chain_df64) {
+    SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_CK(to_df64(fac, 4LL * ns * nn, h->facHl.as<float2>(), s));
+  }
+
   // ---- learned control variate: coefficients, or statistics for training
   if (use_cv) {
     RS_CK(cv_compute_c(h, G, Gb));
@@ -1264,7 +1290,30 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
     for (int x0 = 0; x0 < ns; x0 += nb) {
       const int cnt = std::min(nb, ns - x0);
       // the batch is [kind][x]
-      for (int kind = 0; kind < nkind; ++kind) {
+      if (chain_df64) {
+        // the same products on (hi, lo) pairs: X G and C = X G Y kept as pairs,
+        // B = C Gb in fp64 for the fold
+        const float2 *fh = h->facHl.as<float2>();
+        const float2 *Gh = h->GGhl.as<float2>() + t * nn, *Gbh = h->GGhl.as<float2>() + (nt + t) * nn;
+        for (int kind = 0; kind < nkind; ++kind) {
+          const int xk = (kind == 0 || kind == 2) ? 0 : 1, yk = (kind == 0 || kind == 3) ? 0 : 1;
+          const float2 *X = fh + ((0LL * 2 + xk) * ns + x0) * nn;
+          const float2 *Y = fh + ((1LL * 2 + yk) * ns + x0) * nn;
+          float2 *xg = h->xgHl.as<float2>() + (long long)kind * cnt * nn;
+          float2 *c = h->cHl.as<float2>() + (long long)kind * cnt * nn;
+          DfGemm g;
+          g.M = n; g.N = n; g.K = n; g.batch = cnt;
+          g.lda = g.ldb = g.ldc = n;
+          g.A = X; g.sA = nn; g.B = Gh; g.sB = 0; g.C2 = xg; g.sC = nn;   // X G
+          RS_CK(df_gemm_c(h, RSSRI_PROF_CHAIN_GEMM, g));
+          g.A = xg; g.sA = nn; g.B = Y; g.sB = nn; g.C2 = c; g.sC = nn;   // C = X G Y
+          RS_CK(df_gemm_c(h, RSSRI_PROF_CHAIN_GEMM, g));
+          g.A = c; g.sA = nn; g.B = Gbh; g.sB = 0; g.C2 = nullptr;        // B = C Gb
+          g.C64 = Bm + (long long)kind * cnt * nn; g.sC = nn;
+          RS_CK(df_gemm_c(h, RSSRI_PROF_CHAIN_GEMM, g));
+        }
+      }
+      for (int kind = 0; kind < nkind && !chain_df64; ++kind) {
         const int xk = (kind == 0 || kind == 2) ? 0 : 1, yk = (kind == 0 || kind == 3) ? 0 : 1;
         const double *X = fac + ((0LL * 2 + xk) * ns + x0) * nn;
         const double *Y = fac + ((1LL * 2 + yk) * ns + x0) * nn;
@@ -1283,7 +1332,15 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
       const int tot = cnt * nkind;
       // t = Tr B, s2 = Tr B B, B <- +-(2 t I - B)
       { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(chain_fold(Bm, tot, literal ? 2 * cnt : cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s)); }
-      {
+      if (chain_df64) {
+        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(Bm, (long long)tot * nn, h->bHl.as<float2>(), s)); }
+        DfGemm g;
+        g.M = n; g.N = n; g.K = n; g.batch = tot;
+        g.lda = g.ldb = g.ldc = n;
+        g.A = h->bHl.as<float2>(); g.sA = nn; g.B = h->cHl.as<float2>(); g.sB = nn;
+        g.C64 = BC; g.sC = nn;  // (2tI - B) C
+        RS_CK(df_gemm_c(h, RSSRI_PROF_CHAIN_GEMM, g));
+      } else {
         GemmArgs g;
         g.M = n; g.N = n; g.K = n; g.batch = tot;
         g.lda = g.ldb = g.ldc = n;

@@ -40,13 +40,16 @@ __global__ void to_df64_kernel(const double *__restrict__ x, long long len, floa
 // compiler.  G64: 64 x 64 tiles (256 threads); G40: 40 x 40 tiles (64
 // threads, 25 outputs each), for shapes such as N = 200 and N_aux = 600 that
 // 64-wide tiles would pad by up to 64%.
-template <int TY_, int TX_, int TI_, int TJ_, int BK_, int MINB_>
+// KU: how many k steps of a slab are unrolled; a fully unrolled slab (3-5 k
+// steps x 16-25 multiply-adds x 12 instructions each) outgrew the instruction
+// cache (ncu: "no instruction" the top stall).
+template <int TY_, int TX_, int TI_, int TJ_, int BK_, int MINB_, int KU_>
 struct DfGeo {
-  static constexpr int TY = TY_, TX = TX_, TI = TI_, TJ = TJ_, BK = BK_, MINB = MINB_;
+  static constexpr int TY = TY_, TX = TX_, TI = TI_, TJ = TJ_, BK = BK_, MINB = MINB_, KU = KU_;
   static constexpr int BM = TY * TI, BN = TX * TJ, NT = TY * TX;
 };
-using G64 = DfGeo<16, 16, 4, 4, 16, 2>;
-using G40 = DfGeo<8, 8, 5, 5, 8, 6>;
+using G64 = DfGeo<16, 16, 4, 4, 16, 2, 4>;
+using G40 = DfGeo<8, 8, 5, 5, 8, 6, 1>;
 
 template <class GEO, int MODE, int TA, int TB, int OUT>
 __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
     for (int kt = kbeg; kt < kend; kt += DBK) {
       const bool more = kt + DBK < kend;
       if (more) load(kt + DBK);
-#pragma unroll
+#pragma unroll GEO::KU
       for (int kk = 0; kk < DBK; ++kk) {
         float2 a[TI], bb[TJ];
 #pragma unroll

@@ -36,10 +36,10 @@ def rel(a, b):
 
 
 def run_gpu(B, s, eps_prime, eps, n_s, seed, host=False, estimator=0, xi_offset=0, pair_batch=0,
-            g=None, gb=None, dd_arith=0):
+            g=None, gb=None, dd_arith=0, precision=0):
     h = B.Handle(0)
     opts = B.Handle.options(eps_prime, eps, n_s, seed, xi_offset, estimator, pair_batch,
-                            dd_arith=dd_arith)
+                            dd_arith=dd_arith, precision=precision)
     arrs = [s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w]
     if host:
         sig = np.empty((s.n_tau, s.n, s.n))
@@ -134,6 +134,28 @@ def test_parity_double_float_deterministic_block(B, case):
     h, got = run_gpu(B, s, c["eps_prime"], c["eps"], c["n_s"], c["seed"], dd_arith=1)
     compare_all(h, got, ref, s)
     h.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_parity_double_float_everywhere(B, case):
+    """The fp64-accurate fast form: chain products and deterministic block in
+    double-float (RSSRI_PREC_DF64 with RSSRI_DD_DF64) meet the fp64 bar of 1e-10."""
+    c = CASES[case]
+    s = synth.make_system(*c["sys"], input_seed=1)
+    ref = run_oracle(s, c["eps_prime"], c["eps"], c["n_s"], c["seed"])
+    h, got = run_gpu(B, s, c["eps_prime"], c["eps"], c["n_s"], c["seed"], dd_arith=1,
+                     precision=B.RSSRI_PREC_DF64)
+    compare_all(h, got, ref, s)
+    h.close()
+
+
+def test_double_float_chain_pair_batches(B):
+    s = synth.make_system(30, 12, 60, 3, input_seed=6)
+    _, a = run_gpu(B, s, 0.02, 1e-2, 9, 4, dd_arith=1, precision=B.RSSRI_PREC_DF64)
+    _, b = run_gpu(B, s, 0.02, 1e-2, 9, 4, dd_arith=1, precision=B.RSSRI_PREC_DF64,
+                   pair_batch=4)
+    assert rel(b["sigma"], a["sigma"]) < 1e-13
+    assert np.abs(b["e_pair"] - a["e_pair"]).max() < 1e-13 * abs(a["e_corr"])
 
 
 def test_host_pointers_deterministic_and_batched(B):
