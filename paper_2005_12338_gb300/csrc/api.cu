@@ -1331,9 +1331,9 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
       }
       const int tot = cnt * nkind;
       // t = Tr B, s2 = Tr B B, B <- +-(2 t I - B)
-      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(chain_fold(Bm, tot, literal ? 2 * cnt : cnt, n, h->tarr.as<double>(), h->sarr.as<double>(), s)); }
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(chain_fold(Bm, tot, literal ? 2 * cnt : cnt, n, h->tarr.as<double>(), h->sarr.as<double>(),
+                                                      chain_df64 ? h->bHl.as<float2>() : nullptr, s)); }
       if (chain_df64) {
-        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(Bm, (long long)tot * nn, h->bHl.as<float2>(), s)); }
         DfGemm g;
         g.M = n; g.N = n; g.K = n; g.batch = tot;
         g.lda = g.ldb = g.ldc = n;

@@ -465,24 +465,45 @@ __global__ void dd_fold_kernel(const int *__restrict__ prow, const int *__restri
 }
 
 // ------------------------------------------------------------------ S8 ----
+// One block per batch entry.  Tr(B B) = sum_ij B_ij B_ji is taken over pairs of
+// 32 x 32 tiles staged in shared memory (both tiles read coalesced), then the
+// entry is overwritten with sgn (2 t I - B), or written as (hi, lo) float pairs
+// into Bhl when that is given (the double-float chain's next operand).
 __global__ void chain_fold_kernel(double *__restrict__ Bm, int npos, int n, double *__restrict__ t,
-                                  double *__restrict__ s2) {
+                                  double *__restrict__ s2, float2 *__restrict__ Bhl) {
+  __shared__ double ta[32][33], tb[32][33];
   const int b = blockIdx.x;
   const long long nn = (long long)n * n;
   double *B = Bm + (long long)b * nn;
   double tl = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tl += B[(long long)i * n + i];
   const double tr = block_sum(tl);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+  const int ntile = (n + 31) / 32;
   double sl = 0.0;
-  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-    const long long i = e / n, j = e - i * n;
-    sl += B[e] * B[j * n + i];
-  }
+  for (int bi = 0; bi < ntile; ++bi)
+    for (int bj = 0; bj < ntile; ++bj) {
+      __syncthreads();
+      for (int r = ty; r < 32; r += nty) {
+        const int i = bi * 32 + r, j = bj * 32 + tx;        // tile (bi, bj)
+        const int i2 = bj * 32 + r, j2 = bi * 32 + tx;      // tile (bj, bi)
+        ta[r][tx] = (i < n && j < n) ? B[(long long)i * n + j] : 0.0;
+        tb[r][tx] = (i2 < n && j2 < n) ? B[(long long)i2 * n + j2] : 0.0;
+      }
+      __syncthreads();
+      for (int r = ty; r < 32; r += nty) sl += ta[r][tx] * tb[tx][r];  // B_ij B_ji
+    }
   const double ss = block_sum(sl);  // ends with a barrier: all reads are done
   const double sg = (b < npos) ? 1.0 : -1.0;
   for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
     const long long i = e / n, j = e - i * n;
-    B[e] = sg * (((i == j) ? 2.0 * tr : 0.0) - B[e]);
+    const double v = sg * (((i == j) ? 2.0 * tr : 0.0) - B[e]);
+    if (Bhl) {
+      const float hi = __double2float_rn(v);
+      Bhl[(long long)b * nn + e] = make_float2(hi, __double2float_rn(v - (double)hi));
+    } else {
+      B[e] = v;
+    }
   }
   if (threadIdx.x == 0) {
     t[b] = tr;
@@ -851,8 +872,8 @@ cudaError_t dd_fold_direct(const int *prow, const int *pcol, const double *L, in
 }
 
 cudaError_t chain_fold(double *Bm, int nb, int npos, int n, double *t, double *s2,
-                       cudaStream_t s) {
-  chain_fold_kernel<<<nb, 256, 0, s>>>(Bm, npos, n, t, s2);
+                       float2 *Bhl, cudaStream_t s) {
+  chain_fold_kernel<<<nb, 256, 0, s>>>(Bm, npos, n, t, s2, Bhl);
   RS_LAUNCHED();
   return cudaSuccess;
 }

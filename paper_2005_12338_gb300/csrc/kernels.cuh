@@ -73,9 +73,10 @@ cudaError_t dd_fold_direct(const int *prow, const int *pcol, const double *L, in
 
 // ---------------------------------------------------------------- S8 ------
 // Per batch entry b (n x n): t[b] = Tr B, s2[b] = Tr(B B), then
-// B <- sgn (2 t I - B) with sgn = +1 for b < npos, -1 otherwise.
+// B <- sgn (2 t I - B) with sgn = +1 for b < npos, -1 otherwise; when Bhl is
+// given the result goes there as (hi, lo) float pairs and B is left as is.
 cudaError_t chain_fold(double *Bm, int nb, int npos, int n, double *t, double *s2,
-                       cudaStream_t s);
+                       float2 *Bhl, cudaStream_t s);
 // sig[i][j] (+)= sum_x sum_{k < nkind} BC[k nh + x][i][j] / ns_div;
 // init: sig = base + ..., else sig += ...
 cudaError_t sigma_accumulate(const double *BC, int nh, int nkind, int n, double ns_div,
