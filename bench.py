@@ -8,6 +8,9 @@ the Rademacher draws, R and R^L, the chain products for every (sample pair,
 tau) unit, the energy and the symmetrised output.  The metric is Sigma(tau)
 units per second, a unit being one (sample pair, tau point); inputs are
 resident in HBM when the timed region starts.  Every step draws a new seed.
+The timed form computes every product in double-float arithmetic (fp64
+accurate: within 1e-10 of the fp64 oracle); the IEEE-fp64 form and a
+reduced-precision tensor-core form are timed beside it for comparison.
 
 Multi-GPU: one process per GPU (torchrun); every rank runs independent
 replicas with its own seeds, no collective on the data path (weak scaling).
@@ -37,7 +40,7 @@ WORKLOAD = "c2_n200"
 # fp64 ALU peak of the DFMA pipe: 152 SMs x 2 fp64 FMA/clock/SM x 2 flop x
 # 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# Double-float multiply-add (the exchange contraction with --dd df64): 12 fp32
+# Double-float multiply-add (--dd df64, --precision df64): 12 fp32
 # instructions each (TwoProduct with 3 fma, TwoSum, error collection) on
 # 152 SMs x 128 fp32 lanes x 2070 MHz, counted as 2 fp64-equivalent flop.
 DF64_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
