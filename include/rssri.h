@@ -151,12 +151,14 @@ typedef struct {
  *   precision  RSSRI_PREC_FP64, RSSRI_PREC_BF16, RSSRI_PREC_TF32 or
  *              RSSRI_PREC_DF64 (chain products only).
  *   pair_batch sample pairs processed per group of launches (0 = all;
- *              fp64 chain only, the tensor-core chains take all pairs at once).
+ *              fp64 and double-float chains; the tensor-core chains take all
+ *              pairs at once).
  *   profile    1: time every kernel class with CUDA events on the handle's
  *              stream (rssri_stats.prof_*); 0: off.
  *   cv         1: weight the large-part control variate element-wise by the
  *              coefficients c_ij(tau) of the network trained by
- *              rssri_cv_train (fp64 chain and RSSRI_EST_CV only); 0: c = 1.
+ *              rssri_cv_train (fp64 or double-float chain and RSSRI_EST_CV
+ *              only); 0: c = 1.
  *   dd_arith   arithmetic of the deterministic block (its products and
  *              exchange contraction): RSSRI_DD_FP64 (IEEE fp64 FMAs) or
  *              RSSRI_DD_DF64 (double-float: each fp64 value as a pair of
@@ -338,8 +340,8 @@ RSSRI_API int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, 
  * W2[256][256] b2[256] W3[1][256] b3[1]. */
 #define RSSRI_CV_NPARAM 134657
 
-/* Train the network on an independent run: evaluates the fp64 chain with
- * options `o` (precision FP64, estimator CV; use a seed not used for the
+/* Train the network on an independent run: evaluates the chain with options
+ * `o` (precision FP64 or DF64, estimator CV; use a seed not used for the
  * estimates), collects per-element sums of F, F^L and their products, forms
  * the targets c* and weights Var(F^L), and runs `steps` Adam steps (learning
  * rate lr, betas 0.9/0.999) on minibatches of `batch` elements, minimising
