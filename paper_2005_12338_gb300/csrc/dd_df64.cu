@@ -43,17 +43,13 @@ __global__ void to_df64_kernel(const double *__restrict__ x, long long len, floa
 // KU: how many k steps of a slab are unrolled; a fully unrolled slab (3-5 k
 // steps x 16-25 multiply-adds x 12 instructions each) outgrew the instruction
 // cache (ncu: "no instruction" the top stall).
-// TS: keep the float-pair running totals in shared memory ([output][thread])
-// instead of registers; they are touched only every 256 terms, and the
-// registers saved buy resident warps.
-template <int TY_, int TX_, int TI_, int TJ_, int BK_, int MINB_, int KU_, bool TS_>
+template <int TY_, int TX_, int TI_, int TJ_, int BK_, int MINB_, int KU_>
 struct DfGeo {
   static constexpr int TY = TY_, TX = TX_, TI = TI_, TJ = TJ_, BK = BK_, MINB = MINB_, KU = KU_;
-  static constexpr bool TS = TS_;
   static constexpr int BM = TY * TI, BN = TX * TJ, NT = TY * TX;
 };
-using G64 = DfGeo<16, 16, 4, 4, 16, 2, 4, false>;
-using G40 = DfGeo<8, 8, 5, 5, 8, 8, 1, true>;
+using G64 = DfGeo<16, 16, 4, 4, 16, 2, 4>;
+using G40 = DfGeo<8, 8, 5, 5, 8, 6, 1>;
 
 template <class GEO, int MODE, int TA, int TB, int OUT>
 __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
@@ -89,18 +85,12 @@ __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
   // thread (tx, ty) owns rows ty + TY i and columns tx + TX j of the tile, so
   // that a warp's shared-memory reads are a broadcast or two (A) and runs of
   // consecutive pairs (B)
-  constexpr bool TS = GEO::TS;
-  __shared__ float2 Tot[TS ? TI * TJ : 1][TS ? DNT : 1];
-  float TH[TS ? 1 : TI][TS ? 1 : TJ], TL[TS ? 1 : TI][TS ? 1 : TJ];
+  float TH[TI][TJ], TL[TI][TJ];
   float S[TI][TJ], E[TI][TJ];
 #pragma unroll
   for (int i = 0; i < TI; ++i)
 #pragma unroll
-    for (int j = 0; j < TJ; ++j) {
-      S[i][j] = E[i][j] = 0.0f;
-      if constexpr (TS) Tot[i * TJ + j][tid] = make_float2(0.f, 0.f);
-      else TH[i][j] = TL[i][j] = 0.0f;
-    }
+    for (int j = 0; j < TJ; ++j) TH[i][j] = TL[i][j] = S[i][j] = E[i][j] = 0.0f;
   float2 ra[LA], rb[LB];
   const float2 zero = make_float2(0.f, 0.f);
   auto load = [&](int kt) {
@@ -176,13 +166,7 @@ __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
           E[i][j] = __fsub_rn(E[i][j], __fsub_rn(sn, S[i][j]));
           S[i][j] = sn;
           if (slab == FOLD || !more) {
-            if constexpr (TS) {
-              float2 t = Tot[i * TJ + j][tid];
-              df_acc(t.x, t.y, S[i][j], E[i][j]);
-              Tot[i * TJ + j][tid] = t;
-            } else {
-              df_acc(TH[i][j], TL[i][j], S[i][j], E[i][j]);
-            }
+            df_acc(TH[i][j], TL[i][j], S[i][j], E[i][j]);
             S[i][j] = E[i][j] = 0.0f;
           }
         }
@@ -201,15 +185,7 @@ __global__ void __launch_bounds__(GEO::NT, GEO::MINB) df_gemm_kernel(
     for (int j = 0; j < TJ; ++j) {
       const int gj = col0 + tx + TX * j;
       if (gj >= N) continue;
-      float h, l;
-      if constexpr (TS) {
-        const float2 t = Tot[i * TJ + j][tid];
-        h = t.x;
-        l = t.y;
-      } else {
-        h = TH[i][j];
-        l = TL[i][j];
-      }
+      const float h = TH[i][j], l = TL[i][j];
       if (partial) {
         static_cast<double *>(Cv)[(long long)z * M * N + (long long)gi * N + gj] =
             (double)h + (double)l;
