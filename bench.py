@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--many", type=int, default=0,
                     help="also time K independent chains of uneven size (N from 64 to 256) "
                          "one by one and batched on K streams (rssri_sigma_batch)")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -629,15 +630,45 @@ def our_arm(args):
     if not args.no_cpu_baseline and world == 1:
         cb = oracle_sample(s, cfg, 0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        one = oracle_single_thread(args)
+        if one is not None:
+            line["cpu_baseline"]["single_thread"] = one
     print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
         dist.destroy_process_group()
 
 
+def oracle_single_thread(args):
+    """The same bounded oracle sample in a fresh interpreter whose BLAS may use
+    one thread (the environment is set before numpy loads): the baseline's
+    single-core figure.  None if it fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload",
+           args.workload]
+    if args.eps is not None:
+        cmd += ["--eps", str(args.eps)]
+    if args.n_tau is not None:
+        cmd += ["--n-tau", str(args.n_tau)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_sample:
+        cfg = dict(synth.CONFIGS[args.workload])
+        if args.eps is not None:
+            cfg["eps"] = args.eps
+        if args.n_tau is not None:
+            cfg["n_tau"] = args.n_tau
+        s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
+        r = oracle_sample(s, cfg, 0, budget_s=6.0)
+        print(json.dumps({k: r[k] for k in ("value", "unit", "cores")}), flush=True)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         our_arm(args)
