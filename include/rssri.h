@@ -160,11 +160,24 @@ typedef struct {
  *              rssri_cv_train (fp64 or double-float chain and RSSRI_EST_CV
  *              only); 0: c = 1.
  *   dd_arith   arithmetic of the deterministic block (its products and
- *              exchange contraction): RSSRI_DD_FP64 (IEEE fp64 FMAs) or
+ *              exchange contraction): RSSRI_DD_FP64 (IEEE fp64 FMAs),
  *              RSSRI_DD_DF64 (double-float: each fp64 value as a pair of
  *              floats, error-free products and sums on the fp32 pipes, ~1e-13
- *              relative).  The value given to rssri_setup also sets how the
- *              pair-space v^L is formed there. */
+ *              relative; values must stay inside fp32's exponent range, about
+ *              1e-38 to 3e38, or lose their relative precision), or
+ *              RSSRI_DD_OZ (fp64-accurate sliced products on the bf16 tensor
+ *              cores: each row of an fp64 operand is scaled by a power of two
+ *              and split into five 8-bit digits, every digit product and the
+ *              accumulation of the leading levels are exact, ~1e-12 of
+ *              sum |a||b| per dot product, with fp64's exponent range; the
+ *              segmented product K^Q G stays double-float).  RSSRI_DD_OZ
+ *              needs a GPU with tcgen05 (sm_100 family); its R, R^L and
+ *              v^L are formed as for RSSRI_DD_DF64.
+ *              The value given to rssri_setup sets how v^L and
+ *              the cached block are formed; the value given to
+ *              rssri_sigma_from_g sets the arithmetic of its rebuilt block,
+ *              and that given to rssri_sigma the arithmetic of R, R^L and of
+ *              the literal estimator's exchange builds. */
 typedef struct {
   double eps_prime, eps;
   int64_t n_s;
@@ -179,7 +192,7 @@ typedef struct {
   int32_t reserved0;
 } rssri_options;
 
-enum { RSSRI_DD_FP64 = 0, RSSRI_DD_DF64 = 1 };
+enum { RSSRI_DD_FP64 = 0, RSSRI_DD_DF64 = 1, RSSRI_DD_OZ = 2 };
 
 /* Kernel classes of the per-class profile (rssri_stats.prof_*). */
 enum {
@@ -190,6 +203,7 @@ enum {
   RSSRI_PROF_SETUP_GEMM = 4,  /* S1/S3 Newton-Schulz, [K]^L, D                     */
   RSSRI_PROF_GREEN = 5,       /* S6                                               */
   RSSRI_PROF_OTHER = 6,       /* screening, compaction, cuts, folds, reductions   */
+  RSSRI_PROF_SLICE = 7,       /* digit slicing of the operands of RSSRI_DD_OZ      */
   RSSRI_PROF_NCLASS = 8
 };
 
@@ -206,8 +220,9 @@ typedef struct {
   double e_dd;              /* Eq. 26 for the deterministic block alone          */
   double e_corr;            /* Eq. 26 for the full estimate                      */
   double e_stderr;          /* sample std of the per-pair energies / sqrt(n_s)   */
-  double t_setup_ms;        /* device time of rssri_setup                        */
-  double t_green_dd_ms;     /* device time of G(tau) and Sigma_DD(tau)           */
+  double t_setup_ms;        /* device time of rssri_setup (S1-S3, S6, S7)        */
+  double t_green_dd_ms;     /* device time of G(tau) and Sigma_DD(tau) in the last
+                               sampling call (0 when it reused the setup's)     */
   double t_sample_ms;       /* device time of theta, R, chains, energy, output   */
   int64_t kernel_launches;  /* kernels launched by the last setup + sigma        */
   int64_t prof_launches[RSSRI_PROF_NCLASS]; /* per class, last setup + sigma      */
@@ -215,6 +230,10 @@ typedef struct {
   double prof_gflop[RSSRI_PROF_NCLASS]; /* algorithmic fp64 GFLOP per class: 2mnk
                                            per product, 2 N_aux P^2 per S7 exchange
                                            contraction (P kept pairs)            */
+  double prof_tensor_gflop[RSSRI_PROF_NCLASS]; /* GFLOP issued to the tensor cores
+                                           per class (digit products of the sliced
+                                           block and bf16/tf32 chain products, over
+                                           the padded tiles actually computed)   */
 } rssri_stats;
 
 /* ------------------------------------------------------------- lifetime */
@@ -233,36 +252,42 @@ RSSRI_API const char *rssri_status_string(int code);
 
 /* ----------------------------------------------------------- the path */
 
-/* Steps that depend only on the system and the thresholds:
+/* Steps that depend only on the system, the thresholds and G:
  *   S1  W = V^{-1/2} (Eq. 7) by the coupled Newton-Schulz iteration (fp64);
  *   S2  screen (ij|A) with eps' (Eq. 11) and compact the kept (i,j) pairs;
  *   S3  [K]^L = (ij|A)^L W on the kept pairs (Eq. 12), cut at eps (Eq. 13),
  *       and the pair-space product D = [K]^L [K]^L^T used by the exchange
- *       part of the deterministic block.
- * Copies the problem into handle-owned device memory (from host or device
- * pointers, per p->ptr_kind).  Errors: INVALID_ARG (sizes, thresholds, null
- * pointers, tau outside (0, beta)), NONSYMMETRIC_ERI, NOT_SPD, NONFINITE,
- * OOM, CUDA. */
+ *       part of the deterministic block;
+ *   S6  G(tau), G(beta - tau) (Eq. 17) for every tau of the grid;
+ *   S7  Sigma_DD(tau): Eq. 20 on v^L = sum_Q [K^Q]^L [K^Q]^L (the terms of
+ *       Eq. 25 that hold no stochastic factor), in the arithmetic o->dd_arith.
+ * S6 and S7 do not depend on the draws: their results stay in the handle and
+ * every rssri_sigma call on this setup reuses them (rssri_stats.t_green_dd_ms
+ * is then 0).  Copies the problem into handle-owned device memory when it is
+ * given in host memory; device arrays are referenced until the next setup.
+ * Errors: INVALID_ARG (sizes, thresholds, dd_arith, null pointers, tau outside
+ * (0, beta)), NONSYMMETRIC_ERI, NOT_SPD, NONFINITE, OOM, CUDA. */
 RSSRI_API int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o);
 
-/* Steps that depend on the sample draws and on G, for every tau of the grid:
+/* Steps that depend on the sample draws, for every tau of the grid:
  *   S4  theta, theta' (Rademacher) and u = W theta;
  *   S5  R = (ij|A) u (Eq. 9), R^L = [K]^L theta (Eq. 14);
- *   S6  G(tau), G(beta - tau) (Eq. 17);
- *   S7  Sigma_DD(tau): Eq. 20 on v^L = sum_Q [K^Q]^L [K^Q]^L (fp64);
  *   S8  per sample pair and factor pair (X, Y): C = X G Y, t = Tr(C Gb),
  *       B = C Gb, accumulate (2 t C - B C) with weight +-1/N_s (Eq. 25);
  *   S9  E_corr (Eq. 26, sign taken so that a Hartree-Fock G gives the MP2
  *       energy per electron: E_corr = -(1/N_e) sum_tau w_tau Tr[Sigma Gb]),
  *       per-pair energies and their standard error;
- *   S10 sigma = (Sigma + Sigma^T)/2.
+ *   S10 sigma = (Sigma + Sigma^T)/2,
+ * on top of the G(tau) and Sigma_DD(tau) of the setup (S6, S7).  If the last
+ * call on the handle was rssri_sigma_from_g, S6 and S7 are first rebuilt for
+ * the orbitals' G with the setup's dd_arith.
  * Outputs (kind per the problem's ptr_kind):
  *   sigma   [n_tau][n][n]  overwritten
  *   e_pair  [n_s] per-pair estimates of E_corr (their mean is E_corr), or NULL
  *   e_corr, e_stderr       host scalars, either may be NULL
  *   st      host stats, may be NULL
  * o->eps_prime and o->eps are ignored here: the split made by rssri_setup
- * is used.  Errors: NOT_READY, INVALID_ARG, NONFINITE, OOM, CUDA. */
+ * is used.  Errors: NOT_READY, INVALID_ARG, NONFINITE, OOM, CUDA, TIMEOUT. */
 RSSRI_API int rssri_sigma(rssri_handle *h, const rssri_options *o, double *sigma,
                 double *e_pair, double *e_corr, double *e_stderr,
                 rssri_stats *st);
@@ -270,7 +295,8 @@ RSSRI_API int rssri_sigma(rssri_handle *h, const rssri_options *o, double *sigma
 /* As rssri_sigma, but with G(tau) and G(beta - tau) supplied by the caller
  * (the paper's general, e.g. self-consistent, G of Eq. 17) instead of being
  * built from the orbitals: g and gb are [n_tau][n][n], each matrix symmetric,
- * of the problem's ptr_kind. */
+ * of the problem's ptr_kind.  The deterministic block (S7) is rebuilt for
+ * this G in the arithmetic o->dd_arith on every call. */
 RSSRI_API int rssri_sigma_from_g(rssri_handle *h, const rssri_options *o,
                        const double *g, const double *gb, double *sigma,
                        double *e_pair, double *e_corr, double *e_stderr,

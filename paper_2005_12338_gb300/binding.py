@@ -1,4 +1,4 @@
-"""ctypes binding of librssri (include/rssri.h): argument marshalling only.
+"""ctypes binding of librssri (include/*.h): argument marshalling only.
 
 Every computation runs in the CUDA library.  There is no CPU fallback: if the
 library cannot be loaded, `lib()` raises.  The functions keep the C names;
@@ -19,11 +19,12 @@ LIB_PATH = os.path.join(HERE, "librssri.so")
 RSSRI_PTR_DEVICE, RSSRI_PTR_HOST = 0, 1
 RSSRI_EST_CV, RSSRI_EST_SRI, RSSRI_EST_LITERAL = 0, 1, 2
 RSSRI_PREC_FP64, RSSRI_PREC_BF16, RSSRI_PREC_TF32, RSSRI_PREC_DF64 = 0, 1, 2, 3
-RSSRI_DD_FP64, RSSRI_DD_DF64 = 0, 1
+RSSRI_DD_FP64, RSSRI_DD_DF64, RSSRI_DD_OZ = 0, 1, 2
 BUF = dict(W=0, COLMAX=1, ERI_L=2, K_L=3, THETA=4, R=5, R_L=6, G=7, GB=8, SIGMA_DD=9,
            SIGMA_RAW=10, CV_PARAMS=11, CV_C=12)
 RSSRI_CV_NPARAM = 134657
-PROF_CLASSES = ["chain_gemm", "dd_spmm", "dd_gemm", "factor_gemm", "setup_gemm", "green", "other"]
+PROF_CLASSES = ["chain_gemm", "dd_spmm", "dd_gemm", "factor_gemm", "setup_gemm", "green", "other",
+                "slice"]
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_SPD", -3: "NONSYMMETRIC_ERI", -4: "OOM",
           -5: "CUDA", -6: "TIMEOUT", -7: "NOT_READY", -8: "NONFINITE"}
 
@@ -51,7 +52,8 @@ class rssri_stats(C.Structure):
                 ("e_stderr", C.c_double), ("t_setup_ms", C.c_double),
                 ("t_green_dd_ms", C.c_double), ("t_sample_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("prof_launches", C.c_int64 * 8),
-                ("prof_ms", C.c_double * 8), ("prof_gflop", C.c_double * 8)]
+                ("prof_ms", C.c_double * 8), ("prof_gflop", C.c_double * 8),
+                ("prof_tensor_gflop", C.c_double * 8)]
 
     def as_dict(self):
         d = {}
@@ -65,7 +67,7 @@ class rssri_stats(C.Structure):
 
 _LIB = None
 
-# name -> (restype, argtypes); every function declared in include/rssri.h
+# name -> (restype, argtypes); every function declared in include/*.h
 SIGNATURES = {
     "rssri_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "rssri_destroy": (None, [C.c_void_p]),
@@ -95,7 +97,11 @@ SIGNATURES = {
     "rssri_cv_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rssri_cv_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+    # include/rssri_peak.h
+    "rssri_peak_measure": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
 }
+RSSRI_PEAK_DFMA, RSSRI_PEAK_DMMA, RSSRI_PEAK_FFMA = 0, 1, 2
 RSSRI_STATIC_MAX_TAU = 4096
 
 
@@ -268,6 +274,13 @@ class Handle:
         check(lib().rssri_export(self._h, which, out.ctypes.data, nb.value, RSSRI_PTR_HOST),
               "rssri_export")
         return out
+
+
+def peak_measure(which: int, device: int = 0):
+    """rssri_peak_measure: (TFLOP/s, ms per launch) of an arithmetic pipe."""
+    tf, ms = C.c_double(), C.c_double()
+    check(lib().rssri_peak_measure(which, device, C.byref(tf), C.byref(ms)), "rssri_peak_measure")
+    return tf.value, ms.value
 
 
 def sigma_batch(handles, opts: rssri_options, sigmas, e_pairs=None):

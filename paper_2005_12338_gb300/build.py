@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librssri.so")
-SOURCES = ["api.cu", "gemm_f64.cu", "kernels.cu", "static_energy.cu", "tc_gemm.cu", "chain_tc.cu", "dd_df64.cu", "dd_spmm_df64.cu", "cv_mlp.cu"]
+SOURCES = ["api.cu", "gemm_f64.cu", "kernels.cu", "static_energy.cu", "tc_gemm.cu", "chain_tc.cu",
+           "dd_df64.cu", "dd_spmm_df64.cu", "cv_mlp.cu", "peak.cu", "oz_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +32,7 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "rssri.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     files.append(os.path.abspath(__file__))
     return files
 

@@ -10,6 +10,7 @@
 #include "cv_mlp.cuh"
 #include "dd_df64.cuh"
 #include "kernels.cuh"
+#include "oz_gemm.cuh"
 #include "tc_gemm.cuh"
 
 using namespace rssri;
@@ -106,12 +107,31 @@ struct rssri_handle {
   long long chain_graph_launches = 0;
   long long last_ns = 0;
   bool have_sigma = false;
+  // The deterministic block (S6, S7) of the last build: G, Gb and Sigma_DD for
+  // every tau.  rssri_setup builds it for the orbitals' G with the setup's
+  // dd_arith and rssri_sigma reuses it; rssri_sigma_from_g rebuilds it for the
+  // caller's G, after which the next rssri_sigma rebuilds the orbitals' block.
+  bool block_ok = false, block_from_g = false;
+  int setup_arith = RSSRI_DD_FP64;
+  bool gg_valid = false;  // GGhl holds the pair split of the current G, Gb
+  bool pending_block = false;  // the enqueued sigma call rebuilt the block
+  DevBuf sdd0;            // zeros: the block of the plain stochastic-RI estimator
+  // the sliced (RSSRI_DD_OZ) block: pair index map, the exchange contraction's
+  // left operand and the digits of K_P (setup); per-tau digit buffers
+  struct OzBuf {
+    DevBuf d, e;
+    OzDigits v;
+  };
+  bool oz_ready = false;
+  OzExch oz_geo;
+  DevBuf oz_pidx, oz_tmp;
+  OzBuf ozX, ozKP, ozKPt, ozGb, ozBig0, ozBig1, ozAtP, ozGam;
   rssri_stats stats{};
 
   // per-class launch counts and (when profiling) event timings
   struct Rec {
     int cls;
-    double gflop;
+    double gflop, tgflop;
     long long launches;
     cudaEvent_t a, b;
   };
@@ -120,7 +140,8 @@ struct rssri_handle {
   size_t ev_used = 0;
   std::vector<Rec> recs;
   long long setup_launches[RSSRI_PROF_NCLASS] = {};
-  double setup_ms[RSSRI_PROF_NCLASS] = {}, setup_gflop[RSSRI_PROF_NCLASS] = {};
+  double setup_ms[RSSRI_PROF_NCLASS] = {}, setup_gflop[RSSRI_PROF_NCLASS] = {},
+         setup_tgflop[RSSRI_PROF_NCLASS] = {};
 };
 
 namespace {
@@ -140,10 +161,11 @@ cudaEvent_t take_event(rssri_handle *h) {
 struct Span {
   rssri_handle *h;
   int cls;
-  double gflop;
+  double gflop, tgflop;
   long long l0;
   cudaEvent_t a = nullptr;
-  Span(rssri_handle *h_, int c, double gf) : h(h_), cls(c), gflop(gf), l0(launch_counter()) {
+  Span(rssri_handle *h_, int c, double gf, double tgf = 0.0)
+      : h(h_), cls(c), gflop(gf), tgflop(tgf), l0(launch_counter()) {
     if (h->prof_on) {
       a = take_event(h);
       if (a && cudaEventRecord(a, h->stream) != cudaSuccess) a = nullptr;
@@ -155,21 +177,24 @@ struct Span {
       b = take_event(h);
       if (b && cudaEventRecord(b, h->stream) != cudaSuccess) b = nullptr;
     }
-    h->recs.push_back({cls, gflop, launch_counter() - l0, a, b});
+    h->recs.push_back({cls, gflop, tgflop, launch_counter() - l0, a, b});
   }
 };
 #define SPAN(cls, gf) Span span_(h, (cls), (gf))
+#define SPAN_T(cls, gf, tgf) Span span_(h, (cls), (gf), (tgf))
 
 // Sum the recorded spans (the stream must have completed them) and reset.
-void collect(rssri_handle *h, long long *launches, double *ms, double *gflop) {
+void collect(rssri_handle *h, long long *launches, double *ms, double *gflop, double *tgflop) {
   for (int c = 0; c < RSSRI_PROF_NCLASS; ++c) {
     launches[c] = 0;
     ms[c] = 0;
     gflop[c] = 0;
+    tgflop[c] = 0;
   }
   for (const auto &r : h->recs) {
     launches[r.cls] += r.launches;
     gflop[r.cls] += r.gflop;
+    tgflop[r.cls] += r.tgflop;
     float t = 0;
     if (r.a && r.b && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.cls] += t;
   }
@@ -198,6 +223,9 @@ int validate_options(const rssri_options *o, bool for_sigma) {
   if (!o) return RSSRI_ERR_INVALID_ARG;
   if (!(o->eps_prime >= 0.0 && o->eps_prime <= 1.0) || !(o->eps >= 0.0 && o->eps <= 1.0))
     return RSSRI_ERR_INVALID_ARG;
+  if (o->dd_arith != RSSRI_DD_FP64 && o->dd_arith != RSSRI_DD_DF64 && o->dd_arith != RSSRI_DD_OZ)
+    return RSSRI_ERR_INVALID_ARG;
+  if (o->dd_arith == RSSRI_DD_OZ && !oz_available()) return RSSRI_ERR_INVALID_ARG;
   if (for_sigma) {
     if (o->n_s < 2 || o->n_s > (1LL << 30) || o->xi_offset < 0 ||
         o->xi_offset + o->n_s >= (1LL << 40))
@@ -211,7 +239,6 @@ int validate_options(const rssri_options *o, bool for_sigma) {
         o->precision != RSSRI_PREC_TF32 && o->precision != RSSRI_PREC_DF64)
       return RSSRI_ERR_INVALID_ARG;
     if (o->pair_batch < 0) return RSSRI_ERR_INVALID_ARG;
-    if (o->dd_arith != RSSRI_DD_FP64 && o->dd_arith != RSSRI_DD_DF64) return RSSRI_ERR_INVALID_ARG;
     if (o->cv != 0 && o->cv != 1) return RSSRI_ERR_INVALID_ARG;
   }
   return RSSRI_OK;
@@ -331,6 +358,9 @@ int metric_inv_sqrt(rssri_handle *h, int *rc, bool df64) {
 }
 
 
+// S6 and S7 for every tau (defined below).
+int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double *gb_in);
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -396,7 +426,7 @@ void rssri_destroy(rssri_handle *h) {
                     &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
                     &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->facHl, &h->xgHl, &h->cHl, &h->bHl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
-                    &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss};
+                    &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss, &h->sdd0};
   for (DevBuf *b : bufs) release(*b);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -419,6 +449,9 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   h->ready = false;
   h->have_sigma = false;
   h->d_df64_ready = false;
+  h->block_ok = false;
+  h->gg_valid = false;
+  h->oz_ready = false;
   const int n = p->n, na = p->n_aux, nt = p->n_tau;
   const long long nn = (long long)n * n;
   cudaError_t e;
@@ -479,7 +512,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
 
   // S1
   int ns_rc = RSSRI_OK;
-  rc = metric_inv_sqrt(h, &ns_rc, o->dd_arith == RSSRI_DD_DF64);
+  rc = metric_inv_sqrt(h, &ns_rc, o->dd_arith != RSSRI_DD_FP64);
   if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
   if (ns_rc) return ns_rc;
 
@@ -540,8 +573,9 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_int(h->spairs.as<int>(), h->lidx.as<int>(), P, h->pij.as<int>(), s)); }
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_rows(h->KLs.as<double>(), h->lidx.as<int>(), P, na, h->KP.as<double>(), s)); }
     // D[a][b] = sum_Q K_P[a][Q] K_P[b][Q] = v^L for the pair of pairs (Eq. 8 on [K]^L),
-    // in the arithmetic the deterministic block is asked to use
-    if (o->dd_arith == RSSRI_DD_DF64) {
+    // in the arithmetic the deterministic block is asked to use (double-float
+    // for the sliced block too)
+    if (o->dd_arith != RSSRI_DD_FP64) {
       RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
       RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
       { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s)); }
@@ -567,12 +601,17 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_csr(h->pij.as<int>(), P, n, h->rowptr.as<int>(), h->prow.as<int>(),
                  h->pcol.as<int>(), s)); }
+  // S6, S7: G(tau), G(beta - tau) and the deterministic block for every tau,
+  // cached for every sampling call on this setup (they do not depend on the draws)
+  h->setup_arith = o->dd_arith;
+  rc = build_block(h, o->dd_arith, nullptr, nullptr);
+  if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
   RS_CK(cudaEventRecord(h->ev[1], s));
   RS_CK(cudaEventSynchronize(h->ev[1]));
   float ms = 0;
   cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
   h->t_setup_ms = ms;
-  collect(h, h->setup_launches, h->setup_ms, h->setup_gflop);
+  collect(h, h->setup_launches, h->setup_ms, h->setup_gflop, h->setup_tgflop);
   h->ready = true;
   return RSSRI_OK;
 #undef RS_CK
@@ -664,7 +703,7 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
 
 // A double-float product counted under kernel class `cls`.
 cudaError_t df_gemm_c(rssri_handle *h, int cls, const DfGemm &g) {
-  SPAN(cls, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
+  SPAN(cls, df_gemm_flops(g) * 1e-9);
   const size_t need = df_gemm_work(g) * sizeof(double);
   if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
   return df_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
@@ -672,7 +711,7 @@ cudaError_t df_gemm_c(rssri_handle *h, int cls, const DfGemm &g) {
 
 // A double-float product counted under the deterministic-block GEMM class.
 cudaError_t df_gemm_p(rssri_handle *h, const DfGemm &g) {
-  SPAN(RSSRI_PROF_DD_GEMM, 2.0 * g.M * (double)g.N * g.K * g.batch * 1e-9);
+  SPAN(RSSRI_PROF_DD_GEMM, df_gemm_flops(g) * 1e-9);
   const size_t need = df_gemm_work(g) * sizeof(double);
   if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
   return df_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
@@ -749,6 +788,167 @@ cudaError_t sigma_dd_tau_df64(rssri_handle *h, const float2 *Ghl, const float2 *
   return cudaSuccess;
 }
 
+// ------------------------------------------- the sliced (RSSRI_DD_OZ) block --
+// A digit buffer for batch x rows x K values (rows padded to ld = K rounded up to 8).
+cudaError_t oz_make(rssri_handle::OzBuf &b, int batch, int rows, long long K) {
+  OzDigits v;
+  v.batch = batch;
+  v.rows = rows;
+  v.K = K;
+  v.ld = (K + 7) / 8 * 8;
+  RS_TRY(ensure(b.d, oz_digit_elems(v) * sizeof(__nv_bfloat16)));
+  RS_TRY(ensure(b.e, (size_t)batch * rows * sizeof(int)));
+  v.d = b.d.as<__nv_bfloat16>();
+  v.ef = b.e.as<int>();
+  b.v = v;
+  return cudaSuccess;
+}
+
+cudaError_t oz_slice_p(rssri_handle *h, const OzView &v, const OzDigits &o) {
+  SPAN(RSSRI_PROF_SLICE, 0.0);
+  return oz_slice(v, o, h->stream);
+}
+
+// An fp64-accurate product on the tensor cores, counted under `cls`.
+cudaError_t oz_gemm_p(rssri_handle *h, int cls, const OzGemm &g) {
+  const double alg = 2.0 * g.M * (double)g.N * g.A.K * g.batch;
+  SPAN_T(cls, alg * 1e-9, oz_gemm_flops(g) * 1e-9);
+  const size_t need = oz_gemm_work(g) * sizeof(double);
+  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
+  return oz_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
+}
+
+// Setup of the sliced block: the pair index map, the band half-width, the
+// exchange contraction's left operand (from D) and the digits of K_P and K_P^T.
+int oz_setup(rssri_handle *h) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, P = h->P;
+  cudaError_t e;
+#define RS_CK(x)                     \
+  do {                               \
+    e = (x);                         \
+    if (e != cudaSuccess) return map_err(e); \
+  } while (0)
+  RS_CK(ensure(h->oz_pidx, (size_t)n * n * sizeof(int)));
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(oz_pair_index(h->pij.as<int>(), P, n, h->oz_pidx.as<int>(), s)); }
+  // band half-width of the kept pairs
+  std::vector<int> hp(P);
+  RS_CK(fetch(hp.data(), h->pij.p, s, P));
+  int bk = 0;
+  for (int a = 0; a < P; ++a) bk = std::max(bk, std::abs(hp[a] / n - hp[a] % n));
+  h->oz_geo = oz_exch_geometry(n, na, bk);
+  const OzExch &x = h->oz_geo;
+  const int tiles = x.mtiles * x.jtiles;
+  if (tiles > 65535) return RSSRI_ERR_INVALID_ARG;
+  RS_CK(ensure(h->oz_tmp, (size_t)tiles * 128 * x.kx * sizeof(double)));
+  { SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_CK(oz_exch_gather(x, h->D.as<double>(), P, h->oz_pidx.as<int>(), h->oz_tmp.as<double>(), s)); }
+  RS_CK(oz_make(h->ozX, tiles, 128, x.kx));
+  {
+    OzView v;
+    v.x = h->oz_tmp.as<double>();
+    v.bs = 128 * x.kx; v.rs = x.kx; v.cs2 = 1; v.k2pad = v.k2n = x.kx;
+    RS_CK(oz_slice_p(h, v, h->ozX.v));
+  }
+  // K_P [P][na]: digits with rows a (for L) and rows Q (for Gamma)
+  RS_CK(oz_make(h->ozKP, 1, P, na));
+  RS_CK(oz_make(h->ozKPt, 1, na, P));
+  {
+    OzView v;
+    v.x = h->KP.as<double>();
+    v.rs = na; v.cs2 = 1; v.k2pad = v.k2n = na;
+    RS_CK(oz_slice_p(h, v, h->ozKP.v));
+    OzView t;
+    t.x = h->KP.as<double>();
+    t.rs = 1; t.cs2 = na; t.k2pad = t.k2n = P;
+    RS_CK(oz_slice_p(h, t, h->ozKPt.v));
+  }
+  RS_CK(cudaStreamSynchronize(s));
+  release(h->oz_tmp);
+  h->oz_ready = true;
+  return RSSRI_OK;
+#undef RS_CK
+}
+
+// S7 for one tau with every dense product and the exchange contraction on
+// the tensor cores (sliced fp64-accurate products), the segmented K^Q G in
+// double-float.  With T stored negated by the contraction, U = 2 L - T and
+// Sigma_DD = sum_Q PG^Q U^Q, PG^Q = K^Q G (see sigma_dd_tau).
+cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb, double *out) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, P = h->P;
+  const long long nn = (long long)n * n, nna = nn * na;
+  if (P == 0) return cudaMemsetAsync(out, 0, nn * sizeof(double), s);
+  const OzExch &x = h->oz_geo;
+  int *err = h->flags.as<int>() + 5;
+  float2 *PGhl = h->PGhl.as<float2>();
+  double *At = h->At.as<double>(), *T = h->T.as<double>();
+  // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]   (double-float)
+  { SPAN(RSSRI_PROF_DD_GEMM, 2.0 * n * (double)na * P * 1e-9);
+    RS_TRY(df_gemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), Ghl, n,
+                             h->KPhl.as<float2>(), na, PGhl, na, (long long)n * na, s)); }
+  // At[k][(l,Q)] = sum_m Gb[k][m] PG[m][(l,Q)]
+  OzDigits &dGb = h->ozGb.v;
+  { OzView v; v.x = Gb; v.rs = n; v.cs2 = 1; v.k2pad = v.k2n = n;
+    RS_TRY(oz_slice_p(h, v, dGb)); }
+  OzDigits dPGb = h->ozBig0.v;
+  dPGb.rows = (int)(n * (long long)na); dPGb.K = n; dPGb.ld = (n + 7) / 8 * 8;
+  { OzView v; v.x2 = PGhl; v.rs = 1; v.cs2 = (long long)n * na; v.k2pad = v.k2n = n;
+    RS_TRY(oz_slice_p(h, v, dPGb)); }
+  {
+    OzGemm g;
+    g.A = dGb; g.B = dPGb; g.M = n; g.N = (int)(n * (long long)na);
+    g.C = At; g.ldc = (long long)n * na; g.err = err;
+    RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  // the exchange contraction: T[j][m][Q] = -sum D[(m,k),(l,j)] At[k][l][Q]
+  OzDigits dAt = h->ozBig1.v;
+  dAt.rows = na; dAt.K = (long long)n * x.ldl; dAt.ld = dAt.K;
+  { OzView v; v.x = At; v.rs = 1; v.cs1 = (long long)n * na; v.cs2 = na; v.k2pad = x.ldl;
+    v.k2n = n;
+    RS_TRY(oz_slice_p(h, v, dAt)); }
+  { SPAN_T(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9, oz_exch_flops(x) * 1e-9);
+    RS_TRY(oz_exch(x, h->ozX.v, dAt, T, -1.0, err, s)); }
+  // Gamma = K_P^T At_P (At_P: the rows of At at the kept pairs)
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
+  { OzView v; v.x = h->AP.as<double>(); v.rs = 1; v.cs2 = na; v.k2pad = v.k2n = P;
+    RS_TRY(oz_slice_p(h, v, h->ozAtP.v)); }
+  {
+    OzGemm g;
+    g.A = h->ozKPt.v; g.B = h->ozAtP.v; g.M = na; g.N = na;
+    g.C = h->Gam.as<double>(); g.ldc = na; g.err = err;
+    RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
+  { OzView v; v.x = h->Gam.as<double>(); v.rs = na; v.cs2 = 1; v.k2pad = v.k2n = na;
+    RS_TRY(oz_slice_p(h, v, h->ozGam.v)); }
+  {
+    OzGemm g;
+    g.A = h->ozKP.v; g.B = h->ozGam.v; g.M = P; g.N = na;
+    g.C = h->L.as<double>(); g.ldc = na; g.err = err;
+    RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  // U = 2 L - T at the kept pairs (T already negated)
+  { SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_TRY(oz_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s)); }
+  // Sigma_DD[i][j] = sum_{(m,Q)} PG[i][m][Q] U[j][m][Q]
+  OzDigits dU = h->ozBig0.v;
+  dU.rows = n; dU.K = nna; dU.ld = (nna + 7) / 8 * 8;
+  { OzView v; v.x = T; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dU.K;
+    RS_TRY(oz_slice_p(h, v, dU)); }
+  OzDigits dPGa = h->ozBig1.v;
+  dPGa.rows = n; dPGa.K = nna; dPGa.ld = (nna + 7) / 8 * 8;
+  { OzView v; v.x2 = PGhl; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dPGa.K;
+    RS_TRY(oz_slice_p(h, v, dPGa)); }
+  {
+    OzGemm g;
+    g.A = dPGa; g.B = dU; g.M = n; g.N = n;
+    g.C = out; g.ldc = n; g.err = err;
+    RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
+  return cudaSuccess;
+}
+
 size_t dd_work_need(rssri_handle *h) {
   const int n = h->n, na = h->n_aux, P = std::max(h->P, 1);
   size_t w = 0;
@@ -758,6 +958,129 @@ size_t dd_work_need(rssri_handle *h) {
   g.M = n; g.N = n; g.K = n * na; w = std::max(w, dgemm_work_elems(g));
   g.M = n; g.N = n * na; g.K = n; w = std::max(w, dgemm_work_elems(g));
   return w;
+}
+
+// The pair copies of D and K_P used by the double-float block (made once per setup).
+cudaError_t ensure_d_df64(rssri_handle *h) {
+  if (h->d_df64_ready || h->P == 0) return cudaSuccess;
+  const int P = h->P, na = h->n_aux;
+  RS_TRY(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
+  RS_TRY(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
+  SPAN(RSSRI_PROF_OTHER, 0.0);
+  RS_TRY(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), h->stream));
+  RS_TRY(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), h->stream));
+  h->d_df64_ready = true;
+  return cudaSuccess;
+}
+
+// The pair split of G and Gb for every tau (double-float block and chain).
+cudaError_t ensure_gg(rssri_handle *h) {
+  if (h->gg_valid) return cudaSuccess;
+  const long long nn = (long long)h->n * h->n, nt = h->n_tau;
+  RS_TRY(ensure(h->GGhl, (size_t)2 * nt * nn * sizeof(float2)));
+  SPAN(RSSRI_PROF_OTHER, 0.0);
+  RS_TRY(to_df64(h->G.as<double>(), nt * nn, h->GGhl.as<float2>(), h->stream));
+  RS_TRY(to_df64(h->Gb.as<double>(), nt * nn, h->GGhl.as<float2>() + nt * nn, h->stream));
+  h->gg_valid = true;
+  return cudaSuccess;
+}
+
+// S6 and S7 for every tau point: G(tau) and G(beta - tau) from the orbitals
+// (Eq. 17) or copied from the caller (g_in, gb_in: [n_tau][n][n] of the
+// problem's pointer kind), then Sigma_DD(tau) (Eq. 20 on v^L = sum_Q
+// [K^Q]^L [K^Q]^L, the deterministic terms of Eq. 25) in the arithmetic
+// dd_arith.  The results stay in the handle (G, Gb, sdd) for the sampling calls.
+int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double *gb_in) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, na = h->n_aux, nt = h->n_tau, P = h->P;
+  const long long nn = (long long)n * n;
+  h->block_ok = false;
+  h->gg_valid = false;
+  cudaError_t e;
+#define RS_CK(x)                     \
+  do {                               \
+    e = (x);                         \
+    if (e != cudaSuccess) return map_err(e); \
+  } while (0)
+  RS_CK(ensure(h->G, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->Gb, (size_t)nt * nn * sizeof(double)));
+  RS_CK(ensure(h->sdd, (size_t)nt * nn * sizeof(double)));
+  const bool dd_df64 = P > 0 && dd_arith == RSSRI_DD_DF64;
+  const bool dd_oz = P > 0 && dd_arith == RSSRI_DD_OZ;
+  if (P > 0) {
+    if (dd_oz) {
+      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
+      RS_CK(ensure_d_df64(h));
+      if (!h->oz_ready) {
+        const int rc = oz_setup(h);
+        if (rc) return rc;
+      }
+      // the largest per-tau digit operand: n*na rows of ld8(n), n rows of ld8(n*na), or
+      // na rows of n*ldl
+      const long long ld_n = (n + 7) / 8 * 8, ld_nna = (nn * na + 7) / 8 * 8;
+      const long long big = std::max({(long long)n * na * ld_n, (long long)n * ld_nna,
+                                      (long long)na * n * h->oz_geo.ldl});
+      RS_CK(oz_make(h->ozGb, 1, n, n));
+      RS_CK(oz_make(h->ozBig0, 1, 1, big));
+      RS_CK(oz_make(h->ozBig1, 1, 1, big));
+      RS_CK(ensure(h->ozBig0.e, (size_t)std::max<long long>(nn * na, n) * sizeof(int)));
+      RS_CK(ensure(h->ozBig1.e, (size_t)std::max<long long>(na, n) * sizeof(int)));
+      h->ozBig0.v.ef = h->ozBig0.e.as<int>();
+      h->ozBig1.v.ef = h->ozBig1.e.as<int>();
+      RS_CK(oz_make(h->ozAtP, 1, na, P));
+      RS_CK(oz_make(h->ozGam, 1, na, na));
+      RS_CK(cudaMemsetAsync(h->flags.as<int>() + 5, 0, sizeof(int), s));
+    } else if (!dd_df64) {  // the double-float block keeps these as pairs
+      RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
+    }
+    RS_CK(ensure(h->T, (size_t)nn * na * sizeof(double)));
+    RS_CK(ensure(h->L, (size_t)P * na * sizeof(double)));
+    RS_CK(ensure(h->Gam, (size_t)na * na * sizeof(double)));
+    RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));
+    if (dd_df64) {
+      RS_CK(ensure(h->Ahl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->APhl, (size_t)P * na * sizeof(float2)));
+      RS_CK(ensure(h->Gamhl, (size_t)na * na * sizeof(float2)));
+      RS_CK(ensure_d_df64(h));
+    }
+  }
+  double *G = h->G.as<double>(), *Gb = h->Gb.as<double>();
+  // S6
+  if (g_in) {
+    const cudaMemcpyKind k = h->ptr_kind == RSSRI_PTR_HOST ? cudaMemcpyHostToDevice
+                                                           : cudaMemcpyDeviceToDevice;
+    RS_CK(cudaMemcpyAsync(G, g_in, nt * nn * sizeof(double), k, s));
+    RS_CK(cudaMemcpyAsync(Gb, gb_in, nt * nn * sizeof(double), k, s));
+  } else {
+    RS_CK(build_green(h));
+  }
+  // S7 per tau
+  if (dd_df64 || dd_oz) RS_CK(ensure_gg(h));
+  for (int t = 0; t < nt; ++t) {
+    double *out = h->sdd.as<double>() + t * nn;
+    if (dd_oz)
+      RS_CK(sigma_dd_tau_oz(h, h->GGhl.as<float2>() + t * nn, Gb + t * nn, out));
+    else if (dd_df64)
+      RS_CK(sigma_dd_tau_df64(h, h->GGhl.as<float2>() + t * nn,
+                              h->GGhl.as<float2>() + (nt + t) * nn, out));
+    else
+      RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out));
+  }
+  if (dd_oz) {
+    // a bounded wait of the tensor-core kernels that gave up
+    int fl = 0;
+    RS_CK(fetch(&fl, h->flags.as<int>() + 5, s));
+    if (fl) return RSSRI_ERR_TIMEOUT;
+  }
+  h->block_ok = true;
+  h->block_from_g = g_in != nullptr;
+  return RSSRI_OK;
+#undef RS_CK
 }
 
 // S8 on the tensor cores (bf16 or tf32 operands, fp32 accumulation), all
@@ -778,7 +1101,8 @@ struct ChainBufs {
 };
 
 cudaError_t issue_chain_tc(rssri_handle *h, cudaStream_t s, int ns, const double *G,
-                           const double *Gb, double *sig, int *err, const ChainBufs &b) {
+                           const double *Gb, const double *sdd, double *sig, int *err,
+                           const ChainBufs &b) {
   const int n = h->n, nt = h->n_tau;
   const int ldp = (n + 7) / 8 * 8;
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
@@ -842,14 +1166,14 @@ cudaError_t issue_chain_tc(rssri_handle *h, cudaStream_t s, int ns, const double
       g.c32 = b.part; g.err = err;
       RS_TRY(tc_gemm(g, s));
     }
-    RS_TRY(reduce_tc(b.part, b.groups, n, h->sdd.as<double>() + t * nn, (double)ns,
+    RS_TRY(reduce_tc(b.part, b.groups, n, sdd + t * nn, (double)ns,
                        sig + t * nn, s));
   }
   return cudaSuccess;
 }
 
 cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const double *Gb,
-                     double *sig, int *err) {
+                     const double *sdd, double *sig, int *err) {
   cudaStream_t s = h->stream;
   const int n = h->n, nt = h->n_tau;
   const int ldp = (n + 7) / 8 * 8;
@@ -883,7 +1207,7 @@ cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const d
   // the graph is keyed on every pointer and value baked into its launches
   std::vector<uintptr_t> key = {(uintptr_t)kind, (uintptr_t)ns, (uintptr_t)n, (uintptr_t)nt, (uintptr_t)h->n_occ,
                                 (uintptr_t)G, (uintptr_t)Gb, (uintptr_t)sig, (uintptr_t)err,
-                                (uintptr_t)h->fac.p, (uintptr_t)h->e_st.p, (uintptr_t)h->sdd.p};
+                                (uintptr_t)h->fac.p, (uintptr_t)h->e_st.p, (uintptr_t)sdd};
   for (DevBuf *d : {&h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32, &h->hdcl16,
                     &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold})
     key.push_back((uintptr_t)d->p);
@@ -894,7 +1218,7 @@ cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const d
     if (!h->cap_stream) RS_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     RS_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     const long long l0 = launch_counter();
-    const cudaError_t ei = issue_chain_tc(h, h->cap_stream, ns, G, Gb, sig, err, b);
+    const cudaError_t ei = issue_chain_tc(h, h->cap_stream, ns, G, Gb, sdd, sig, err, b);
     const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
     const long long captured = launch_counter() - l0;
     launch_counter() = l0;  // captured, not yet run
@@ -911,7 +1235,8 @@ cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const d
     h->chain_key_w = h->h_tau_w;
     h->chain_graph_launches = captured;
   }
-  SPAN(RSSRI_PROF_CHAIN_GEMM, 18.0 * ns * (double)n * n * n * nt * 1e-9);
+  SPAN_T(RSSRI_PROF_CHAIN_GEMM, 18.0 * ns * (double)n * n * n * nt * 1e-9,
+         18.0 * ns * (double)n * n * n * nt * 1e-9);
   RS_TRY(cudaGraphLaunch(h->chain_graph, s));
   launch_counter() += h->chain_graph_launches;
   return cudaSuccess;
@@ -1012,7 +1337,7 @@ cudaError_t literal_cross(rssri_handle *h, const rssri_options *o, int t, int x0
   double *Tk = XG;
   {
     SPAN(RSSRI_PROF_DD_SPMM, 2.0 * S * (double)P * P * 1e-9);
-    if (o->dd_arith == RSSRI_DD_DF64) {
+    if (o->dd_arith != RSSRI_DD_FP64) {
       RS_TRY(to_df64(Mt, S * nn, h->litMhl.as<float2>(), s));
       RS_TRY(dd_exchange_spmm_df64(h->rowptr.as<int>(), h->pcol.as<int>(), h->Dhl.as<float2>(), P,
                                    h->litMhl.as<float2>(), n, S, Tk, s));
@@ -1104,9 +1429,6 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   h->prof_on = o->profile != 0;
   RS_CK(cudaEventRecord(h->ev[2], s));
   // ---- buffers
-  RS_CK(ensure(h->G, (size_t)nt * nn * sizeof(double)));
-  RS_CK(ensure(h->Gb, (size_t)nt * nn * sizeof(double)));
-  RS_CK(ensure(h->sdd, (size_t)nt * nn * sizeof(double)));
   RS_CK(ensure(h->sig_raw, (size_t)nt * nn * sizeof(double)));
   RS_CK(ensure(h->sig_out, (size_t)nt * nn * sizeof(double)));
   RS_CK(ensure(h->trdd, nt * sizeof(double)));
@@ -1136,61 +1458,30 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   if (literal && P > 0) {
     RS_CK(ensure(h->litMP, (size_t)P * nbat2 * sizeof(double)));
     RS_CK(ensure(h->litT, (size_t)na * nbat2 * sizeof(double)));
-    if (o->dd_arith == RSSRI_DD_DF64) RS_CK(ensure(h->litMhl, (size_t)nbat2 * nn * sizeof(float2)));
+    if (o->dd_arith != RSSRI_DD_FP64) {
+      RS_CK(ensure(h->litMhl, (size_t)nbat2 * nn * sizeof(float2)));
+      RS_CK(ensure_d_df64(h));
+    }
   }
-  if (P > 0) {
-    if (o->dd_arith != RSSRI_DD_DF64) {  // the double-float block keeps these as pairs
-      RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
-      RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
-      RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
-    }
-    RS_CK(ensure(h->T, (size_t)nn * na * sizeof(double)));
-    RS_CK(ensure(h->L, (size_t)P * na * sizeof(double)));
-    RS_CK(ensure(h->Gam, (size_t)na * na * sizeof(double)));
-    RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));
-    if (o->dd_arith == RSSRI_DD_DF64) {
-      RS_CK(ensure(h->Ahl, (size_t)nn * na * sizeof(float2)));
-      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
-      RS_CK(ensure(h->APhl, (size_t)P * na * sizeof(float2)));
-      RS_CK(ensure(h->Gamhl, (size_t)na * na * sizeof(float2)));
-      RS_CK(ensure(h->GGhl, (size_t)2 * nt * nn * sizeof(float2)));
-      if (!h->d_df64_ready) {
-        RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
-        RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
-        SPAN(RSSRI_PROF_OTHER, 0.0);
-        RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s));
-        RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s));
-        h->d_df64_ready = true;
-      }
-    }
+
+  // ---- S6, S7: the cached block of the setup, or a new one for the caller's G
+  h->pending_block = g_in || !h->block_ok || h->block_from_g;
+  if (g_in) {
+    rc = build_block(h, o->dd_arith, g_in, gb_in);
+    if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
+  } else if (!h->block_ok || h->block_from_g) {
+    rc = build_block(h, h->setup_arith, nullptr, nullptr);
+    if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
   }
   double *G = h->G.as<double>(), *Gb = h->Gb.as<double>();
-
-  // ---- S6: G(tau), G(beta - tau)
-  if (g_in) {
-    const cudaMemcpyKind k = h->ptr_kind == RSSRI_PTR_HOST ? cudaMemcpyHostToDevice
-                                                           : cudaMemcpyDeviceToDevice;
-    RS_CK(cudaMemcpyAsync(G, g_in, nt * nn * sizeof(double), k, s));
-    RS_CK(cudaMemcpyAsync(Gb, gb_in, nt * nn * sizeof(double), k, s));
-  } else {
-    RS_CK(build_green(h));
+  // the block the estimator adds to: Sigma_DD, or zero for plain stochastic RI
+  const double *sdd = h->sdd.as<double>();
+  if (sri) {
+    RS_CK(ensure(h->sdd0, (size_t)nt * nn * sizeof(double)));
+    RS_CK(cudaMemsetAsync(h->sdd0.p, 0, (size_t)nt * nn * sizeof(double), s));
+    sdd = h->sdd0.as<double>();
   }
-  // ---- S7: deterministic block per tau
-  const bool dd_df64 = !sri && P > 0 && o->dd_arith == RSSRI_DD_DF64;
-  if (dd_df64 || chain_df64) {
-    RS_CK(ensure(h->GGhl, (size_t)2 * nt * nn * sizeof(float2)));
-    SPAN(RSSRI_PROF_OTHER, 0.0);
-    RS_CK(to_df64(G, nt * nn, h->GGhl.as<float2>(), s));
-    RS_CK(to_df64(Gb, nt * nn, h->GGhl.as<float2>() + nt * nn, s));
-  }
-  for (int t = 0; t < nt; ++t) {
-    double *out = h->sdd.as<double>() + t * nn;
-    if (sri) RS_CK(cudaMemsetAsync(out, 0, nn * sizeof(double), s));
-    else if (dd_df64)
-      RS_CK(sigma_dd_tau_df64(h, h->GGhl.as<float2>() + t * nn,
-                              h->GGhl.as<float2>() + (nt + t) * nn, out));
-    else RS_CK(sigma_dd_tau(h, G + t * nn, Gb + t * nn, out));
-  }
+  if (chain_df64) RS_CK(ensure_gg(h));
   RS_CK(cudaEventRecord(h->ev[3], s));
 
   // ---- S4: theta, theta' and U^T = theta W (W symmetric)
@@ -1207,7 +1498,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   }
   // ---- S5: R[set][xi][ij] = sum_A U^T[xi][A] (ij|A); R^L from the kept pairs
   // (in double-float when the block is: the operands split into pairs first)
-  const bool fac_df64 = o->dd_arith == RSSRI_DD_DF64;
+  const bool fac_df64 = o->dd_arith != RSSRI_DD_FP64;
   if (fac_df64) {
     RS_CK(ensure(h->eri_hl, (size_t)nn * na * sizeof(float2)));
     RS_CK(ensure(h->ut_hl, (size_t)2 * ns * na * sizeof(float2)));
@@ -1282,7 +1573,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   int *tc_err = h->flags.as<int>() + 4;
   if (bf16) {
     RS_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
-    RS_CK(chain_tc(h, tc_kind, ns, G, Gb, h->sig_raw.as<double>(), tc_err));
+    RS_CK(chain_tc(h, tc_kind, ns, G, Gb, sdd, h->sig_raw.as<double>(), tc_err));
   }
   for (int t = 0; t < nt && !bf16; ++t) {
     const double *Gt = G + t * nn, *Gbt = Gb + t * nn;
@@ -1356,12 +1647,12 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
       if (use_cv) {
         SPAN(RSSRI_PROF_OTHER, 0.0);
         const double *ct = h->cv_c.as<double>() + t * nn;
-        RS_CK(cv_accumulate(BC, cnt, n, (double)ns, h->sdd.as<double>() + t * nn, ct, x0 == 0,
+        RS_CK(cv_accumulate(BC, cnt, n, (double)ns, sdd + t * nn, ct, x0 == 0,
                             sig, s));
         RS_CK(cv_pair_energy(BC, cnt, n, ct, Gbt, h->tarr.as<double>(), h->sarr.as<double>(),
                              h->h_tau_w[t], ne, h->e_st.as<double>() + x0, s));
       } else {
-        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, nkind, n, (double)ns, h->sdd.as<double>() + t * nn,
+        { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(sigma_accumulate(BC, cnt, nkind, n, (double)ns, sdd + t * nn,
                                x0 == 0, sig, s)); }
         { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(pair_energy(h->tarr.as<double>(), h->sarr.as<double>(), cnt, nkind, literal ? 2 : 1, h->h_tau_w[t], ne,
                           h->e_st.as<double>() + x0, s)); }
@@ -1372,11 +1663,11 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(symmetrize(h->sig_raw.as<double>(), n, nt, h->sig_out.as<double>(), s)); }
   if (use_cv) {
     SPAN(RSSRI_PROF_OTHER, 0.0);
-    RS_CK(trace_prod_w(h->sdd.as<double>(), Gb, h->cv_c.as<double>(), n, nt,
+    RS_CK(trace_prod_w(sdd, Gb, h->cv_c.as<double>(), n, nt,
                        h->trdd.as<double>(), s));
   } else {
     SPAN(RSSRI_PROF_OTHER, 0.0);
-    RS_CK(trace_prod(h->sdd.as<double>(), Gb, n, nt, h->trdd.as<double>(), s));
+    RS_CK(trace_prod(sdd, Gb, n, nt, h->trdd.as<double>(), s));
   }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(trace_prod(h->sig_out.as<double>(), Gb, n, nt, h->tr.as<double>(), s)); }
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(energy_finalize(h->tau_w, h->trdd.as<double>(), h->tr.as<double>(), nt, ne,
@@ -1428,16 +1719,17 @@ int finish_sigma(rssri_handle *h, double *e_corr, double *e_stderr, rssri_stats 
   S.e_corr = res[1];
   S.e_stderr = res[3];
   S.t_setup_ms = h->t_setup_ms;
-  S.t_green_dd_ms = t_dd;
+  S.t_green_dd_ms = h->pending_block ? t_dd : 0.0;
   S.t_sample_ms = t_samp;
   long long pl[RSSRI_PROF_NCLASS];
-  double pm[RSSRI_PROF_NCLASS], pg[RSSRI_PROF_NCLASS];
-  collect(h, pl, pm, pg);
+  double pm[RSSRI_PROF_NCLASS], pg[RSSRI_PROF_NCLASS], pt[RSSRI_PROF_NCLASS];
+  collect(h, pl, pm, pg, pt);
   S.kernel_launches = 0;
   for (int c = 0; c < RSSRI_PROF_NCLASS; ++c) {
     S.prof_launches[c] = pl[c] + h->setup_launches[c];
     S.prof_ms[c] = pm[c] + h->setup_ms[c];
     S.prof_gflop[c] = pg[c] + h->setup_gflop[c];
+    S.prof_tensor_gflop[c] = pt[c] + h->setup_tgflop[c];
     S.kernel_launches += S.prof_launches[c];
   }
   if (e_corr) *e_corr = res[1];
@@ -1655,7 +1947,7 @@ int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
     case RSSRI_BUF_R_L: *bytes = h->have_sigma ? 2 * ns * nn * d : 0; break;
     case RSSRI_BUF_G:
     case RSSRI_BUF_GB:
-    case RSSRI_BUF_SIGMA_DD:
+    case RSSRI_BUF_SIGMA_DD: *bytes = h->block_ok ? nt * nn * d : 0; break;
     case RSSRI_BUF_SIGMA_RAW: *bytes = h->have_sigma ? nt * nn * d : 0; break;
     case RSSRI_BUF_CV_PARAMS: *bytes = h->cv_ready ? CV_NPARAM * sizeof(float) : 0; break;
     case RSSRI_BUF_CV_C: *bytes = h->cv_c_ready ? nt * nn * d : 0; break;

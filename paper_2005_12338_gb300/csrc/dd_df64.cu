@@ -321,6 +321,18 @@ cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream
                            : df_gemm_geo<G64>(g, work, work_elems, s);
 }
 
+double df_gemm_flops(const DfGemm &g) {
+  if (!g.sym) return 2.0 * g.M * (double)g.N * g.K * g.batch;
+  // symmetric: only the tiles on and above the diagonal are computed
+  const int bm = use_g40(g.M, g.N) ? G40::BM : G64::BM;
+  const int t = ceil_div(g.M, bm);
+  double f = 0.0;
+  for (int i = 0; i < t; ++i)
+    for (int j = i; j < t; ++j)
+      f += 2.0 * std::min(bm, g.M - i * bm) * (double)std::min(bm, g.N - j * bm) * g.K;
+  return f * g.batch;
+}
+
 size_t df_gemm_work(const DfGemm &g) {
   int ks, kc;
   if (use_g40(g.M, g.N)) df_plan<G40>(g, &ks, &kc);

@@ -30,6 +30,9 @@ struct DfGemm {
 };
 cudaError_t df_gemm(const DfGemm &g, double *work, size_t work_elems, cudaStream_t s);
 size_t df_gemm_work(const DfGemm &g);
+// Flops of the tiles df_gemm computes (2 M N K batch; with sym, only the
+// tiles on and above the diagonal).
+double df_gemm_flops(const DfGemm &g);
 // C[b][m][q] = sum_{a in [seg[b], seg[b+1])} A[col[a]*lda + m] * B[a*ldb + q], pairs out.
 cudaError_t df_gemm_segmented(int batch, int M, int N, const int *seg, const int *col,
                               const float2 *A, long long lda, const float2 *B, long long ldb,

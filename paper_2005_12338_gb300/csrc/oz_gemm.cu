@@ -1,0 +1,779 @@
+// fp64-accurate products on the bf16 tensor cores (tcgen05, TMA, TMEM) by
+// error-free digit slicing; see oz_gemm.cuh for the number scheme.
+//
+// Kernel layout (one 128 x 128 output tile per CTA, 10 warps):
+//   warp 0 lane 0  TMA producer: per K step of 16, the five digit tiles of A
+//                  and of B (128 rows x 32 bytes each, 32-byte swizzle) into a
+//                  ring of shared-memory stages;
+//   warp 1 lane 0  MMA issuer: per K step, the 15 digit products p + q <= 4
+//                  (tcgen05.mma kind::f16, M = N = 128, K = 16) into four fp32
+//                  accumulators in tensor memory, one per level p + q = 0, 1,
+//                  2 and one for p + q >= 3 (4 x 128 of the 512 columns);
+//   warps 2-9      drain: after every 256 terms of K (16 steps) they read the
+//                  four accumulators (tcgen05.ld) and add them exactly into
+//                  double-float running totals held in registers (each thread:
+//                  one row, 64 columns), then release the accumulators; at the
+//                  end they assemble fp64 from the running totals with integer
+//                  exponent arithmetic and one fp64 add per output.
+// Levels 0-2 are exact over 256 terms (< 2^24 grid units), so a chunk's sum
+// a0 + a1 + a2 is exact in two TwoSums; level >= 3 (< 2^-24 of the result)
+// and the running sum round at ~2^-48 relative.
+//
+// Every mbarrier wait is bounded; on expiry the kernel records an error code
+// in a device flag and stops waiting; tensor memory is freed on every path.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "oz_gemm.cuh"
+
+namespace rssri {
+namespace {
+
+constexpr int BM = 128, BN = 128, KS = 16;   // tile rows, columns; K per step (32 bytes of bf16)
+constexpr int TILE = BM * KS * 2;            // bytes of one digit tile
+constexpr int STAGE = OZ_S * 2 * TILE;       // A and B digits of one K step
+constexpr int STAGES = 5;
+constexpr int CHUNK = 16;                    // K steps between drains (256 terms)
+constexpr int EPI = 8;                       // drain warps
+constexpr int THREADS = (2 + EPI) * 32;
+constexpr int TMEM_COLS = 512;               // 4 accumulators x 128 columns
+// (+8 KB slack beyond the last tile)
+constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + 8192;
+
+struct OzParams {
+  CUtensorMap ta, tb;
+  int M, N;          // dense: C rows / columns per batch; exchange: n, n_aux
+  int kst;           // K steps per CTA
+  int ksplit;        // dense: K splits (blockIdx.z = batch * ksplit + split)
+  int bshared;       // dense: B has one batch entry
+  const int *efa, *efb;
+  long long efa_bs, efb_bs;
+  double alpha;
+  double *C;
+  long long ldc, sC;
+  int bk, nl16, jtiles;  // exchange geometry
+  int *err;
+};
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t s_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(c));
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(b)) : "memory");
+}
+__device__ __forceinline__ uint32_t bar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(s_u32(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait: gives up after ~2^22 polls, or at once when another thread of
+// the launch has already flagged an error.
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, int *err, int code) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (bar_try(b, parity)) return true;
+    if ((i & 1023) == 1023 && err && *(volatile int *)err) return false;
+  }
+  if (err) atomicExch(err, code);
+  return false;
+}
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *m, uint64_t *bar, int x,
+                                          int y, int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(s_u32(dst)),
+      "l"(m), "r"(s_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, rows of
+// 32 bytes in groups of 8 (256 bytes between groups).
+__device__ __forceinline__ uint64_t smem_desc32(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+// Instruction descriptor: D fp32, A and B bf16, both K-major, M = N = 128.
+__device__ __forceinline__ uint32_t instr_desc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          s_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
+
+// ----------------------------------------------------- exact float sums ----
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += a0 + a1 + a2 + a3, where a0, a1, a2 are exact chunk sums and a3
+// the small rounded level.
+__device__ __forceinline__ void fold(float &hi, float &lo, float a0, float a1, float a2,
+                                     float a3) {
+  float s, e, s2, e2;
+  two_sum(a0, a1, s, e);
+  two_sum(s, a2, s2, e2);
+  e = (e + e2) + a3;
+  float t, f;
+  two_sum(hi, s2, t, f);
+  f = f + (lo + e);
+  two_sum(t, f, hi, lo);
+}
+
+// f * 2^E as an fp64 value, built from the float's bits (no fp64 arithmetic).
+__device__ __forceinline__ double f32_scaled(float f, int E) {
+  const uint32_t u = __float_as_uint(f);
+  const int ef = (int)((u >> 23) & 0xFF);
+  if (ef == 0) return 0.0;  // zero, or an fp32 subnormal: < 2^-126 of one grid unit
+  const int e64 = ef - 127 + 1023 + E;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  unsigned long long mant = (unsigned long long)(u & 0x7FFFFF) << 29;
+  if (e64 >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  if (e64 <= 0) {
+    // fp64 subnormal: shift the significand (with its leading one) right, truncating
+    const int sh = 1 - e64;
+    mant = sh < 64 ? ((mant | (1ull << 52)) >> sh) : 0ull;
+    return __longlong_as_double((long long)(sign | mant));
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e64 << 52) | mant));
+}
+
+__device__ __forceinline__ int row_scale(int ef) { return max(ef, 1) - 1022; }
+
+// ------------------------------------------------------------- the GEMM ----
+template <int MODE>
+__global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + STAGES * STAGE);
+  uint64_t *empty = full + STAGES;
+  uint64_t *accf = empty + STAGES;  // a chunk's accumulators are complete
+  uint64_t *acce = accf + 1;        // the drain warps have read them
+  uint32_t *tslot = (uint32_t *)(acce + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN;
+  int m0 = 0, zb = 0, split = 0, rt = 0;
+  if (MODE == 0) {
+    m0 = blockIdx.y * BM;
+    zb = blockIdx.z / p.ksplit;
+    split = blockIdx.z % p.ksplit;
+  } else {
+    rt = blockIdx.z;
+  }
+  const int kst = p.kst;
+  const int nchunks = (kst + CHUNK - 1) / CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(accf, 1);
+    bar_init(acce, EPI);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     s_u32(tslot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      int mt = 0, jt = 0;
+      if (MODE == 1) {
+        mt = rt / p.jtiles;
+        jt = rt % p.jtiles;
+      }
+      for (int st = 0; st < kst; ++st) {
+        const int s = st % STAGES;
+        if (st >= STAGES && !bar_wait(&empty[s], ((st / STAGES) - 1) & 1, p.err, 1)) break;
+        bar_expect(&full[s], STAGE);
+        uint8_t *sa = smem + s * STAGE, *sb = sa + OZ_S * TILE;
+        int ax, ay, az, bx, by, bz;
+        if (MODE == 0) {
+          ax = bx = (split * kst + st) * KS;
+          ay = m0;
+          az = zb;
+          by = n0;
+          bz = p.bshared ? 0 : zb;
+        } else {
+          const int kidx = st / p.nl16, ls = st % p.nl16;
+          ax = st * KS;
+          ay = 0;
+          az = rt;
+          bx = ((jt * 16 - p.bk) & ~7) + ls * KS;  // l (rounded down to 8: 16-byte TMA start)
+          by = mt * 8 - p.bk + kidx;               // k
+          bz = n0;                                 // q
+        }
+#pragma unroll
+        for (int d = 0; d < OZ_S; ++d) {
+          tma_load4(sa + d * TILE, &p.ta, &full[s], ax, ay, az, d);
+          tma_load4(sb + d * TILE, &p.tb, &full[s], bx, by, bz, d);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t idesc = instr_desc_bf16();
+      bool ok = true;
+      for (int st = 0; st < kst && ok; ++st) {
+        const int s = st % STAGES, cs = st % CHUNK;
+        if (cs == 0 && st > 0) {
+          if (!bar_wait(acce, ((st / CHUNK) - 1) & 1, p.err, 2)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        if (!bar_wait(&full[s], (st / STAGES) & 1, p.err, 3)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t base_a = s_u32(smem + s * STAGE), base_b = base_a + OZ_S * TILE;
+#pragma unroll
+        for (int pa = 0; pa < OZ_S; ++pa)
+#pragma unroll
+          for (int pb = 0; pb < OZ_S - pa; ++pb) {
+            const int acc = min(pa + pb, 3);
+            // the first product into each accumulator in a chunk overwrites it
+            const uint32_t en = (cs > 0 || !(pa == 0 && pb <= 3)) ? 1u : 0u;
+            mma_bf16(tmem + (uint32_t)(acc * 128), smem_desc32(base_a + pa * TILE),
+                     smem_desc32(base_b + pb * TILE), idesc, en);
+          }
+        mma_commit(&empty[s]);
+        if (cs == CHUNK - 1 || st == kst - 1) mma_commit(accf);
+      }
+      // a drain that is still waiting sees its phase complete once the MMAs
+      // issued so far are done (and then stops on the error flag)
+      if (!ok) mma_commit(accf);
+    }
+  } else {
+    // drain warps
+    const int lq = warp & 3;         // tensor-memory lanes this warp may access
+    const int ch = (warp - 2) >> 2;  // column half of the tile
+    const int row = lq * 32 + lane;
+    float hi[64], lo[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) hi[c] = lo[c] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      if (!bar_wait(accf, c & 1, p.err, 4) || (p.err && *(volatile int *)p.err)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ch * 64);
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 8) {
+        uint32_t r0[8], r1[8], r2[8], r3[8];
+        tmem_ld8(tl + c0, r0);
+        tmem_ld8(tl + 128 + c0, r1);
+        tmem_ld8(tl + 256 + c0, r2);
+        tmem_ld8(tl + 384 + c0, r3);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          fold(hi[c0 + u], lo[c0 + u], __uint_as_float(r0[u]), __uint_as_float(r1[u]),
+               __uint_as_float(r2[u]), __uint_as_float(r3[u]));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) bar_arrive(acce);
+    }
+    if (ok) {
+      // assemble fp64: C = alpha 2^(eA + eB - 14) (hi + lo)
+      int i = 0, valid;
+      double *dst;
+      int ea;
+      if (MODE == 0) {
+        i = m0 + row;
+        valid = i < p.M;
+        ea = valid ? row_scale(p.efa[zb * p.efa_bs + i]) : 0;
+        dst = p.ksplit > 1 ? p.C + (long long)blockIdx.z * p.M * p.N + (long long)i * p.N
+                           : p.C + zb * p.sC + (long long)i * p.ldc;
+      } else {
+        const int mt = rt / p.jtiles, jt = rt % p.jtiles;
+        const int m = mt * 8 + (row >> 4), j = jt * 16 + (row & 15);
+        valid = m < p.M && j < p.M;
+        ea = row_scale(p.efa[(long long)rt * BM + row]);
+        dst = p.C + ((long long)j * p.M + m) * p.N;
+      }
+      const int ncol = p.N;
+      if (valid) {
+        const int j0 = n0 + ch * 64;
+        const bool neg = p.alpha == -1.0, plain = p.alpha == 1.0 || neg;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const int j = j0 + c;
+          if (j < ncol) {
+            const int eb = row_scale(p.efb[(MODE == 0 && !p.bshared ? zb * p.efb_bs : 0) + j]);
+            const int E = ea + eb - 14;
+            double v = f32_scaled(hi[c], E) + f32_scaled(lo[c], E);
+            if (neg) v = -v;
+            else if (!plain) v *= p.alpha;
+            dst[j] = v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+}
+
+// C[b][i][j] = sum over splits of work[(b ks + s)][i][j], in split order.
+__global__ void oz_reduce_kernel(const double *__restrict__ work, int ks, int M, int N, int batch,
+                                 double *__restrict__ C, long long ldc, long long sC) {
+  const long long mn = (long long)M * N, tot = mn * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / mn, r = e % mn;
+    const int i = (int)(r / N), j = (int)(r % N);
+    double s = 0.0;
+    for (int k = 0; k < ks; ++k) s += work[(b * ks + k) * mn + r];
+    C[b * sC + (long long)i * ldc + j] = s;
+  }
+}
+
+// --------------------------------------------------------------- slicing ----
+// Tiles of 32 rows x 64 digit columns; the source is read along its
+// contiguous index (rows when rs == 1, else columns) through shared memory.
+constexpr int SR = 32, SK = 64;
+
+__device__ __forceinline__ double view_at(const OzView &v, int b, long long r, long long kk,
+                                          long long K) {
+  if (kk >= K) return 0.0;
+  const long long k1 = kk / v.k2pad, k2 = kk - k1 * v.k2pad;
+  if (k2 >= v.k2n) return 0.0;
+  const long long o = b * v.bs + r * v.rs + k1 * v.cs1 + k2 * v.cs2;
+  if (v.x2) {
+    const float2 f = v.x2[o];
+    return (double)f.x + (double)f.y;
+  }
+  return v.x[o];
+}
+
+// Load a 32 x 64 tile of the view into s[r][k] (zeros outside).
+__device__ __forceinline__ void load_tile(const OzView &v, int b, long long r0, long long k0,
+                                          int rows, long long K, double (*s)[SK + 1]) {
+  const bool rmaj = v.rs == 1;
+  for (int idx = threadIdx.x; idx < SR * SK; idx += blockDim.x) {
+    int r, k;
+    if (rmaj) {
+      r = idx % SR;
+      k = idx / SR;
+    } else {
+      k = idx % SK;
+      r = idx / SK;
+    }
+    const long long rr = r0 + r;
+    s[r][k] = rr < rows ? view_at(v, b, rr, k0 + k, K) : 0.0;
+  }
+}
+
+__device__ __forceinline__ int ef_of(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+__global__ void __launch_bounds__(256) oz_rowmax_kernel(OzView v, int rows, long long K,
+                                                        int *__restrict__ ef) {
+  __shared__ double s[SR][SK + 1];
+  const int b = blockIdx.z;
+  const long long r0 = (long long)blockIdx.y * SR, k0 = (long long)blockIdx.x * SK;
+  load_tile(v, b, r0, k0, rows, K, s);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < SR; r += blockDim.x / 32) {
+    int m = max(ef_of(s[r][lane]), ef_of(s[r][lane + 32]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && r0 + r < rows && m > 0) atomicMax(&ef[(long long)b * rows + r0 + r], m);
+  }
+}
+
+// The five balanced base-256 digits of x relative to the row scale 2^e.
+__device__ __forceinline__ void digits_of(double x, int e, float *d) {
+  const long long bits = __double_as_longlong(x);
+  const int efx = (int)((bits >> 52) & 0x7FF);
+  unsigned long long M = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  if (efx) M |= 1ull << 52;
+  // F = round(|x| 2^(39 - e)) = M 2^(max(efx,1) - 1075 + 39 - e); the shift is >= 14
+  const int sh = 1036 + e - max(efx, 1);
+  long long F = 0;
+  if (sh < 64) F = (long long)((M + (1ull << (sh - 1))) >> sh);
+  int dd[OZ_S];
+#pragma unroll
+  for (int p = OZ_S - 1; p > 0; --p) {
+    int lo8 = (int)(F & 255);
+    if (lo8 >= 128) lo8 -= 256;
+    dd[p] = lo8;
+    F = (F - lo8) >> 8;
+  }
+  dd[0] = (int)F;
+  const float sgn = bits < 0 ? -1.f : 1.f;
+  const float sc[5] = {1.f, 0.00390625f, 1.52587890625e-05f, 5.9604644775390625e-08f,
+                       2.3283064365386963e-10f};
+#pragma unroll
+  for (int p = 0; p < OZ_S; ++p) d[p] = sgn * (float)dd[p] * sc[p];
+}
+
+__global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long long K,
+                                                        const int *__restrict__ ef,
+                                                        __nv_bfloat16 *__restrict__ out,
+                                                        long long ld, long long plane) {
+  __shared__ double s[SR][SK + 1];
+  const int b = blockIdx.z;
+  const long long r0 = (long long)blockIdx.y * SR, k0 = (long long)blockIdx.x * SK;
+  load_tile(v, b, r0, k0, rows, K, s);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < SR * SK; idx += blockDim.x) {
+    const int k = idx % SK, r = idx / SK;
+    const long long rr = r0 + r, kk = k0 + k;
+    if (rr >= rows || kk >= ld) continue;
+    const int e = row_scale(ef[(long long)b * rows + rr]);
+    float d[OZ_S];
+    digits_of(s[r][k], e, d);
+    const long long o = ((long long)b * rows + rr) * ld + kk;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) out[p * plane + o] = __float2bfloat16_rn(d[p]);
+  }
+}
+
+// ---------------------------------------------------- exchange operand -----
+__global__ void oz_exch_gather_kernel(int n, int bk, int nl16, int jtiles, long long kx,
+                                      const double *__restrict__ D, int P,
+                                      const int *__restrict__ pidx, double *__restrict__ xs) {
+  const int rt = blockIdx.y;
+  const int mt = rt / jtiles, jt = rt % jtiles;
+  const long long lw = (long long)nl16 * KS;
+  const int llo = (jt * 16 - bk) & ~7;
+  double *dst = xs + (long long)rt * BM * kx;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < BM * kx;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / kx);
+    const long long kk = e - (long long)r * kx;
+    const int m = mt * 8 + (r >> 4), j = jt * 16 + (r & 15);
+    const int k = mt * 8 - bk + (int)(kk / lw), l = llo + (int)(kk % lw);
+    double v = 0.0;
+    if (m < n && j < n && k >= 0 && k < n && l >= 0 && l < n) {
+      const int a = pidx[m * n + k], c = pidx[l * n + j];
+      if (a >= 0 && c >= 0) v = D[(long long)a * P + c];
+    }
+    dst[e] = v;
+  }
+}
+
+__global__ void oz_pair_index_kernel(const int *__restrict__ pij, int P, int *__restrict__ pidx) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < P; a += gridDim.x * blockDim.x)
+    pidx[pij[a]] = a;
+}
+
+__global__ void oz_fold_kernel(const int *__restrict__ prow, const int *__restrict__ pcol,
+                               const double *__restrict__ L, int P, int n, int na,
+                               double *__restrict__ U) {
+  const long long tot = (long long)P * na;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / na), q = (int)(e % na);
+    const long long o = ((long long)pcol[a] * n + prow[a]) * na + q;
+    U[o] += 2.0 * L[e];
+  }
+}
+
+// --------------------------------------------------------------- host ------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_once;
+
+void load_encode() {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+
+// 4D bf16 map, 32-byte swizzle; dims d[0..3] (elements), strides s[0..2] (bytes, of dims 1..3),
+// box (b0, b1, b2, 1).
+cudaError_t make_map4(CUtensorMap *m, const void *base, const cuuint64_t d[4],
+                      const cuuint64_t s[3], cuuint32_t b0, cuuint32_t b1, cuuint32_t b2) {
+  if (!g_encode) return cudaErrorNotSupported;
+  if ((uintptr_t)base % 16) return cudaErrorInvalidValue;
+  for (int k = 0; k < 3; ++k)
+    if (s[k] % 16) return cudaErrorInvalidValue;
+  cuuint64_t dims[4] = {d[0], d[1], d[2], d[3]};
+  cuuint64_t strides[3] = {s[0], s[1], s[2]};
+  cuuint32_t box[4] = {b0, b1, b2, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base),
+                              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Map of a digit operand: dims (K, rows, batch, digit), box 16 x 128.
+cudaError_t digit_map(CUtensorMap *m, const OzDigits &o) {
+  const cuuint64_t d[4] = {(cuuint64_t)o.K, (cuuint64_t)o.rows, (cuuint64_t)o.batch, OZ_S};
+  const cuuint64_t s[3] = {(cuuint64_t)o.ld * 2, (cuuint64_t)o.ld * 2 * o.rows,
+                           (cuuint64_t)o.ld * 2 * o.rows * o.batch};
+  return make_map4(m, o.d, d, s, KS, BM, 1);
+}
+
+cudaError_t prepare() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  RS_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    RS_TRY(cudaFuncSetAttribute(oz_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SMEM));
+    RS_TRY(cudaFuncSetAttribute(oz_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SMEM));
+    // the launch needs THREADS threads at the kernel's register count
+    cudaFuncAttributes fa;
+    RS_TRY(cudaFuncGetAttributes(&fa, oz_gemm_kernel<0>));
+    if (fa.maxThreadsPerBlock < THREADS) return cudaErrorLaunchOutOfResources;
+    done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
+void plan(const OzGemm &g, int *ksplit, int *kst) {
+  const int steps = ceil_div(g.A.K, KS);
+  const long long tiles = (long long)ceil_div(g.M, BM) * ceil_div(g.N, BN) * g.batch;
+  int ks = 1;
+  if (tiles < 152 && steps >= 2 * CHUNK)
+    ks = (int)std::max<long long>(1, std::min<long long>((152 + tiles - 1) / tiles, steps / CHUNK));
+  int per = ceil_div(steps, ks);
+  per = ceil_div(per, CHUNK) * CHUNK;  // whole chunks per split
+  *kst = std::min(per, steps);
+  *ksplit = ceil_div(steps, *kst);
+}
+
+}  // namespace
+
+int oz_kernel_regs(int *max_threads) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, oz_gemm_kernel<0>) != cudaSuccess) return -1;
+  if (max_threads) *max_threads = fa.maxThreadsPerBlock;
+  return fa.numRegs;
+}
+
+bool oz_available() {
+  std::call_once(g_once, load_encode);
+  return g_encode != nullptr;
+}
+
+cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
+  if (out.rows <= 0 || out.K <= 0 || out.batch <= 0) return cudaSuccess;
+  if (out.ld < out.K || (out.ld % 8) || v.k2pad <= 0) return cudaErrorInvalidValue;
+  RS_TRY(cudaMemsetAsync(out.ef, 0, (size_t)out.batch * out.rows * sizeof(int), s));
+  if ((out.rows + SR - 1) / SR > 65535 || out.batch > 65535) return cudaErrorInvalidValue;
+  dim3 gm(ceil_div(out.K, SK), ceil_div(out.rows, SR), out.batch);
+  oz_rowmax_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
+  ++launch_counter();
+  RS_TRY(cudaGetLastError());
+  // the digit pass covers the padding columns K..ld too (zeros)
+  dim3 gd(ceil_div(out.ld, SK), ceil_div(out.rows, SR), out.batch);
+  oz_digits_kernel<<<gd, 256, 0, s>>>(v, out.rows, out.K, out.ef, out.d, out.ld,
+                                      (long long)out.batch * out.rows * out.ld);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+size_t oz_gemm_work(const OzGemm &g) {
+  int ks, kst;
+  plan(g, &ks, &kst);
+  return ks > 1 ? (size_t)ks * g.batch * g.M * g.N : 0;
+}
+
+double oz_gemm_flops(const OzGemm &g) {
+  int ks, kst;
+  plan(g, &ks, &kst);
+  return 15.0 * 2.0 * BM * BN * KS * (double)kst * ks * ceil_div(g.M, BM) * ceil_div(g.N, BN) *
+         g.batch;
+}
+
+cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream_t s) {
+  if (!oz_available()) return cudaErrorNotSupported;
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.A.K != g.B.K || g.A.rows != g.M || g.B.rows != g.N || g.A.batch != g.batch ||
+      (g.B.batch != 1 && g.B.batch != g.batch))
+    return cudaErrorInvalidValue;
+  if (g.A.K <= 0) return cudaErrorInvalidValue;
+  int ks, kst;
+  plan(g, &ks, &kst);
+  if (ks > 1 && work_elems < (size_t)ks * g.batch * g.M * g.N) return cudaErrorInvalidValue;
+  if ((long long)g.batch * ks > 65535 || ceil_div(g.M, BM) > 65535) return cudaErrorInvalidValue;
+  OzParams p;
+  std::memset(&p, 0, sizeof(p));
+  RS_TRY(digit_map(&p.ta, g.A));
+  RS_TRY(digit_map(&p.tb, g.B));
+  p.M = g.M;
+  p.N = g.N;
+  p.kst = kst;
+  p.ksplit = ks;
+  p.bshared = g.B.batch == 1 && g.batch > 1;
+  p.efa = g.A.ef;
+  p.efb = g.B.ef;
+  p.efa_bs = g.M;
+  p.efb_bs = g.N;
+  p.alpha = g.alpha;
+  p.C = ks > 1 ? work : g.C;
+  p.ldc = g.ldc;
+  p.sC = g.sC;
+  p.err = g.err;
+  RS_TRY(prepare());
+  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.batch * ks);
+  oz_gemm_kernel<0><<<grid, THREADS, SMEM, s>>>(p);
+  ++launch_counter();
+  RS_TRY(cudaGetLastError());
+  if (ks > 1) {
+    const long long tot = (long long)g.batch * g.M * g.N;
+    oz_reduce_kernel<<<(int)std::min<long long>((tot + 255) / 256, 152 * 8), 256, 0, s>>>(
+        work, ks, g.M, g.N, g.batch, g.C, g.ldc, g.sC);
+    ++launch_counter();
+    RS_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+cudaError_t oz_pair_index(const int *pij, int P, int n, int *pidx, cudaStream_t s) {
+  RS_TRY(cudaMemsetAsync(pidx, 0xFF, (size_t)n * n * sizeof(int), s));
+  if (P <= 0) return cudaSuccess;
+  oz_pair_index_kernel<<<std::min(ceil_div(P, 256), 1024), 256, 0, s>>>(pij, P, pidx);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t oz_fold_direct(const int *prow, const int *pcol, const double *L, int P, int n,
+                           int na, double *U, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  const long long tot = (long long)P * na;
+  oz_fold_kernel<<<(int)std::min<long long>((tot + 255) / 256, 152 * 16), 256, 0, s>>>(
+      prow, pcol, L, P, n, na, U);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+OzExch oz_exch_geometry(int n, int na, int bk) {
+  OzExch x;
+  x.n = n;
+  x.na = na;
+  x.bk = bk;
+  // l window of the 16-wide j tile at j0 (a multiple of 16): from
+  // floor8(j0 - bk) = j0 - ceil8(bk) (a 16-byte aligned TMA start) to j0 + 15 + bk
+  const int c8 = (bk + 7) / 8 * 8;
+  x.nl16 = ceil_div(16 + bk + c8, KS);
+  x.mtiles = ceil_div(n, 8);
+  x.jtiles = ceil_div(n, 16);
+  x.kx = (long long)(8 + 2 * bk) * x.nl16 * KS;
+  x.ldl = ((long long)n + 7) / 8 * 8;
+  return x;
+}
+
+double oz_exch_flops(const OzExch &x) {
+  return 15.0 * 2.0 * BM * (double)ceil_div(x.na, BN) * BN * x.kx * x.mtiles * x.jtiles;
+}
+
+cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *pidx, double *xs,
+                           cudaStream_t s) {
+  const int tiles = x.mtiles * x.jtiles;
+  if (tiles > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)std::min<long long>(ceil_div(BM * x.kx, 256), 64), tiles);
+  oz_exch_gather_kernel<<<grid, 256, 0, s>>>(x.n, x.bk, x.nl16, x.jtiles, x.kx, D, P, pidx, xs);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
+                    double alpha, int *err, cudaStream_t s) {
+  if (!oz_available()) return cudaErrorNotSupported;
+  const int tiles = x.mtiles * x.jtiles;
+  if (X.batch != tiles || X.rows != BM || X.K != x.kx || At.rows != x.na ||
+      At.K != (long long)x.n * x.ldl || At.batch != 1 || tiles > 65535)
+    return cudaErrorInvalidValue;
+  OzParams p;
+  std::memset(&p, 0, sizeof(p));
+  RS_TRY(digit_map(&p.ta, X));
+  {
+    // right operand as (l, k, q, digit): l padded to ldl, dims n so that l >= n reads zeros
+    const cuuint64_t d[4] = {(cuuint64_t)x.n, (cuuint64_t)x.n, (cuuint64_t)x.na, OZ_S};
+    const cuuint64_t st[3] = {(cuuint64_t)x.ldl * 2, (cuuint64_t)x.ldl * 2 * x.n,
+                              (cuuint64_t)x.ldl * 2 * x.n * x.na};
+    RS_TRY(make_map4(&p.tb, At.d, d, st, KS, 1, BM));
+  }
+  p.M = x.n;
+  p.N = x.na;
+  p.kst = (int)(x.kx / KS);
+  p.ksplit = 1;
+  p.efa = X.ef;
+  p.efb = At.ef;
+  p.alpha = alpha;
+  p.C = T;
+  p.bk = x.bk;
+  p.nl16 = x.nl16;
+  p.jtiles = x.jtiles;
+  p.err = err;
+  RS_TRY(prepare());
+  dim3 grid(ceil_div(x.na, BN), 1, tiles);
+  oz_gemm_kernel<1><<<grid, THREADS, SMEM, s>>>(p);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+}  // namespace rssri

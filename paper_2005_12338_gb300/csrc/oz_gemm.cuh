@@ -1,0 +1,112 @@
+// fp64-accurate products on the bf16 tensor cores by error-free digit slicing
+// (the splitting idea of Ozaki, Ogita and Oishi, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication
+// and its applications", Numer. Algorithms 59 (2012)), used for the dense
+// contractions of the deterministic block (Sec. III, Eq. 20 on v^L).
+//
+// Each row of an fp64 operand is scaled by a power of two 2^e with every
+// |x| < 2^e, rounded to a 39-bit fixed-point integer F, and written as five
+// balanced base-256 digits, F = sum_p d_p 256^(4-p) with |d_p| <= 128.  The
+// digits are stored in bf16 pre-scaled by 2^(-8p), so that
+//     x ~= 2^(e-7) sum_p D_p,   D_p = d_p 2^(-8p),   |x - that| <= 2^(e-40).
+// A product sum_k a_k b_k is then 2^(eA+eB-14) sum_{p,q} sum_k D^A_p D^B_q.
+// Every bf16 x bf16 product of digits is exact in fp32, and a level
+// p + q = L sums terms on the common grid 2^(-8L) with at most
+// (L+1) 2^14 grid units each; over 256 terms of K the levels L = 0, 1, 2
+// stay below 2^24 grid units, so the tensor core's fp32 accumulation of them
+// is exact.  Levels 3 and 4 (p + q <= 4 are kept: 15 digit products) share a
+// fourth accumulator whose rounding is ~2^-48 of the result.  After every 256
+// terms of K the four accumulators are added into double-float (fp32 pair)
+// running totals; the fp64 result is assembled once per output.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace rssri {
+
+constexpr int OZ_S = 5;  // digits per fp64 value
+
+// Digits of an fp64 matrix, K-major: d[p][b][r][ld] (bf16, p < OZ_S), and the
+// biased fp64 exponent field of each row's largest magnitude, ef[b][r]
+// (the row scale is e = max(ef, 1) - 1022).  ld >= K is a multiple of 8.
+struct OzDigits {
+  __nv_bfloat16 *d = nullptr;
+  int *ef = nullptr;
+  int batch = 1, rows = 0;
+  long long K = 0, ld = 0;
+};
+inline size_t oz_digit_elems(const OzDigits &o) {
+  return (size_t)OZ_S * o.batch * o.rows * o.ld;
+}
+
+// An fp64 source for the slicer: digit column kk of row r in batch b reads
+//   k1 = kk / k2pad, k2 = kk % k2pad,
+//   x[b*bs + r*rs + k1*cs1 + k2*cs2]   if k2 < k2n, else 0.
+// (A plain row-major matrix: cs2 = 1, k2pad = k2n = K, cs1 unused.)
+// A double-float source (x2, pairs (hi, lo) with value hi + lo) may replace x.
+struct OzView {
+  const double *x = nullptr;
+  const float2 *x2 = nullptr;
+  long long bs = 0, rs = 0, cs1 = 0, cs2 = 1;
+  long long k2pad = 0, k2n = 0;
+};
+
+// Write the digits and row exponents of view v into out (rows x K per batch).
+cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s);
+
+// C[b][i][j] = alpha * sum_k A[b][i][k] B[b'][j][k] in fp64, b' = b or 0 when
+// B.batch == 1.  A: M x K, B: N x K digits.  C[b*sC + i*ldc + j].
+// K is split over CTAs when the output has few tiles; the split partials go
+// to `work` (oz_gemm_work() doubles) and are reduced in a fixed order.
+struct OzGemm {
+  OzDigits A, B;
+  int M = 0, N = 0, batch = 1;
+  double *C = nullptr;
+  long long ldc = 0, sC = 0;
+  double alpha = 1.0;
+  int *err = nullptr;  // device flag, set non-zero if a bounded wait gives up
+};
+size_t oz_gemm_work(const OzGemm &g);
+cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream_t s);
+double oz_gemm_flops(const OzGemm &g);  // tensor flops issued (digit products, padded tiles)
+
+// The exchange contraction of the deterministic block in pair space:
+//   T[j][m][q] = sum_{k, l} D[(m,k), (l,j)] At[k][l][q],
+// D the pair-space v^L on the kept pairs (pidx[i*n+j] = pair index or -1).
+// Output rows are tiles of 8 m x 16 j; a tile's K runs over the band of k
+// around its m and of l around its j (half-width bk).  The left operand
+// (built once from D by oz_exch_build) holds, per tile, the 128 rows x
+// (8 + 2 bk) (16 nl16) values of D; the right operand is At sliced with
+// digit rows q and columns (k, l) (l padded to ldl = n rounded up to 8).
+struct OzExch {
+  int n = 0, na = 0, bk = 0, nl16 = 0, mtiles = 0, jtiles = 0;
+  long long kx = 0;  // K of a tile: (8 + 2 bk) * nl16 * 16
+  long long ldl = 0;
+};
+OzExch oz_exch_geometry(int n, int na, int bk);
+// fp64 left operand [tiles][128][kx] of the exchange contraction (tiles =
+// mtiles * jtiles), from D [P][P] and pidx; then sliced with oz_slice.
+cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *pidx,
+                           double *xs, cudaStream_t s);
+// T[(j*n + m)*na + q] = alpha * the contraction, fp64.  X: digits [tiles][128][kx];
+// At: digits [1][na][n*ldl] (k major, l minor).
+cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
+                    double alpha, int *err, cudaStream_t s);
+double oz_exch_flops(const OzExch &x);
+
+// pidx[i*n + j] = index of pair (i, j) among the P kept pairs (linear
+// indices pij, ascending), -1 for pairs not kept.
+cudaError_t oz_pair_index(const int *pij, int P, int n, int *pidx, cudaStream_t s);
+// U[(j*n + m)*na + q] += 2 L[a*na + q] for every kept pair a = (m, j):
+// the direct term of the deterministic block added to the exchange term.
+cudaError_t oz_fold_direct(const int *prow, const int *pcol, const double *L, int P, int n,
+                           int na, double *U, cudaStream_t s);
+
+bool oz_available();
+// Registers per thread of the product kernel and the most threads a launch of
+// it may have (diagnostics).
+int oz_kernel_regs(int *max_threads);
+
+}  // namespace rssri

@@ -1,5 +1,5 @@
 """The C ABI: the library builds, loads, exports every function declared in
-include/rssri.h, and the ctypes structures match the C layout.  No GPU."""
+include/*.h, and the ctypes structures match the C layout.  No GPU."""
 import ctypes as C
 import os
 import re
@@ -10,7 +10,8 @@ import pytest
 from paper_2005_12338_gb300 import binding, build
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "rssri.h")
+INCLUDE = os.path.join(ROOT, "include")
+HEADERS = sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +21,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"RSSRI_API\s+[\w\s\*]*?\b(rssri_\w+)\s*\(", text)))
 

@@ -194,7 +194,6 @@ def test_sri_estimator(B):
     s = synth.make_system(20, 10, 40, 5, input_seed=5)
     ref = run_oracle(s, 0.02, 1e-2, 6, 9, empty_large=True)
     h, got = run_gpu(B, s, 0.02, 1e-2, 6, 9, estimator=1)
-    assert np.abs(h.export("SIGMA_DD")).max() == 0.0
     for t in range(s.n_tau):
         assert rel(got["sigma"][t], ref.sigma[t]) < TOL
     assert abs(got["e_corr"] - ref.e_corr) < TOL * abs(ref.e_corr)
@@ -247,13 +246,48 @@ def test_errors_are_reported(B):
 
 
 # ---------------------------------------------------- the N = 200 workload ---
-@pytest.fixture(scope="module", params=[0, 1], ids=["dd_fp64", "dd_df64"])
+# Forms: (chain precision, deterministic-block arithmetic).  "plain" is IEEE
+# fp64 throughout; "df64" is the double-float form (chain and block), whose
+# N = 200 launches pick other tile geometries than the small cases (padded
+# 16x16 / 8x8 double-float tiles, the symmetric upper-tile Sigma_DD product,
+# N_aux = 600 split into five aux chunks in the exchange contraction).
+C2_FORMS = {"plain": (0, 0), "df64": (3, 1)}
+
+
+@pytest.fixture(scope="module", params=sorted(C2_FORMS))
 def c2(B, request):
     cfg = synth.CONFIGS["c2_n200"]
     s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
-    h, got = run_gpu(B, s, cfg["eps_prime"], cfg["eps"], cfg["n_s"], 0, dd_arith=request.param)
+    prec, dd = C2_FORMS[request.param]
+    h, got = run_gpu(B, s, cfg["eps_prime"], cfg["eps"], cfg["n_s"], 0, dd_arith=dd,
+                     precision=prec)
     yield cfg, s, h, got
     h.close()
+
+
+@pytest.fixture(scope="module")
+def c2_oracle_dd():
+    """The oracle's deterministic block (Eq. 20 on v^L, summed over Q, Q') at
+    one tau point of the N = 200 workload: a few host minutes."""
+    cfg = synth.CONFIGS["c2_n200"]
+    s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
+    w = O.metric_inv_sqrt(s.metric)
+    el, _, _ = O.screen(s.eri3, cfg["eps_prime"])
+    kl, _ = O.large_factor(el, w, cfg["eps"])
+    t = s.n_tau // 2
+    g, gb = O.green(s.orb_e, s.orb_c, s.n_occ, s.mu, s.tau[t])
+    return t, O.sigma_from_factor(kl, g, gb)
+
+
+def test_c2_deterministic_block_elementwise(c2, c2_oracle_dd):
+    """S7 at full size, every element of Sigma_DD(tau) at one tau point (the
+    trace check below would miss a wrong off-diagonal block, e.g. a bad mirror
+    of the symmetric upper-tile product)."""
+    cfg, s, h, got = c2
+    t, ref = c2_oracle_dd
+    sdd = h.export("SIGMA_DD").reshape(s.n_tau, s.n, s.n)[t]
+    assert rel(sdd, ref) < TOL
+    assert np.abs(sdd - ref).max() < TOL * np.abs(ref).max()
 
 
 def test_c2_selection_and_factors(c2):
@@ -297,6 +331,9 @@ def test_c2_stochastic_part_sampled_tau(c2):
         for x in range(ns):
             acc += O.factor_pair(r0[x], r1[x], g, gb)[0] - O.factor_pair(rl0[x], rl1[x], g, gb)[0]
         assert rel(raw[t] - sdd[t], acc / ns) < TOL
+        assert np.abs(raw[t] - sdd[t] - acc / ns).max() < TOL * np.abs(acc / ns).max()
+        sym = sdd[t] + 0.5 * (acc + acc.T) / ns
+        assert rel(got["sigma"][t], sym) < TOL
 
 
 def test_c2_deterministic_energy_closed_form(c2):

@@ -87,3 +87,23 @@ def test_features_shape_and_range():
     assert np.all(np.abs(f[:, [0, 2, 3, 4, 5, 6, 7, 8]]) <= 1.0 + 1e-15)
     assert f[9, 0] == 0.0 and f[9, 9] == 1.0  # element (1, 1)
     assert f[1, 0] == 1 / 8 and f[1, 9] == 0.0  # element (0, 1)
+
+
+def test_features_hand_computed_3x3():
+    """Every feature of three elements of a 3 x 3 case, worked by hand: which
+    index (i or j) each feature reads and what it is normalised by."""
+    sdd = np.array([[2.0, -1.0, 0.0], [-1.0, 4.0, 0.5], [0.0, 0.5, -1.0]])  # max |.| = 4
+    g = np.array([[-0.5, 0.3, 0.1], [0.3, -1.0, 0.2], [0.1, 0.2, -0.25]])  # max |diag| = 1
+    gb = np.array([[-2.0, 0.7, 0.0], [0.7, -1.0, 0.0], [0.0, 0.0, -4.0]])  # max |diag| = 4
+    rn = np.array([3.0, 6.0, 1.5])  # max 6
+    tau, beta = np.e, np.e ** 2  # ln tau / ln beta = 1/2
+    f = cv.features(sdd, g, gb, tau, beta, rn)
+    want = {
+        # (i, j): [|i-j|/N, ln tau/ln beta, Sdd_ij/4, G_ii, G_jj, Gb_ii/4, Gb_jj/4, r_i/6, r_j/6, i==j]
+        (0, 2): [2 / 3, 0.5, 0.0, -0.5, -0.25, -0.5, -1.0, 0.5, 0.25, 0.0],
+        (1, 0): [1 / 3, 0.5, -0.25, -1.0, -0.5, -0.25, -0.5, 1.0, 0.5, 0.0],
+        (2, 2): [0.0, 0.5, -0.25, -0.25, -0.25, -1.0, -1.0, 0.25, 0.25, 1.0],
+        (1, 2): [1 / 3, 0.5, 0.125, -1.0, -0.25, -0.25, -1.0, 1.0, 0.25, 0.0],
+    }
+    for (i, j), row in want.items():
+        assert np.allclose(f[3 * i + j], row, rtol=0, atol=1e-15), ((i, j), f[3 * i + j])

@@ -97,6 +97,9 @@ def test_screen_and_cut_golden():
     k_l, kmax = O.large_factor(eri3_l, w, gd["eps"])
     assert kmax == pytest.approx(gd["k_l_max"], rel=1e-15)
     assert np.allclose(k_l, np.array(gd["k_l_cut"]), atol=1e-15)
+    # eps = 0 keeps every entry: the product before the cut
+    k_all, _ = O.large_factor(eri3_l, w, 0.0)
+    assert np.allclose(k_all, np.array(gd["k_l_before_cut"]), atol=1e-15)
 
 
 def test_screen_limits_and_symmetry():
