@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librssri.so")
+# RSSRI_CHECKS=1: the build whose kernels check their own indices (see build.py)
+LIB_PATH = os.path.join(HERE, "librssri_checks.so" if os.environ.get("RSSRI_CHECKS", "") == "1"
+                        else "librssri.so")
 
 RSSRI_PTR_DEVICE, RSSRI_PTR_HOST = 0, 1
 RSSRI_EST_CV, RSSRI_EST_SRI, RSSRI_EST_LITERAL = 0, 1, 2

@@ -16,8 +16,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "librssri.so")
+# RSSRI_CHECKS=1 in the environment builds (and binding.py loads) a separate
+# library whose kernels check their own indices: the first out-of-range
+# access is recorded and skipped, and the call returns an error.
+CHECKS = os.environ.get("RSSRI_CHECKS", "") == "1"
+BUILD = os.path.join(HERE, "_build_checks" if CHECKS else "_build")
+LIB = os.path.join(HERE, "librssri_checks.so" if CHECKS else "librssri.so")
 SOURCES = ["api.cu", "gemm_f64.cu", "kernels.cu", "static_energy.cu", "tc_gemm.cu", "chain_tc.cu",
            "dd_df64.cu", "dd_spmm_df64.cu", "cv_mlp.cu", "peak.cu", "oz_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -51,6 +55,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
                     "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+    if CHECKS:
+        flags.append("-DRSSRI_CHECKS")
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

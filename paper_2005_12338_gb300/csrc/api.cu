@@ -2,6 +2,7 @@
 // RS-SRI-GF2 self-energy path (see include/rssri.h for the contract).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -842,12 +843,14 @@ int oz_setup(rssri_handle *h) {
   if (tiles > 65535) return RSSRI_ERR_INVALID_ARG;
   RS_CK(ensure(h->oz_tmp, (size_t)tiles * 128 * x.kx * sizeof(double)));
   { SPAN(RSSRI_PROF_OTHER, 0.0);
-    RS_CK(oz_exch_gather(x, h->D.as<double>(), P, h->oz_pidx.as<int>(), h->oz_tmp.as<double>(), s)); }
+    RS_CK(oz_exch_gather(x, h->D.as<double>(), P, h->oz_pidx.as<int>(), h->oz_tmp.as<double>(),
+                         (long long)tiles * 128 * x.kx, s)); }
   RS_CK(oz_make(h->ozX, tiles, 128, x.kx));
   {
     OzView v;
     v.x = h->oz_tmp.as<double>();
     v.bs = 128 * x.kx; v.rs = x.kx; v.cs2 = 1; v.k2pad = v.k2n = x.kx;
+    v.xlen = (long long)tiles * 128 * x.kx;
     RS_CK(oz_slice_p(h, v, h->ozX.v));
   }
   // K_P [P][na]: digits with rows a (for L) and rows Q (for Gamma)
@@ -856,11 +859,11 @@ int oz_setup(rssri_handle *h) {
   {
     OzView v;
     v.x = h->KP.as<double>();
-    v.rs = na; v.cs2 = 1; v.k2pad = v.k2n = na;
+    v.rs = na; v.cs2 = 1; v.k2pad = v.k2n = na; v.xlen = (long long)P * na;
     RS_CK(oz_slice_p(h, v, h->ozKP.v));
     OzView t;
     t.x = h->KP.as<double>();
-    t.rs = 1; t.cs2 = na; t.k2pad = t.k2n = P;
+    t.rs = 1; t.cs2 = na; t.k2pad = t.k2n = P; t.xlen = (long long)P * na;
     RS_CK(oz_slice_p(h, t, h->ozKPt.v));
   }
   RS_CK(cudaStreamSynchronize(s));
@@ -889,43 +892,46 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
                              h->KPhl.as<float2>(), na, PGhl, na, (long long)n * na, s)); }
   // At[k][(l,Q)] = sum_m Gb[k][m] PG[m][(l,Q)]
   OzDigits &dGb = h->ozGb.v;
-  { OzView v; v.x = Gb; v.rs = n; v.cs2 = 1; v.k2pad = v.k2n = n;
+  { OzView v; v.x = Gb; v.rs = n; v.cs2 = 1; v.k2pad = v.k2n = n; v.xlen = nn;
     RS_TRY(oz_slice_p(h, v, dGb)); }
   OzDigits dPGb = h->ozBig0.v;
   dPGb.rows = (int)(n * (long long)na); dPGb.K = n; dPGb.ld = (n + 7) / 8 * 8;
   { OzView v; v.x2 = PGhl; v.rs = 1; v.cs2 = (long long)n * na; v.k2pad = v.k2n = n;
+    v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dPGb)); }
   {
     OzGemm g;
     g.A = dGb; g.B = dPGb; g.M = n; g.N = (int)(n * (long long)na);
-    g.C = At; g.ldc = (long long)n * na; g.err = err;
+    g.C = At; g.ldc = (long long)n * na; g.ccap = nna; g.err = err;
     RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // the exchange contraction: T[j][m][Q] = -sum D[(m,k),(l,j)] At[k][l][Q]
   OzDigits dAt = h->ozBig1.v;
   dAt.rows = na; dAt.K = (long long)n * x.ldl; dAt.ld = dAt.K;
   { OzView v; v.x = At; v.rs = 1; v.cs1 = (long long)n * na; v.cs2 = na; v.k2pad = x.ldl;
-    v.k2n = n;
+    v.k2n = n; v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dAt)); }
   { SPAN_T(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9, oz_exch_flops(x) * 1e-9);
-    RS_TRY(oz_exch(x, h->ozX.v, dAt, T, -1.0, err, s)); }
+    RS_TRY(oz_exch(x, h->ozX.v, dAt, T, nna, -1.0, err, s)); }
   // Gamma = K_P^T At_P (At_P: the rows of At at the kept pairs)
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
   { OzView v; v.x = h->AP.as<double>(); v.rs = 1; v.cs2 = na; v.k2pad = v.k2n = P;
+    v.xlen = (long long)P * na;
     RS_TRY(oz_slice_p(h, v, h->ozAtP.v)); }
   {
     OzGemm g;
     g.A = h->ozKPt.v; g.B = h->ozAtP.v; g.M = na; g.N = na;
-    g.C = h->Gam.as<double>(); g.ldc = na; g.err = err;
+    g.C = h->Gam.as<double>(); g.ldc = na; g.ccap = (long long)na * na; g.err = err;
     RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // L[a][Q] = sum_Q' K_P[a][Q'] Gamma[Q][Q']
   { OzView v; v.x = h->Gam.as<double>(); v.rs = na; v.cs2 = 1; v.k2pad = v.k2n = na;
+    v.xlen = (long long)na * na;
     RS_TRY(oz_slice_p(h, v, h->ozGam.v)); }
   {
     OzGemm g;
     g.A = h->ozKP.v; g.B = h->ozGam.v; g.M = P; g.N = na;
-    g.C = h->L.as<double>(); g.ldc = na; g.err = err;
+    g.C = h->L.as<double>(); g.ldc = na; g.ccap = (long long)P * na; g.err = err;
     RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   // U = 2 L - T at the kept pairs (T already negated)
@@ -933,17 +939,20 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
     RS_TRY(oz_fold_direct(h->prow.as<int>(), h->pcol.as<int>(), h->L.as<double>(), P, n, na, T, s)); }
   // Sigma_DD[i][j] = sum_{(m,Q)} PG[i][m][Q] U[j][m][Q]
   OzDigits dU = h->ozBig0.v;
-  dU.rows = n; dU.K = nna; dU.ld = (nna + 7) / 8 * 8;
+  const long long kmq = (long long)n * na;  // the contraction index (m, Q)
+  dU.rows = n; dU.K = kmq; dU.ld = (kmq + 7) / 8 * 8;
   { OzView v; v.x = T; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dU.K;
+    v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dU)); }
   OzDigits dPGa = h->ozBig1.v;
-  dPGa.rows = n; dPGa.K = nna; dPGa.ld = (nna + 7) / 8 * 8;
+  dPGa.rows = n; dPGa.K = kmq; dPGa.ld = (kmq + 7) / 8 * 8;
   { OzView v; v.x2 = PGhl; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dPGa.K;
+    v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dPGa)); }
   {
     OzGemm g;
     g.A = dPGa; g.B = dU; g.M = n; g.N = n;
-    g.C = out; g.ldc = n; g.err = err;
+    g.C = out; g.ldc = n; g.ccap = nn; g.err = err;
     RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   return cudaSuccess;
@@ -1019,8 +1028,8 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
       }
       // the largest per-tau digit operand: n*na rows of ld8(n), n rows of ld8(n*na), or
       // na rows of n*ldl
-      const long long ld_n = (n + 7) / 8 * 8, ld_nna = (nn * na + 7) / 8 * 8;
-      const long long big = std::max({(long long)n * na * ld_n, (long long)n * ld_nna,
+      const long long ld_n = (n + 7) / 8 * 8, ld_kmq = ((long long)n * na + 7) / 8 * 8;
+      const long long big = std::max({(long long)n * na * ld_n, (long long)n * ld_kmq,
                                       (long long)na * n * h->oz_geo.ldl});
       RS_CK(oz_make(h->ozGb, 1, n, n));
       RS_CK(oz_make(h->ozBig0, 1, 1, big));
@@ -1076,6 +1085,15 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
     int fl = 0;
     RS_CK(fetch(&fl, h->flags.as<int>() + 5, s));
     if (fl) return RSSRI_ERR_TIMEOUT;
+#ifdef RSSRI_CHECKS
+    int chk[4];
+    RS_CK(oz_check_fetch(chk));
+    if (chk[0]) {
+      std::fprintf(stderr, "rssri bounds check %d failed at oz_gemm.cu:%d, index %lld\n", chk[0],
+                   chk[1], ((long long)chk[3] << 32) | (unsigned)chk[2]);
+      return RSSRI_ERR_CUDA;
+    }
+#endif
   }
   h->block_ok = true;
   h->block_from_g = g_in != nullptr;

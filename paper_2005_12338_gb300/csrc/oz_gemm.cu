@@ -1,22 +1,22 @@
 // fp64-accurate products on the bf16 tensor cores (tcgen05, TMA, TMEM) by
 // error-free digit slicing; see oz_gemm.cuh for the number scheme.
 //
-// Kernel layout (one 128 x 128 output tile per CTA, 10 warps):
-//   warp 0 lane 0  TMA producer: per K step of 16, the five digit tiles of A
+// Kernel layout (one 128 x 128 output tile per CTA, 18 warps):
+//   warp 0 lane 0  TMA producer: per K step of 16, the six digit tiles of A
 //                  and of B (128 rows x 32 bytes each, 32-byte swizzle) into a
 //                  ring of shared-memory stages;
-//   warp 1 lane 0  MMA issuer: per K step, the 15 digit products p + q <= 4
+//   warp 1 lane 0  MMA issuer: per K step, the 21 digit products p + q <= 5
 //                  (tcgen05.mma kind::f16, M = N = 128, K = 16) into four fp32
 //                  accumulators in tensor memory, one per level p + q = 0, 1,
 //                  2 and one for p + q >= 3 (4 x 128 of the 512 columns);
-//   warps 2-9      drain: after every 256 terms of K (16 steps) they read the
+//   warps 2-17     drain: after every 256 terms of K (16 steps) they read the
 //                  four accumulators (tcgen05.ld) and add them exactly into
 //                  double-float running totals held in registers (each thread:
-//                  one row, 64 columns), then release the accumulators; at the
+//                  one row, 32 columns), then release the accumulators; at the
 //                  end they assemble fp64 from the running totals with integer
 //                  exponent arithmetic and one fp64 add per output.
 // Levels 0-2 are exact over 256 terms (< 2^24 grid units), so a chunk's sum
-// a0 + a1 + a2 is exact in two TwoSums; level >= 3 (< 2^-24 of the result)
+// a0 + a1 + a2 is exact in two TwoSums; level >= 3 (~2^-24 of the result)
 // and the running sum round at ~2^-48 relative.
 //
 // Every mbarrier wait is bounded; on expiry the kernel records an error code
@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -36,13 +37,32 @@ namespace {
 constexpr int BM = 128, BN = 128, KS = 16;   // tile rows, columns; K per step (32 bytes of bf16)
 constexpr int TILE = BM * KS * 2;            // bytes of one digit tile
 constexpr int STAGE = OZ_S * 2 * TILE;       // A and B digits of one K step
-constexpr int STAGES = 5;
+constexpr int STAGES = 4;
 constexpr int CHUNK = 16;                    // K steps between drains (256 terms)
-constexpr int EPI = 8;                       // drain warps
+constexpr int EPI = 16;                      // drain warps (4 per tensor-memory lane quarter)
+constexpr int DC = BN / 4;                   // accumulator columns per drain thread
 constexpr int THREADS = (2 + EPI) * 32;
 constexpr int TMEM_COLS = 512;               // 4 accumulators x 128 columns
 // (+8 KB slack beyond the last tile)
 constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + 8192;
+
+// Bounds checks (RSSRI_CHECKS builds): the first violation is recorded and
+// the access skipped; release builds compile them away.
+__device__ int g_check[4];
+__device__ long long g_check_ctx[12];  // context of the first violation (where recorded)
+#ifdef RSSRI_CHECKS
+__device__ __noinline__ void check_fail(int code, int line, long long idx) {
+  if (atomicCAS(&g_check[0], 0, code) == 0) {
+    g_check[1] = line;
+    g_check[2] = (int)(idx & 0xFFFFFFFF);
+    g_check[3] = (int)(idx >> 32);
+  }
+}
+#define OZ_IN(idx, cap, code) \
+  ((cap) <= 0 || ((idx) >= 0 && (idx) < (cap)) ? true : (check_fail((code), __LINE__, (idx)), false))
+#else
+#define OZ_IN(idx, cap, code) true
+#endif
 
 struct OzParams {
   CUtensorMap ta, tb;
@@ -57,6 +77,7 @@ struct OzParams {
   long long ldc, sC;
   int bk, nl16, jtiles;  // exchange geometry
   int *err;
+  long long ccap, efa_cap, efb_cap;  // bounds of C and the exponent arrays (checks)
 };
 
 // ------------------------------------------------------------ PTX helpers --
@@ -130,6 +151,11 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
           s_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t *r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -181,7 +207,7 @@ __device__ __forceinline__ int row_scale(int ef) { return max(ef, 1) - 1022; }
 
 // ------------------------------------------------------------- the GEMM ----
 template <int MODE>
-__global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams p) {
+__global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + STAGES * STAGE);
@@ -297,12 +323,12 @@ __global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams
     }
   } else {
     // drain warps
-    const int lq = warp & 3;         // tensor-memory lanes this warp may access
-    const int ch = (warp - 2) >> 2;  // column half of the tile
+    const int lq = warp & 3;            // tensor-memory lanes this warp may access
+    const int cq = (warp - 2) >> 2;     // column quarter of the tile
     const int row = lq * 32 + lane;
-    float hi[64], lo[64];
+    float hi[DC], lo[DC];
 #pragma unroll
-    for (int c = 0; c < 64; ++c) hi[c] = lo[c] = 0.f;
+    for (int c = 0; c < DC; ++c) hi[c] = lo[c] = 0.f;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       if (!bar_wait(accf, c & 1, p.err, 4) || (p.err && *(volatile int *)p.err)) {
@@ -310,17 +336,17 @@ __global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ch * 64);
+      const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * DC);
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 8) {
-        uint32_t r0[8], r1[8], r2[8], r3[8];
-        tmem_ld8(tl + c0, r0);
-        tmem_ld8(tl + 128 + c0, r1);
-        tmem_ld8(tl + 256 + c0, r2);
-        tmem_ld8(tl + 384 + c0, r3);
+      for (int c0 = 0; c0 < DC; c0 += 4) {
+        uint32_t r0[4], r1[4], r2[4], r3[4];
+        tmem_ld4(tl + c0, r0);
+        tmem_ld4(tl + 128 + c0, r1);
+        tmem_ld4(tl + 256 + c0, r2);
+        tmem_ld4(tl + 384 + c0, r3);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 4; ++u)
           fold(hi[c0 + u], lo[c0 + u], __uint_as_float(r0[u]), __uint_as_float(r1[u]),
                __uint_as_float(r2[u]), __uint_as_float(r3[u]));
       }
@@ -336,6 +362,7 @@ __global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams
       if (MODE == 0) {
         i = m0 + row;
         valid = i < p.M;
+        if (valid && !OZ_IN(zb * p.efa_bs + i, p.efa_cap, 10)) valid = 0;
         ea = valid ? row_scale(p.efa[zb * p.efa_bs + i]) : 0;
         dst = p.ksplit > 1 ? p.C + (long long)blockIdx.z * p.M * p.N + (long long)i * p.N
                            : p.C + zb * p.sC + (long long)i * p.ldc;
@@ -343,18 +370,22 @@ __global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams
         const int mt = rt / p.jtiles, jt = rt % p.jtiles;
         const int m = mt * 8 + (row >> 4), j = jt * 16 + (row & 15);
         valid = m < p.M && j < p.M;
-        ea = row_scale(p.efa[(long long)rt * BM + row]);
+        if (!OZ_IN((long long)rt * BM + row, p.efa_cap, 11)) valid = 0;
+        ea = valid ? row_scale(p.efa[(long long)rt * BM + row]) : 0;
         dst = p.C + ((long long)j * p.M + m) * p.N;
       }
       const int ncol = p.N;
       if (valid) {
-        const int j0 = n0 + ch * 64;
+        const int j0 = n0 + cq * DC;
         const bool neg = p.alpha == -1.0, plain = p.alpha == 1.0 || neg;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
+        for (int c = 0; c < DC; ++c) {
           const int j = j0 + c;
           if (j < ncol) {
-            const int eb = row_scale(p.efb[(MODE == 0 && !p.bshared ? zb * p.efb_bs : 0) + j]);
+            const long long ie = (MODE == 0 && !p.bshared ? zb * p.efb_bs : 0) + j;
+            if (!OZ_IN(ie, p.efb_cap, 12)) continue;
+            if (!OZ_IN((long long)(dst + j - p.C), p.ccap, 13)) continue;
+            const int eb = row_scale(p.efb[ie]);
             const int E = ea + eb - 14;
             double v = f32_scaled(hi[c], E) + f32_scaled(lo[c], E);
             if (neg) v = -v;
@@ -374,7 +405,8 @@ __global__ void __maxnreg__(200) oz_gemm_kernel(const __grid_constant__ OzParams
 
 // C[b][i][j] = sum over splits of work[(b ks + s)][i][j], in split order.
 __global__ void oz_reduce_kernel(const double *__restrict__ work, int ks, int M, int N, int batch,
-                                 double *__restrict__ C, long long ldc, long long sC) {
+                                 double *__restrict__ C, long long ldc, long long sC,
+                                 long long ccap) {
   const long long mn = (long long)M * N, tot = mn * batch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
@@ -382,7 +414,8 @@ __global__ void oz_reduce_kernel(const double *__restrict__ work, int ks, int M,
     const int i = (int)(r / N), j = (int)(r % N);
     double s = 0.0;
     for (int k = 0; k < ks; ++k) s += work[(b * ks + k) * mn + r];
-    C[b * sC + (long long)i * ldc + j] = s;
+    const long long o = b * sC + (long long)i * ldc + j;
+    if (OZ_IN(o, ccap, 20)) C[o] = s;
   }
 }
 
@@ -391,12 +424,21 @@ __global__ void oz_reduce_kernel(const double *__restrict__ work, int ks, int M,
 // contiguous index (rows when rs == 1, else columns) through shared memory.
 constexpr int SR = 32, SK = 64;
 
-__device__ __forceinline__ double view_at(const OzView &v, int b, long long r, long long kk,
-                                          long long K) {
-  if (kk >= K) return 0.0;
-  const long long k1 = kk / v.k2pad, k2 = kk - k1 * v.k2pad;
+// Element (b, r, kk) of the view, kk = k1 k2pad + k2 given as (k1, k2).
+__device__ __forceinline__ double view_at(const OzView &v, int b, long long r, long long k1,
+                                          long long k2) {
   if (k2 >= v.k2n) return 0.0;
   const long long o = b * v.bs + r * v.rs + k1 * v.cs1 + k2 * v.cs2;
+#ifdef RSSRI_CHECKS
+  if (v.xlen > 0 && (o < 0 || o >= v.xlen)) {
+    if (atomicCAS((int *)&g_check_ctx[11], 0, 1) == 0) {
+      g_check_ctx[0] = b; g_check_ctx[1] = r; g_check_ctx[2] = k1; g_check_ctx[3] = k2;
+      g_check_ctx[4] = v.bs; g_check_ctx[5] = v.rs; g_check_ctx[6] = v.cs1; g_check_ctx[7] = v.cs2;
+      g_check_ctx[8] = v.k2pad; g_check_ctx[9] = v.k2n; g_check_ctx[10] = v.xlen;
+    }
+  }
+#endif
+  if (!OZ_IN(o, v.xlen, 30)) return 0.0;
   if (v.x2) {
     const float2 f = v.x2[o];
     return (double)f.x + (double)f.y;
@@ -408,6 +450,7 @@ __device__ __forceinline__ double view_at(const OzView &v, int b, long long r, l
 __device__ __forceinline__ void load_tile(const OzView &v, int b, long long r0, long long k0,
                                           int rows, long long K, double (*s)[SK + 1]) {
   const bool rmaj = v.rs == 1;
+  const long long k1_0 = k0 / v.k2pad, k2_0 = k0 - k1_0 * v.k2pad;  // once per tile
   for (int idx = threadIdx.x; idx < SR * SK; idx += blockDim.x) {
     int r, k;
     if (rmaj) {
@@ -418,7 +461,16 @@ __device__ __forceinline__ void load_tile(const OzView &v, int b, long long r0, 
       r = idx / SK;
     }
     const long long rr = r0 + r;
-    s[r][k] = rr < rows ? view_at(v, b, rr, k0 + k, K) : 0.0;
+    double val = 0.0;
+    if (rr < rows && k0 + k < K) {
+      long long k1 = k1_0, k2 = k2_0 + k;
+      while (k2 >= v.k2pad) {
+        k2 -= v.k2pad;
+        ++k1;
+      }
+      val = view_at(v, b, rr, k1, k2);
+    }
+    s[r][k] = val;
   }
 }
 
@@ -448,8 +500,10 @@ __device__ __forceinline__ void digits_of(double x, int e, float *d) {
   const int efx = (int)((bits >> 52) & 0x7FF);
   unsigned long long M = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
   if (efx) M |= 1ull << 52;
-  // F = round(|x| 2^(39 - e)) = M 2^(max(efx,1) - 1075 + 39 - e); the shift is >= 14
-  const int sh = 1036 + e - max(efx, 1);
+  // F = round(|x| 2^(FB - e)) = M 2^(max(efx,1) - 1075 + FB - e), FB = 7 + 8 (S - 1)
+  // fraction bits; |x| < 2^e makes the shift >= 53 - FB
+  constexpr int FB = 7 + 8 * (OZ_S - 1);
+  const int sh = 1075 - FB + e - max(efx, 1);
   long long F = 0;
   if (sh < 64) F = (long long)((M + (1ull << (sh - 1))) >> sh);
   int dd[OZ_S];
@@ -462,8 +516,7 @@ __device__ __forceinline__ void digits_of(double x, int e, float *d) {
   }
   dd[0] = (int)F;
   const float sgn = bits < 0 ? -1.f : 1.f;
-  const float sc[5] = {1.f, 0.00390625f, 1.52587890625e-05f, 5.9604644775390625e-08f,
-                       2.3283064365386963e-10f};
+  const float sc[6] = {1.f, 0x1p-8f, 0x1p-16f, 0x1p-24f, 0x1p-32f, 0x1p-40f};
 #pragma unroll
   for (int p = 0; p < OZ_S; ++p) d[p] = sgn * (float)dd[p] * sc[p];
 }
@@ -485,6 +538,7 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
     float d[OZ_S];
     digits_of(s[r][k], e, d);
     const long long o = ((long long)b * rows + rr) * ld + kk;
+    if (!OZ_IN(o, plane, 31)) continue;
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) out[p * plane + o] = __float2bfloat16_rn(d[p]);
   }
@@ -493,7 +547,8 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
 // ---------------------------------------------------- exchange operand -----
 __global__ void oz_exch_gather_kernel(int n, int bk, int nl16, int jtiles, long long kx,
                                       const double *__restrict__ D, int P,
-                                      const int *__restrict__ pidx, double *__restrict__ xs) {
+                                      const int *__restrict__ pidx, double *__restrict__ xs,
+                                      long long xs_cap) {
   const int rt = blockIdx.y;
   const int mt = rt / jtiles, jt = rt % jtiles;
   const long long lw = (long long)nl16 * KS;
@@ -508,15 +563,16 @@ __global__ void oz_exch_gather_kernel(int n, int bk, int nl16, int jtiles, long 
     double v = 0.0;
     if (m < n && j < n && k >= 0 && k < n && l >= 0 && l < n) {
       const int a = pidx[m * n + k], c = pidx[l * n + j];
-      if (a >= 0 && c >= 0) v = D[(long long)a * P + c];
+      if (a >= 0 && c >= 0 && OZ_IN(a, P, 40) && OZ_IN(c, P, 41)) v = D[(long long)a * P + c];
     }
-    dst[e] = v;
+    if (OZ_IN((long long)rt * BM * kx + e, xs_cap, 42)) dst[e] = v;
   }
 }
 
-__global__ void oz_pair_index_kernel(const int *__restrict__ pij, int P, int *__restrict__ pidx) {
+__global__ void oz_pair_index_kernel(const int *__restrict__ pij, int P, int n,
+                                     int *__restrict__ pidx) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < P; a += gridDim.x * blockDim.x)
-    pidx[pij[a]] = a;
+    if (OZ_IN(pij[a], (long long)n * n, 50)) pidx[pij[a]] = a;
 }
 
 __global__ void oz_fold_kernel(const int *__restrict__ prow, const int *__restrict__ pcol,
@@ -527,7 +583,7 @@ __global__ void oz_fold_kernel(const int *__restrict__ prow, const int *__restri
        e += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(e / na), q = (int)(e % na);
     const long long o = ((long long)pcol[a] * n + prow[a]) * na + q;
-    U[o] += 2.0 * L[e];
+    if (OZ_IN(o, (long long)n * n * na, 51)) U[o] += 2.0 * L[e];
   }
 }
 
@@ -606,6 +662,21 @@ void plan(const OzGemm &g, int *ksplit, int *kst) {
 
 }  // namespace
 
+cudaError_t oz_check_fetch(int out[4]) {
+  RS_TRY(cudaMemcpyFromSymbol(out, g_check, 4 * sizeof(int)));
+#ifdef RSSRI_CHECKS
+  long long ctx[12];
+  RS_TRY(cudaMemcpyFromSymbol(ctx, g_check_ctx, sizeof(ctx)));
+  if (ctx[11])
+    fprintf(stderr,
+            "view read: b %lld r %lld k1 %lld k2 %lld | bs %lld rs %lld cs1 %lld cs2 %lld k2pad "
+            "%lld k2n %lld xlen %lld\n",
+            ctx[0], ctx[1], ctx[2], ctx[3], ctx[4], ctx[5], ctx[6], ctx[7], ctx[8], ctx[9], ctx[10]);
+#endif
+  const int zero[4] = {0, 0, 0, 0};
+  return cudaMemcpyToSymbol(g_check, zero, 4 * sizeof(int));
+}
+
 int oz_kernel_regs(int *max_threads) {
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, oz_gemm_kernel<0>) != cudaSuccess) return -1;
@@ -644,8 +715,8 @@ size_t oz_gemm_work(const OzGemm &g) {
 double oz_gemm_flops(const OzGemm &g) {
   int ks, kst;
   plan(g, &ks, &kst);
-  return 15.0 * 2.0 * BM * BN * KS * (double)kst * ks * ceil_div(g.M, BM) * ceil_div(g.N, BN) *
-         g.batch;
+  return OZ_PRODUCTS * 2.0 * BM * BN * KS * (double)kst * ks * ceil_div(g.M, BM) *
+         ceil_div(g.N, BN) * g.batch;
 }
 
 cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream_t s) {
@@ -677,6 +748,9 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   p.ldc = g.ldc;
   p.sC = g.sC;
   p.err = g.err;
+  p.ccap = ks > 1 ? (long long)ks * g.batch * g.M * g.N : g.ccap;
+  p.efa_cap = (long long)g.A.batch * g.A.rows;
+  p.efb_cap = (long long)g.B.batch * g.B.rows;
   RS_TRY(prepare());
   dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.batch * ks);
   oz_gemm_kernel<0><<<grid, THREADS, SMEM, s>>>(p);
@@ -685,7 +759,7 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   if (ks > 1) {
     const long long tot = (long long)g.batch * g.M * g.N;
     oz_reduce_kernel<<<(int)std::min<long long>((tot + 255) / 256, 152 * 8), 256, 0, s>>>(
-        work, ks, g.M, g.N, g.batch, g.C, g.ldc, g.sC);
+        work, ks, g.M, g.N, g.batch, g.C, g.ldc, g.sC, g.ccap);
     ++launch_counter();
     RS_TRY(cudaGetLastError());
   }
@@ -695,7 +769,7 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
 cudaError_t oz_pair_index(const int *pij, int P, int n, int *pidx, cudaStream_t s) {
   RS_TRY(cudaMemsetAsync(pidx, 0xFF, (size_t)n * n * sizeof(int), s));
   if (P <= 0) return cudaSuccess;
-  oz_pair_index_kernel<<<std::min(ceil_div(P, 256), 1024), 256, 0, s>>>(pij, P, pidx);
+  oz_pair_index_kernel<<<std::min(ceil_div(P, 256), 1024), 256, 0, s>>>(pij, P, n, pidx);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -727,21 +801,22 @@ OzExch oz_exch_geometry(int n, int na, int bk) {
 }
 
 double oz_exch_flops(const OzExch &x) {
-  return 15.0 * 2.0 * BM * (double)ceil_div(x.na, BN) * BN * x.kx * x.mtiles * x.jtiles;
+  return OZ_PRODUCTS * 2.0 * BM * (double)ceil_div(x.na, BN) * BN * x.kx * x.mtiles * x.jtiles;
 }
 
 cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *pidx, double *xs,
-                           cudaStream_t s) {
+                           long long xs_cap, cudaStream_t s) {
   const int tiles = x.mtiles * x.jtiles;
   if (tiles > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)std::min<long long>(ceil_div(BM * x.kx, 256), 64), tiles);
-  oz_exch_gather_kernel<<<grid, 256, 0, s>>>(x.n, x.bk, x.nl16, x.jtiles, x.kx, D, P, pidx, xs);
+  oz_exch_gather_kernel<<<grid, 256, 0, s>>>(x.n, x.bk, x.nl16, x.jtiles, x.kx, D, P, pidx, xs,
+                                             xs_cap);
   ++launch_counter();
   return cudaGetLastError();
 }
 
 cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
-                    double alpha, int *err, cudaStream_t s) {
+                    long long tcap, double alpha, int *err, cudaStream_t s) {
   if (!oz_available()) return cudaErrorNotSupported;
   const int tiles = x.mtiles * x.jtiles;
   if (X.batch != tiles || X.rows != BM || X.K != x.kx || At.rows != x.na ||
@@ -769,6 +844,9 @@ cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, doub
   p.nl16 = x.nl16;
   p.jtiles = x.jtiles;
   p.err = err;
+  p.ccap = tcap;
+  p.efa_cap = (long long)X.batch * X.rows;
+  p.efb_cap = (long long)At.batch * At.rows;
   RS_TRY(prepare());
   dim3 grid(ceil_div(x.na, BN), 1, tiles);
   oz_gemm_kernel<1><<<grid, THREADS, SMEM, s>>>(p);

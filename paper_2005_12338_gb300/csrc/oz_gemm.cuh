@@ -5,19 +5,21 @@
 // contractions of the deterministic block (Sec. III, Eq. 20 on v^L).
 //
 // Each row of an fp64 operand is scaled by a power of two 2^e with every
-// |x| < 2^e, rounded to a 39-bit fixed-point integer F, and written as five
-// balanced base-256 digits, F = sum_p d_p 256^(4-p) with |d_p| <= 128.  The
+// |x| < 2^e, rounded to a 47-bit fixed-point integer F, and written as six
+// balanced base-256 digits, F = sum_p d_p 256^(5-p) with |d_p| <= 128.  The
 // digits are stored in bf16 pre-scaled by 2^(-8p), so that
-//     x ~= 2^(e-7) sum_p D_p,   D_p = d_p 2^(-8p),   |x - that| <= 2^(e-40).
+//     x ~= 2^(e-7) sum_p D_p,   D_p = d_p 2^(-8p),   |x - that| <= 2^(e-48).
 // A product sum_k a_k b_k is then 2^(eA+eB-14) sum_{p,q} sum_k D^A_p D^B_q.
 // Every bf16 x bf16 product of digits is exact in fp32, and a level
 // p + q = L sums terms on the common grid 2^(-8L) with at most
 // (L+1) 2^14 grid units each; over 256 terms of K the levels L = 0, 1, 2
 // stay below 2^24 grid units, so the tensor core's fp32 accumulation of them
-// is exact.  Levels 3 and 4 (p + q <= 4 are kept: 15 digit products) share a
-// fourth accumulator whose rounding is ~2^-48 of the result.  After every 256
-// terms of K the four accumulators are added into double-float (fp32 pair)
-// running totals; the fp64 result is assembled once per output.
+// is exact.  Levels 3 to 5 (p + q <= 5 are kept: 21 digit products; the
+// dropped ones are below 2^-46 of the row maxima's product) share a fourth
+// accumulator, which is ~2^-24 of the result and rounds at ~2^-48 of it.
+// After every 256 terms of K the four accumulators are added into
+// double-float (fp32 pair) running totals; the fp64 result is assembled once
+// per output.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -26,7 +28,8 @@
 
 namespace rssri {
 
-constexpr int OZ_S = 5;  // digits per fp64 value
+constexpr int OZ_S = 6;  // digits per fp64 value
+constexpr int OZ_PRODUCTS = OZ_S * (OZ_S + 1) / 2;  // digit products kept (p + q < OZ_S)
 
 // Digits of an fp64 matrix, K-major: d[p][b][r][ld] (bf16, p < OZ_S), and the
 // biased fp64 exponent field of each row's largest magnitude, ef[b][r]
@@ -51,6 +54,7 @@ struct OzView {
   const float2 *x2 = nullptr;
   long long bs = 0, rs = 0, cs1 = 0, cs2 = 1;
   long long k2pad = 0, k2n = 0;
+  long long xlen = 0;  // elements of the source (bounds checks of RSSRI_CHECKS builds)
 };
 
 // Write the digits and row exponents of view v into out (rows x K per batch).
@@ -65,6 +69,7 @@ struct OzGemm {
   int M = 0, N = 0, batch = 1;
   double *C = nullptr;
   long long ldc = 0, sC = 0;
+  long long ccap = 0;  // elements of C (bounds checks of RSSRI_CHECKS builds)
   double alpha = 1.0;
   int *err = nullptr;  // device flag, set non-zero if a bounded wait gives up
 };
@@ -89,11 +94,11 @@ OzExch oz_exch_geometry(int n, int na, int bk);
 // fp64 left operand [tiles][128][kx] of the exchange contraction (tiles =
 // mtiles * jtiles), from D [P][P] and pidx; then sliced with oz_slice.
 cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *pidx,
-                           double *xs, cudaStream_t s);
+                           double *xs, long long xs_cap, cudaStream_t s);
 // T[(j*n + m)*na + q] = alpha * the contraction, fp64.  X: digits [tiles][128][kx];
 // At: digits [1][na][n*ldl] (k major, l minor).
 cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
-                    double alpha, int *err, cudaStream_t s);
+                    long long tcap, double alpha, int *err, cudaStream_t s);
 double oz_exch_flops(const OzExch &x);
 
 // pidx[i*n + j] = index of pair (i, j) among the P kept pairs (linear
@@ -105,6 +110,10 @@ cudaError_t oz_fold_direct(const int *prow, const int *pcol, const double *L, in
                            int na, double *U, cudaStream_t s);
 
 bool oz_available();
+// RSSRI_CHECKS builds: the first bounds violation any kernel of this file
+// recorded since the last call, as {code, line, index low, index high}
+// (code 0: none); the record is cleared.  Other builds return all zeros.
+cudaError_t oz_check_fetch(int out[4]);
 // Registers per thread of the product kernel and the most threads a launch of
 // it may have (diagnostics).
 int oz_kernel_regs(int *max_threads);

@@ -149,6 +149,20 @@ def test_parity_double_float_everywhere(B, case):
     h.close()
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_parity_sliced_block(B, case):
+    """The deterministic block on the tensor cores (RSSRI_DD_OZ: fp64 operands
+    split into bf16 digits, exact digit products) with the double-float chain
+    meets the fp64 bar of 1e-10."""
+    c = CASES[case]
+    s = synth.make_system(*c["sys"], input_seed=1)
+    ref = run_oracle(s, c["eps_prime"], c["eps"], c["n_s"], c["seed"])
+    h, got = run_gpu(B, s, c["eps_prime"], c["eps"], c["n_s"], c["seed"], dd_arith=B.RSSRI_DD_OZ,
+                     precision=B.RSSRI_PREC_DF64)
+    compare_all(h, got, ref, s)
+    h.close()
+
+
 def test_double_float_chain_pair_batches(B):
     s = synth.make_system(30, 12, 60, 3, input_seed=6)
     _, a = run_gpu(B, s, 0.02, 1e-2, 9, 4, dd_arith=1, precision=B.RSSRI_PREC_DF64)
@@ -247,11 +261,13 @@ def test_errors_are_reported(B):
 
 # ---------------------------------------------------- the N = 200 workload ---
 # Forms: (chain precision, deterministic-block arithmetic).  "plain" is IEEE
-# fp64 throughout; "df64" is the double-float form (chain and block), whose
+# fp64 throughout; "sliced" has the block's products on the tensor cores
+# (RSSRI_DD_OZ) and the double-float chain; "df64" is the double-float form
+# (chain and block), whose
 # N = 200 launches pick other tile geometries than the small cases (padded
 # 16x16 / 8x8 double-float tiles, the symmetric upper-tile Sigma_DD product,
 # N_aux = 600 split into five aux chunks in the exchange contraction).
-C2_FORMS = {"plain": (0, 0), "df64": (3, 1)}
+C2_FORMS = {"plain": (0, 0), "df64": (3, 1), "sliced": (3, 2)}
 
 
 @pytest.fixture(scope="module", params=sorted(C2_FORMS))
