@@ -2,15 +2,21 @@
 
 Workload: N = 200 basis functions, 100 occupied, N_aux = 600, 64 tau points,
 N_s = 300 sample pairs, eps = 1e-3, eps' = 0.02 (synthetic hydrogen-chain-like
-integrals).  One step is one pass of the whole path: V^{-1/2}, screening,
-[K]^L and its cut, the pair-space product, G(tau), the deterministic block,
-the Rademacher draws, R and R^L, the chain products for every (sample pair,
-tau) unit, the energy and the symmetrised output.  The metric is Sigma(tau)
-units per second, a unit being one (sample pair, tau point); inputs are
-resident in HBM when the timed region starts.  Every step draws a new seed.
-The timed form computes every product in double-float arithmetic (fp64
-accurate: within 1e-10 of the fp64 oracle); the IEEE-fp64 form and a
-reduced-precision tensor-core form are timed beside it for comparison.
+integrals).  One step is one pass of the whole path for a new seed:
+rssri_setup (V^{-1/2}, screening, [K]^L and its cut, the pair-space product,
+G(tau) and the deterministic block for every tau) and rssri_sigma (the
+Rademacher draws, R and R^L, the chain products for every (sample pair, tau)
+unit, the energy and the symmetrised output).  The metric is Sigma(tau) units
+per second, a unit being one (sample pair, tau point); inputs are resident in
+HBM when the timed region starts.
+
+The benchmark line times the plain form: every product in IEEE fp64.  Beside
+it (extra): the chosen form (the deterministic block's products as
+fp64-accurate sliced products on the bf16 tensor cores, the stochastic chain
+in bf16 on the tensor cores), its error against the plain form on the same
+draws, and the time of each form to reach a 1 mEh standard error of E_corr;
+the double-float form; the range-separated estimator against plain stochastic
+RI at the same N_s.
 
 Multi-GPU: one process per GPU (torchrun); every rank runs independent
 replicas with its own seeds, no collective on the data path (weak scaling).
@@ -37,14 +43,9 @@ sys.path.insert(0, ROOT)
 from paper_2005_12338_gb300 import replicas, synth  # noqa: E402
 
 WORKLOAD = "c2_n200"
-# fp64 ALU peak of the DFMA pipe: 152 SMs x 2 fp64 FMA/clock/SM x 2 flop x
-# 2070 MHz maximum SM clock.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# Double-float multiply-add (--dd df64, --precision df64): 12 fp32
-# instructions each (TwoProduct with 3 fma, TwoSum, error collection) on
-# 152 SMs x 128 fp32 lanes x 2070 MHz, counted as 2 fp64-equivalent flop.
-DF64_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# (chain precision, deterministic-block arithmetic) of the forms
+FORMS = {"plain": ("fp64", "fp64"), "chosen": ("bf16", "oz"), "df64": ("df64", "df64")}
 
 
 def parse():
@@ -54,17 +55,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
-    ap.add_argument("--precision", default="df64", choices=["df64", "bf16", "tf32", "fp64"],
-                    help="chain products: double-float on the fp32 pipes (fp64-accurate, the "
-                         "benchmark line), bf16 or tf32 tensor cores (reduced precision), or "
-                         "IEEE fp64 (plain)")
-    ap.add_argument("--reduced", default="bf16", choices=["bf16", "tf32", "none"],
-                    help="also time this reduced-precision tensor-core form and report its "
-                         "error against the IEEE fp64 form on the same draws")
-    ap.add_argument("--dd", default="df64", choices=["df64", "fp64"],
-                    help="exchange contraction of the deterministic block: double-float on "
-                         "the fp32 pipes (chosen) or IEEE fp64")
-    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--form", default="plain", choices=sorted(FORMS),
+                    help="the form on the benchmark line: plain (IEEE fp64 products), chosen "
+                         "(sliced fp64-accurate block on the tensor cores + bf16 chain) or df64 "
+                         "(double-float products)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="time only the form on the benchmark line")
     ap.add_argument("--eps", type=float, default=None,
                     help="override the K^L cut eps of the workload (e.g. the paper's 0.1)")
     ap.add_argument("--n-tau", type=int, default=None,
@@ -99,19 +95,6 @@ def measured_peaks():
             d = json.load(f)
         return d, "measured"
     return dict(FALLBACK_PEAKS), "fallback"
-
-
-def tensor_peak(peaks, precision):
-    """Dense tensor peak of the chain's operand type: the measured bf16 figure,
-    halved for tf32 (the nominal tf32 : bf16 ratio)."""
-    bf16 = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
-    return bf16 / 2.0 if precision == "tf32" else bf16
-
-
-def tensor_peak_source(peak_src, precision):
-    if precision == "tf32":
-        return "bf16 dense tensor peak x 1/2 (nominal tf32 ratio), " + peak_src
-    return "bf16 dense tensor peak, " + peak_src
 
 
 # --------------------------------------------------------------- clocks ----
@@ -281,14 +264,14 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------- our arm -----
-def traffic_for(key):
-    """Per-launch DRAM bytes of the dominant kernel (key: kernel class, with
-    "/df64" for the double-float deterministic block) from the committed ncu
-    summary, or None if absent or taken on a different kernel source."""
+def traffic_for(cls, form):
+    """Per-launch DRAM bytes of the dominant kernel class of a form from the
+    committed ncu summary (profiles/traffic.json, keyed "form/class"), or None
+    if absent or taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path)).get(key)
+    d = json.load(open(path)).get(f"{form}/{cls}")
     if not d:
         return None
     src = os.path.join(ROOT, "paper_2005_12338_gb300", "csrc", d["source"])
@@ -342,6 +325,40 @@ def many_systems(args, binding, torch, prec, dd):
             **res, "speedup": res["one_by_one"]["s_per_pass"] / res["batched"]["s_per_pass"]}
 
 
+def pipe_peaks(binding, device):
+    """Measured fp64 and fp32 pipe peaks of this GPU, TFLOP/s: the library's
+    DFMA, DMMA and FFMA micro-benchmarks, and (fp64, for reference only: not
+    on the path) the library DGEMM behind torch's float64 matmul, 4096^3."""
+    import torch
+    out = {}
+    for name, which in (("dfma", binding.RSSRI_PEAK_DFMA), ("dmma", binding.RSSRI_PEAK_DMMA),
+                        ("ffma", binding.RSSRI_PEAK_FFMA)):
+        try:
+            out[name] = binding.peak_measure(which, device)[0]
+        except Exception:
+            out[name] = None
+    try:
+        a = torch.randn(4096, 4096, dtype=torch.float64, device=f"cuda:{device}")
+        b = torch.randn(4096, 4096, dtype=torch.float64, device=f"cuda:{device}")
+        for _ in range(2):
+            torch.matmul(a, b)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 5
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        out["dgemm_library"] = 2.0 * 4096 ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        del a, b
+    except Exception:
+        out["dgemm_library"] = None
+    out["fp64"] = max(v for k, v in out.items() if k != "ffma" and v)
+    return out
+
+
 def our_arm(args):
     import torch
     import torch.distributed as dist
@@ -359,162 +376,173 @@ def our_arm(args):
         cfg["n_tau"] = args.n_tau
     s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
     n, nt, ns = s.n, s.n_tau, cfg["n_s"]
+    units_step = ns * nt
     host = [s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w]
     dev = [torch.from_numpy(a).to(f"cuda:{local}") for a in host]
     sig = torch.empty((nt, n, n), dtype=torch.float64, device=f"cuda:{local}")
     ep = torch.empty(ns, dtype=torch.float64, device=f"cuda:{local}")
     h = binding.Handle(local)
     stream = torch.cuda.current_stream(local)
-
     prec_code = {"bf16": binding.RSSRI_PREC_BF16, "tf32": binding.RSSRI_PREC_TF32,
                  "fp64": binding.RSSRI_PREC_FP64, "df64": binding.RSSRI_PREC_DF64}
-    prec = prec_code[args.precision]
-    tensor_chain = args.precision in ("bf16", "tf32")
-    dd = binding.RSSRI_DD_DF64 if args.dd == "df64" else binding.RSSRI_DD_FP64
+    dd_code = {"fp64": binding.RSSRI_DD_FP64, "df64": binding.RSSRI_DD_DF64,
+               "oz": binding.RSSRI_DD_OZ}
 
-    def step(seed, profile=0, precision=prec, dd_arith=dd, estimator=binding.RSSRI_EST_CV,
-             pair_batch=0):
-        o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, profile=profile,
-                                   precision=precision, dd_arith=dd_arith, estimator=estimator,
-                                   pair_batch=pair_batch)
+    def opts(form, seed, profile=0, estimator=binding.RSSRI_EST_CV, **kw):
+        prec, dd = FORMS[form]
+        return binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, profile=profile,
+                                      precision=prec_code[prec], dd_arith=dd_code[dd],
+                                      estimator=estimator, **kw)
+
+    def step(form, seed, profile=0, **kw):
+        o = opts(form, seed, profile, **kw)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
         return h.sigma(o, sig, ep)
 
+    def timed(form, seeds, profile=1, clock=None):
+        """Steps over the seeds between CUDA events on the stream; returns
+        (ms, per-step (e, se, fixed ms, sampling ms), summed stats)."""
+        prof = {"ms": np.zeros(8), "gf": np.zeros(8), "tgf": np.zeros(8),
+                "l": np.zeros(8, dtype=np.int64), "launches": 0}
+        res = []
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for sd in seeds:
+            e, se, st = step(form, sd, profile=profile)
+            res.append((e, se, st["t_setup_ms"] + st["t_green_dd_ms"], st["t_sample_ms"]))
+            prof["ms"] += st["prof_ms"]
+            prof["gf"] += st["prof_gflop"]
+            prof["tgf"] += st["prof_tensor_gflop"]
+            prof["l"] += np.array(st["prof_launches"], dtype=np.int64)
+            prof["launches"] += st["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res, prof
+
+    form = args.form
+    # ---- the benchmark line
     for k in range(args.warmup):
-        step(replicas.rank_seed(rank, 900_000 + k))
+        step(form, replicas.rank_seed(rank, 900_000 + k))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    prof_ms = np.zeros(8)
-    prof_gf = np.zeros(8)
-    prof_l = np.zeros(8, dtype=np.int64)
-    launches = 0
-    results = []
+    seeds = [replicas.rank_seed(rank, k) for k in range(args.steps)]
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(args.steps):
-            e, se, st = step(replicas.rank_seed(rank, k), profile=1)
-            results.append((e, se, st["t_setup_ms"] + st["t_green_dd_ms"], st["t_sample_ms"]))
-            if k == 0:
-                sig_first = sig.clone()
-            prof_ms += st["prof_ms"]
-            prof_gf += st["prof_gflop"]
-            prof_l += np.array(st["prof_launches"], dtype=np.int64)
-            launches += st["kernel_launches"]
-        e1.record(stream)
+        ms_line, results, prof = timed(form, seeds[:1])
+        sig_first = sig.clone()
+        if args.steps > 1:
+            ms_rest, res_rest, prof_rest = timed(form, seeds[1:])
+            ms_line += ms_rest
+            results += res_rest
+            for key in ("ms", "gf", "tgf", "l"):
+                prof[key] = prof[key] + prof_rest[key]
+            prof["launches"] += prof_rest["launches"]
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     clocks = clk.summary()
-    ms_max = replicas.max_over_ranks(e0.elapsed_time(e1), device=f"cuda:{local}")
-    units = ns * nt * args.steps * world
-    value = replicas.job_throughput(ns * nt, args.steps, world, ms_max / 1e3)
+    ms_max = replicas.max_over_ranks(ms_line, device=f"cuda:{local}")
+    value = replicas.job_throughput(units_step, args.steps, world, ms_max / 1e3)
+    forms = {form: {"chain": FORMS[form][0], "block": FORMS[form][1],
+                    "units_per_s": units_step * args.steps / (ms_line / 1e3),
+                    "ms_per_step": ms_line / args.steps,
+                    "fixed_ms_per_step": float(np.mean([r[2] for r in results])),
+                    "sampling_ms_per_step": float(np.mean([r[3] for r in results])),
+                    "time_to_1mEh": time_to_target(results, ns, 1e-3)}}
+    profs = {form: prof}
 
-    # the plain fp64 form on the same seed: throughput and the error of the chosen form
-    compare = None
-    # (on the largest workloads the fp64 chain takes its pairs 100 at a time to
-    # bound its scratch; the sums are the same up to rounding order)
-    plain = dict(precision=binding.RSSRI_PREC_FP64, dd_arith=binding.RSSRI_DD_FP64,
-                 pair_batch=100 if n >= 500 else 0)
-    sig64 = None
-    if (tensor_chain or args.dd == "df64" or args.precision == "df64") and \
-            not args.no_fp64_compare:
-        step(replicas.rank_seed(rank, 990_001), **plain)  # tunes the fp64 chain shapes
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        e64, se64, st64 = step(replicas.rank_seed(rank, 0), profile=1, **plain)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        sdd = torch.from_numpy(h.export("SIGMA_DD").reshape(nt, n, n)).to(sig.device)
-        st_ref = sig - 0.5 * (sdd + sdd.transpose(1, 2))
-        err_sigma = float(torch.linalg.norm(sig_first - sig) / torch.linalg.norm(sig))
-        err_st = float(torch.linalg.norm(sig_first - sig) / torch.linalg.norm(st_ref))
-        sig64, st_ref64 = sig.clone(), st_ref.clone()
-        res64 = [(e64, se64, st64["t_setup_ms"] + st64["t_green_dd_ms"], st64["t_sample_ms"])]
-        compare = {"plain_fp64_units_per_s": ns * nt / (ms64 / 1e3),
-                   "plain_fp64_ms_per_step": ms64,
-                   "plain_fp64_sampling_ms_per_step": st64["t_sample_ms"],
-                   "chosen_sampling_ms_per_step": float(np.mean([r[3] for r in results])),
-                   "sampling_speedup": st64["t_sample_ms"] / float(np.mean([r[3] for r in results])),
-                   "chosen_vs_fp64_same_seed": {
-                       "sigma_rel_fro": err_sigma,
-                       "sigma_stochastic_part_rel_fro": err_st,
-                       "e_corr_abs": abs(results[0][0] - e64),
-                       "e_corr_rel": abs(results[0][0] - e64) / abs(e64),
-                       "e_stderr": se64},
-                   "time_to_1mEh_plain_fp64_s": time_to_target(res64, ns, 1e-3)}
-
-    # the reduced-precision tensor-core form: throughput, and its error against
-    # the IEEE fp64 form on the same draws
-    reduced = None
-    if args.reduced != "none" and not tensor_chain and sig64 is not None:
-        rp = prec_code[args.reduced]
-        er, ser, _ = step(replicas.rank_seed(rank, 0), precision=rp)  # graph capture + error
-        torch.cuda.synchronize()
-        d = sig - sig64
-        err = {"sigma_rel_fro": float(torch.linalg.norm(d) / torch.linalg.norm(sig64)),
-               "sigma_stochastic_part_rel_fro": float(torch.linalg.norm(d) /
-                                                      torch.linalg.norm(st_ref64)),
-               "e_corr_abs": abs(er - e64), "e_corr_rel": abs(er - e64) / abs(e64),
-               "e_stderr": se64}
-        step(replicas.rank_seed(rank, 990_002), precision=rp)
-        torch.cuda.synchronize()
-        r0 = torch.cuda.Event(enable_timing=True)
-        r1 = torch.cuda.Event(enable_timing=True)
-        rres = []
-        r0.record(stream)
-        for k in range(args.steps):
-            e_, se_, st_ = step(replicas.rank_seed(rank, k), precision=rp)
-            rres.append((e_, se_, st_["t_setup_ms"] + st_["t_green_dd_ms"], st_["t_sample_ms"]))
-        r1.record(stream)
-        torch.cuda.synchronize()
-        rms = r0.elapsed_time(r1) / args.steps
-        reduced = {"precision": args.reduced, "units_per_s": ns * nt / (rms / 1e3),
-                   "ms_per_step": rms,
-                   "sampling_ms_per_step": float(np.mean([r[3] for r in rres])),
-                   "vs_fp64_same_seed": err,
-                   "time_to_1mEh_s": time_to_target(rres, ns, 1e-3)}
+    # ---- the other forms on the same first seed: throughput and error against this one
+    if not args.no_compare:
+        base = sig_first
+        base_e = results[0][0]
+        for other in [f for f in ("chosen", "plain", "df64") if f != form]:
+            k_other = args.steps if other == "chosen" else 1
+            for k in range(min(args.warmup, 2)):
+                step(other, replicas.rank_seed(rank, 990_000 + k))
+            ms_o, res_o, prof_o = timed(other, seeds[:k_other])
+            if k_other > 1:
+                step(other, seeds[0])  # the output of the first seed, for the comparison
+            sig_o = sig.clone()
+            forms[other] = {"chain": FORMS[other][0], "block": FORMS[other][1],
+                            "units_per_s": units_step * k_other / (ms_o / 1e3),
+                            "ms_per_step": ms_o / k_other,
+                            "steps_timed": k_other,
+                            "fixed_ms_per_step": float(np.mean([r[2] for r in res_o])),
+                            "sampling_ms_per_step": float(np.mean([r[3] for r in res_o])),
+                            "time_to_1mEh": time_to_target(res_o, ns, 1e-3)}
+            profs[other] = prof_o
+            if other == "plain" or form == "plain":
+                ref_sig = sig_o if other == "plain" else base
+                ref_e = res_o[0][0] if other == "plain" else base_e
+                got_sig = base if other == "plain" else sig_o
+                got_e = base_e if other == "plain" else res_o[0][0]
+                # the stochastic remainder of the plain form's estimate on these draws
+                h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=opts("plain", seeds[0]))
+                sdd = torch.from_numpy(h.export("SIGMA_DD").reshape(nt, n, n)).to(sig.device)
+                rem = ref_sig - 0.5 * (sdd + sdd.transpose(1, 2))
+                d = got_sig - ref_sig
+                entry = forms[form if other == "plain" else other]
+                entry["vs_plain_same_draws"] = {
+                    "sigma_rel_fro": float(torch.linalg.norm(d) / torch.linalg.norm(ref_sig)),
+                    "sigma_stochastic_part_rel_fro": float(torch.linalg.norm(d) /
+                                                           torch.linalg.norm(rem)),
+                    "e_corr_abs": abs(got_e - ref_e), "e_corr_rel": abs(got_e - ref_e) / abs(ref_e),
+                    "e_stderr": results[0][1]}
+    t_plain = forms.get("plain", {}).get("time_to_1mEh")
+    t_chosen = forms.get("chosen", {}).get("time_to_1mEh")
+    chosen_vs_plain = None
+    if t_plain and t_chosen:
+        chosen_vs_plain = {"time_to_1mEh_plain_s": t_plain["seconds"],
+                           "time_to_1mEh_chosen_s": t_chosen["seconds"],
+                           "speedup": t_plain["seconds"] / t_chosen["seconds"],
+                           "sampling_only_speedup": t_plain["sampling_only_s"] /
+                           max(t_chosen["sampling_only_s"], 1e-12),
+                           "throughput_ratio": forms["chosen"]["units_per_s"] /
+                           forms["plain"]["units_per_s"]}
 
     # Sec. IV: the range-separated estimator against plain stochastic RI at the
-    # same number of sample pairs and the same seed
-    e_sri, se_sri, _ = step(replicas.rank_seed(rank, 0), estimator=binding.RSSRI_EST_SRI)
-    rs_vs_sri = {"e_corr_rs": results[0][0], "stderr_rs": results[0][1], "e_corr_sri": e_sri,
-                 "stderr_sri": se_sri, "stderr_ratio_sri_over_rs": se_sri / results[0][1],
-                 "agree_within_3_sigma": abs(e_sri - results[0][0]) <
-                 3 * (se_sri ** 2 + results[0][1] ** 2) ** 0.5}
+    # same number of sample pairs and the same seed (chosen form)
+    rs_vs_sri = None
+    if not args.no_compare:
+        e_rs, se_rs, _ = step("chosen", seeds[0])
+        e_sri, se_sri, _ = step("chosen", seeds[0], estimator=binding.RSSRI_EST_SRI)
+        rs_vs_sri = {"e_corr_rs": e_rs, "stderr_rs": se_rs, "e_corr_sri": e_sri,
+                     "stderr_sri": se_sri, "stderr_ratio_sri_over_rs": se_sri / se_rs,
+                     "agree_within_3_sigma": abs(e_sri - e_rs) < 3 * (se_sri ** 2 + se_rs ** 2) ** 0.5}
 
     # learned control variate (fp64 chain): train on an independent run, then
     # estimate with it on the first timed seed, next to the plain estimate
     cv_report = None
     if args.cv:
-        # the control variate needs F and F^L separately: fp64 or double-float chain
-        cvp = prec if args.precision in ("fp64", "df64") else binding.RSSRI_PREC_FP64
         tr = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 777),
-                                    dd_arith=dd, precision=cvp)
+                                    dd_arith=binding.RSSRI_DD_DF64,
+                                    precision=binding.RSSRI_PREC_DF64)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=tr)
         c0 = time.perf_counter()
         lb, la = h.cv_train(tr, synth.mlp_init(0), 400, 4096, 1e-3)
         t_train = time.perf_counter() - c0
-        ev = dict(precision=cvp, dd_arith=dd)
-        e_cv, se_cv, st_cv = step(replicas.rank_seed(rank, 0), **ev,
-                                  estimator=binding.RSSRI_EST_CV)
-        o_cv = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 0),
-                                      dd_arith=dd, cv=1, precision=cvp)
-        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o_cv)
-        e_l, se_l, st_l = h.sigma(o_cv, sig, ep)
+        o_p = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seeds[0],
+                                     dd_arith=binding.RSSRI_DD_DF64,
+                                     precision=binding.RSSRI_PREC_DF64)
+        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o_p)
+        e_cv, se_cv, _ = h.sigma(o_p, sig, ep)
+        o_cv = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seeds[0],
+                                      dd_arith=binding.RSSRI_DD_DF64, cv=1,
+                                      precision=binding.RSSRI_PREC_DF64)
+        e_l, se_l, _ = h.sigma(o_cv, sig, ep)
         cv_report = {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
                      "e_corr_plain": e_cv, "stderr_plain": se_cv, "e_corr_learned": e_l,
                      "stderr_learned": se_l, "stderr_ratio_plain_over_learned": se_cv / se_l}
 
-    many_report = many_systems(args, binding, torch, prec, dd) if args.many > 0 else None
+    many_report = None
+    if args.many > 0:
+        pr, dd = FORMS["chosen"]
+        many_report = many_systems(args, binding, torch, prec_code[pr], dd_code[dd])
 
     # the literal reading of Eq. 25 on the same draws as the first timed step
     literal_report = None
@@ -522,9 +550,7 @@ def our_arm(args):
         l0 = torch.cuda.Event(enable_timing=True)
         l1 = torch.cuda.Event(enable_timing=True)
         l0.record(stream)
-        e_lit, se_lit, st_lit = step(replicas.rank_seed(rank, 0),
-                                     precision=binding.RSSRI_PREC_FP64,
-                                     estimator=binding.RSSRI_EST_LITERAL)
+        e_lit, se_lit, st_lit = step("plain", seeds[0], estimator=binding.RSSRI_EST_LITERAL)
         l1.record(stream)
         torch.cuda.synchronize()
         literal_report = {"e_corr_literal": e_lit, "stderr_literal": se_lit,
@@ -542,20 +568,21 @@ def our_arm(args):
         hh = binding.Handle(local)
 
         def step_host(seed):
-            o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seed, precision=prec,
-                                       dd_arith=dd)
+            o = opts(form, seed)
             hh.setup(*pinned, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
             return hh.sigma(o, sig_h, ep_h)
         step_host(replicas.rank_seed(rank, 990_000))
+        k_e2e = min(args.steps, 3)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for k in range(args.steps):
-            step_host(replicas.rank_seed(rank, k))
+        for k in range(k_e2e):
+            step_host(seeds[k])
         el = replicas.max_over_ranks(time.perf_counter() - t0, device=f"cuda:{local}")
-        e2e = {"value": units / el, "unit": "units/s",
+        e2e = {"value": units_step * k_e2e * world / el, "unit": "units/s",
                "h2d_bytes_per_step": int(sum(a.nbytes for a in host)),
-               "d2h_bytes_per_step": int(sig_h.nbytes + ep_h.nbytes + 4 * 8)}
+               "d2h_bytes_per_step": int(sig_h.nbytes + ep_h.nbytes + 4 * 8),
+               "steps": k_e2e}
         hh.close()
 
     if rank != 0:
@@ -564,66 +591,81 @@ def our_arm(args):
             dist.destroy_process_group()
         return
     peaks, peak_src = measured_peaks()
-    dom = int(np.argmax(prof_ms))
-    name = binding.PROF_CLASSES[dom]
-    per_launch_gf = prof_gf[dom] / max(prof_l[dom], 1)
-    achieved = prof_gf[dom] / (prof_ms[dom] / 1e3) / 1e3  # TFLOP/s
-    df64_class = ((name in ("dd_spmm", "dd_gemm") and args.dd == "df64") or
-                  (name in ("chain_gemm", "factor_gemm", "setup_gemm") and
-                   args.precision == "df64"))
-    if df64_class:
-        peak = DF64_PEAK_TFLOPS
-        psrc = ("derived: 152 SMs x 128 fp32 lanes x 2070 MHz / 12 fp32 instructions per "
-                "double-float multiply-add x 2 flop (fp64-equivalent)")
-    elif name == "chain_gemm" and tensor_chain:
-        peak = tensor_peak(peaks, args.precision)
-        psrc = tensor_peak_source(peak_src, args.precision)
-    else:
-        peak = FP64_PEAK_TFLOPS
-        psrc = "derived: 152 SMs x 2 fp64 FMA/clk/SM x 2 flop x 2070 MHz (fp64 DFMA pipe)"
-    roofline = {"bound": "tensor" if (name == "chain_gemm" and tensor_chain) else "alu",
-                "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_for(name + ("/df64" if name in ("dd_spmm", "dd_gemm") and
-                                               args.dd == "df64" else "")),
-                "peak_source": psrc + "; HBM/bf16 peaks " + peak_src,
-                "gflop_per_launch": per_launch_gf, "launches": int(prof_l[dom]),
-                "share_of_step": float(prof_ms[dom] / max(prof_ms.sum(), 1e-9))}
-    tensor = None
-    if tensor_chain:
-        tpk = tensor_peak(peaks, args.precision)
-        tf = prof_gf[0] / (prof_ms[0] / 1e3) / 1e3
-        tensor = {"kernel": f"chain_gemm (tcgen05 {args.precision})", "bound": "tensor",
-                  "achieved": tf, "peak": tpk, "unit": "TFLOP/s", "frac": tf / tpk,
-                  "peak_source": tensor_peak_source(peak_src, args.precision)}
-    classes = {binding.PROF_CLASSES[c]: {"ms_per_step": prof_ms[c] / args.steps,
-                                         "gflop_per_step": prof_gf[c] / args.steps,
-                                         "launches_per_step": int(prof_l[c]) // args.steps,
-                                         "tflops": (prof_gf[c] / (prof_ms[c] / 1e3) / 1e3
-                                                    if prof_ms[c] > 0 else None)}
-               for c in range(len(binding.PROF_CLASSES))}
+    pipes = pipe_peaks(binding, local)
+    bf16_peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+
+    def classes_of(pr, steps_):
+        return {binding.PROF_CLASSES[c]: {
+            "ms_per_step": pr["ms"][c] / steps_, "gflop_per_step": pr["gf"][c] / steps_,
+            "tensor_gflop_per_step": pr["tgf"][c] / steps_,
+            "launches_per_step": int(pr["l"][c]) // steps_,
+            "tflops_fp64_equivalent": (pr["gf"][c] / (pr["ms"][c] / 1e3) / 1e3
+                                       if pr["ms"][c] > 0 else None),
+            "tensor_tflops": (pr["tgf"][c] / (pr["ms"][c] / 1e3) / 1e3
+                              if pr["ms"][c] > 0 and pr["tgf"][c] > 0 else None)}
+            for c in range(len(binding.PROF_CLASSES))}
+
+    for f in forms:
+        forms[f]["classes"] = classes_of(profs[f], forms[f].get("steps_timed", args.steps))
+
+    def roofline_of(f, pr):
+        dom = int(np.argmax(pr["ms"]))
+        name = binding.PROF_CLASSES[dom]
+        chain, block = FORMS[f]
+        tensor = pr["tgf"][dom] > 0
+        if tensor:
+            achieved = pr["tgf"][dom] / (pr["ms"][dom] / 1e3) / 1e3
+            peak, unit = (bf16_peak / 2 if chain == "tf32" and name == "chain_gemm"
+                          else bf16_peak), "TFLOP/s"
+            psrc = "bf16 dense tensor peak, " + peak_src
+            bound = "tensor"
+            work = "tensor flops issued (digit products over the padded tiles)"
+        else:
+            achieved = pr["gf"][dom] / (pr["ms"][dom] / 1e3) / 1e3
+            df = (block == "df64" and name in ("dd_spmm", "dd_gemm")) or \
+                 (chain == "df64" and name == "chain_gemm")
+            peak = pipes["ffma"] if df else pipes["fp64"]
+            psrc = ("measured fp32 FFMA pipe (double-float: each multiply-add is about a "
+                    "dozen fp32 instructions; the fraction is fp64-equivalent flops over the "
+                    "fp32 rate)" if df else
+                    "measured fp64 pipe: best of the DFMA and DMMA micro-benchmarks "
+                    "(rssri_peak_measure) and the library DGEMM (torch float64 matmul, "
+                    "4096^3)")
+            bound, unit = "alu", "TFLOP/s"
+            work = "algorithmic fp64 flops (2 N_aux P^2 per exchange contraction, 2mnk per product)"
+        launches = int(pr["l"][dom])
+        return {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak if peak else None,
+                "traffic": traffic_for(name, f),
+                "peak_source": psrc, "work": work,
+                "gflop_per_launch": (pr["tgf"][dom] if tensor else pr["gf"][dom]) /
+                max(launches, 1),
+                "launches": launches,
+                "share_of_step": float(pr["ms"][dom] / max(pr["ms"].sum(), 1e-9))}
+
+    roofline = roofline_of(form, prof)
+    other_rooflines = {f: roofline_of(f, profs[f]) for f in forms if f != form}
     line = {"metric": "Sigma(tau) units/s (unit = one sample pair x one tau point)",
             "value": value, "unit": "units/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "+".join(([args.precision] if tensor_chain else []) +
-                              (["df64"] if "df64" in (args.precision, args.dd) else []) +
-                              ["f64"]), "data": "synthetic",
+            "dtype": {"plain": "f64", "chosen": "bf16+f64", "df64": "df64"}[form],
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: N={n} n_occ={s.n_occ} N_aux={s.n_aux} "
                                    f"N_tau={nt} N_s={ns} eps={cfg['eps']} "
                                    f"eps'={cfg['eps_prime']}, whole path per step",
-                       "chain_precision": args.precision,
-                       "dd_exchange_arith": args.dd,
+                       "form": form, "chain_precision": FORMS[form][0],
+                       "block_arith": FORMS[form][1],
                        "l2": "inputs larger than L2 (3-index integrals 192 MB); steps of seconds",
                        "parallelism": f"replicas x{world} (independent seeds, no collective)"},
-            "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+            "roofline": roofline, "clocks": clocks, "gpu_launches": int(prof["launches"]),
             "e2e": e2e,
             "extra": {"e_corr_per_step": [r[0] for r in results],
                       "e_stderr_per_step": [r[1] for r in results],
-                      "time_to_1mEh_s": time_to_target(results, ns, 1e-3),
-                      "classes": classes, "tensor_roofline": tensor,
-                      "chosen_vs_plain_fp64": compare, "rs_vs_sri_same_n_s": rs_vs_sri,
-                      "reduced_precision_form": reduced,
+                      "forms": forms, "chosen_vs_plain_fp64": chosen_vs_plain,
+                      "rooflines_other_forms": other_rooflines,
+                      "measured_pipe_peaks_tflops": pipes,
+                      "rs_vs_sri_same_n_s": rs_vs_sri,
                       "learned_control_variate": cv_report,
                       "literal_estimator": literal_report,
                       "many_systems": many_report}}

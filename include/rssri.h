@@ -59,7 +59,11 @@ typedef enum {
   RSSRI_ERR_CUDA = -5,            /* a CUDA runtime call failed; handle is unusable    */
   RSSRI_ERR_TIMEOUT = -6,         /* a bounded device-side wait expired                */
   RSSRI_ERR_NOT_READY = -7,       /* rssri_sigma before a successful rssri_setup       */
-  RSSRI_ERR_NONFINITE = -8        /* an input or result is NaN or infinite             */
+  RSSRI_ERR_NONFINITE = -8,       /* an input or result is NaN or infinite             */
+  RSSRI_ERR_RANGE = -9            /* a double-float input (RSSRI_PREC_DF64 or
+                                     RSSRI_DD_DF64) has its largest magnitude outside
+                                     [2^-40, 2^40], where fp32 pairs lose precision;
+                                     use IEEE fp64 or RSSRI_DD_OZ instead           */
 } rssri_status;
 
 /* Where the arrays of a call live. */
@@ -98,7 +102,14 @@ enum { RSSRI_EST_CV = 0, RSSRI_EST_SRI = 1, RSSRI_EST_LITERAL = 2 };
  *   the fp32 pipes (each fp64 value as a pair of floats, error-free products
  *   and sums, ~1e-13 relative): fp64-accurate, within the same 1e-10 of the
  *   fp64 form, and several times faster on GPUs whose fp64 rate is a small
- *   fraction of their fp32 rate. */
+ *   fraction of their fp32 rate.  A pair has fp32's exponent range: every
+ *   input matrix converted to pairs ((ij|A), the metric's Newton-Schulz
+ *   iterates, [K]^L and v^L, the sign vectors and factors, and G and
+ *   G(beta - tau) per tau point) must have its largest magnitude in
+ *   [2^-40, 2^40], else the call returns RSSRI_ERR_RANGE.  Intermediates of
+ *   the block (Gamma, T) are not checked: they are products of checked
+ *   inputs and, for G with entries far below 2^-40 at some tau, lose
+ *   precision without notice; IEEE fp64 and RSSRI_DD_OZ keep fp64's range. */
 enum { RSSRI_PREC_FP64 = 0, RSSRI_PREC_BF16 = 1, RSSRI_PREC_TF32 = 2, RSSRI_PREC_DF64 = 3 };
 
 typedef struct rssri_handle rssri_handle;
@@ -157,8 +168,9 @@ typedef struct {
  *              stream (rssri_stats.prof_*); 0: off.
  *   cv         1: weight the large-part control variate element-wise by the
  *              coefficients c_ij(tau) of the network trained by
- *              rssri_cv_train (fp64 or double-float chain and RSSRI_EST_CV
- *              only); 0: c = 1.
+ *              rssri_cv_train (RSSRI_EST_CV only; with the tensor-core
+ *              chains, F(R^L, R'^L) of every pair is formed by one more
+ *              product on the tensor cores); 0: c = 1.
  *   dd_arith   arithmetic of the deterministic block (its products and
  *              exchange contraction): RSSRI_DD_FP64 (IEEE fp64 FMAs),
  *              RSSRI_DD_DF64 (double-float: each fp64 value as a pair of
@@ -167,10 +179,12 @@ typedef struct {
  *              1e-38 to 3e38, or lose their relative precision), or
  *              RSSRI_DD_OZ (fp64-accurate sliced products on the bf16 tensor
  *              cores: each row of an fp64 operand is scaled by a power of two
- *              and split into five 8-bit digits, every digit product and the
+ *              and split into six 8-bit digits, every digit product and the
  *              accumulation of the leading levels are exact, ~1e-12 of
  *              sum |a||b| per dot product, with fp64's exponent range; the
- *              segmented product K^Q G stays double-float).  RSSRI_DD_OZ
+ *              segmented product K^Q G runs in double-float on G(tau)
+ *              normalised by a power of two per tau point and rescaled
+ *              exactly, the block being homogeneous of degree 2 in G).  RSSRI_DD_OZ
  *              needs a GPU with tcgen05 (sm_100 family); its R, R^L and
  *              v^L are formed as for RSSRI_DD_DF64.
  *              The value given to rssri_setup sets how v^L and
@@ -189,6 +203,13 @@ typedef struct {
   int32_t profile;
   int32_t dd_arith;
   int32_t cv;         /* 1: apply the learned control variate (see rssri_cv_train) */
+  int32_t test_wait_polls;  /* testing only, 0 otherwise: > 0 makes the tensor-core
+                               kernels of this call issue no copy or product and give
+                               up each bounded wait after this many polls, so that the
+                               call returns RSSRI_ERR_TIMEOUT with nothing in flight */
+  int32_t test_fail_alloc;  /* testing only, 0 otherwise: k > 0 makes the k-th device
+                               allocation of this call fail (RSSRI_ERR_OOM) without
+                               calling the allocator */
   int32_t reserved0;
 } rssri_options;
 

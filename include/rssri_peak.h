@@ -21,13 +21,14 @@ enum {
   RSSRI_PEAK_FFMA = 2  /* fp32 fused multiply-add pipe (FFMA), 2 flop per FMA          */
 };
 
-/* Run a compute-only kernel on every SM of `device` (64 resident warps per
- * SM, 8 independent dependency chains per thread), time 5 launches with CUDA
- * events on the legacy default stream after one warm-up launch, and return
- * the achieved rate in TFLOP/s (*tflops) and the mean launch time in ms
- * (*ms, may be NULL).  Allocates and frees one small device buffer; makes
- * `device` current; synchronises.  Errors: INVALID_ARG (unknown `which`,
- * null tflops), OOM, CUDA. */
+/* Run compute-only kernels on every SM of `device` in several shapes (4 to 16
+ * independent dependency chains per thread, 16 to 64 resident warps per SM,
+ * shared or distinct operand registers), time each with CUDA events on the
+ * legacy default stream (one warm-up and three timed launches of ~10 ms),
+ * and return the best rate in TFLOP/s (*tflops) and that shape's mean launch
+ * time in ms (*ms, may be NULL).  Allocates and frees one small device
+ * buffer; makes `device` current; synchronises; takes about a second.
+ * Errors: INVALID_ARG (unknown `which`, null tflops), OOM, CUDA. */
 RSSRI_API int rssri_peak_measure(int which, int device, double *tflops, double *ms);
 
 #ifdef __cplusplus

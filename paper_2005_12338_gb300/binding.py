@@ -28,7 +28,7 @@ RSSRI_CV_NPARAM = 134657
 PROF_CLASSES = ["chain_gemm", "dd_spmm", "dd_gemm", "factor_gemm", "setup_gemm", "green", "other",
                 "slice"]
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_SPD", -3: "NONSYMMETRIC_ERI", -4: "OOM",
-          -5: "CUDA", -6: "TIMEOUT", -7: "NOT_READY", -8: "NONFINITE"}
+          -5: "CUDA", -6: "TIMEOUT", -7: "NOT_READY", -8: "NONFINITE", -9: "RANGE"}
 
 
 class rssri_problem(C.Structure):
@@ -43,7 +43,8 @@ class rssri_options(C.Structure):
     _fields_ = [("eps_prime", C.c_double), ("eps", C.c_double), ("n_s", C.c_int64),
                 ("seed", C.c_uint64), ("xi_offset", C.c_int64), ("estimator", C.c_int32),
                 ("precision", C.c_int32), ("pair_batch", C.c_int64), ("profile", C.c_int32),
-                ("dd_arith", C.c_int32), ("cv", C.c_int32), ("reserved0", C.c_int32)]
+                ("dd_arith", C.c_int32), ("cv", C.c_int32), ("test_wait_polls", C.c_int32),
+                ("test_fail_alloc", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class rssri_stats(C.Structure):
@@ -181,9 +182,11 @@ class Handle:
     @staticmethod
     def options(eps_prime=0.02, eps=1e-3, n_s=64, seed=0, xi_offset=0, estimator=RSSRI_EST_CV,
                 pair_batch=0, profile=0, precision=RSSRI_PREC_FP64,
-                dd_arith=RSSRI_DD_FP64, cv=0) -> rssri_options:
+                dd_arith=RSSRI_DD_FP64, cv=0, test_wait_polls=0,
+                test_fail_alloc=0) -> rssri_options:
         return rssri_options(eps_prime, eps, n_s, seed & ((1 << 64) - 1), xi_offset, estimator,
-                             precision, pair_batch, profile, dd_arith, cv, 0)
+                             precision, pair_batch, profile, dd_arith, cv, test_wait_polls,
+                             test_fail_alloc, 0)
 
     def setup(self, eri3, metric, orb_e, orb_c, tau, tau_w, n_occ: int, mu: float, beta: float,
               opts: rssri_options):

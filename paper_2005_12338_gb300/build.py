@@ -23,7 +23,8 @@ CHECKS = os.environ.get("RSSRI_CHECKS", "") == "1"
 BUILD = os.path.join(HERE, "_build_checks" if CHECKS else "_build")
 LIB = os.path.join(HERE, "librssri_checks.so" if CHECKS else "librssri.so")
 SOURCES = ["api.cu", "gemm_f64.cu", "kernels.cu", "static_energy.cu", "tc_gemm.cu", "chain_tc.cu",
-           "dd_df64.cu", "dd_spmm_df64.cu", "cv_mlp.cu", "peak.cu", "oz_gemm.cu"]
+           "dd_df64.cu", "dd_spmm_df64.cu", "cv_mlp.cu", "peak.cu", "oz_gemm.cu",
+           "tc_group.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

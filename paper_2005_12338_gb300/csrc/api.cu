@@ -13,6 +13,7 @@
 #include "kernels.cuh"
 #include "oz_gemm.cuh"
 #include "tc_gemm.cuh"
+#include "tc_group.cuh"
 
 using namespace rssri;
 
@@ -24,9 +25,22 @@ struct DevBuf {
   template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Testing: the device allocation (counted from 1 within one API call) that is
+// made to fail without calling the allocator; 0 = none (rssri_options.test_fail_alloc).
+thread_local int g_fail_alloc_at = 0, g_alloc_count = 0;
+
+struct AllocFailScope {
+  explicit AllocFailScope(int k) {
+    g_fail_alloc_at = k;
+    g_alloc_count = 0;
+  }
+  ~AllocFailScope() { g_fail_alloc_at = 0; }
+};
+
 cudaError_t ensure(DevBuf &b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return cudaSuccess;
+  if (g_fail_alloc_at > 0 && ++g_alloc_count == g_fail_alloc_at) return cudaErrorMemoryAllocation;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -100,6 +114,7 @@ struct rssri_handle {
   bool d_df64_ready = false;
   // bf16 chain buffers
   DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
+  DevBuf hclt, hfl;  // learned control variate on the tensor-core chain: (C^L)^T, F^L per pair
   // the bf16 chain captured as a CUDA graph, valid for the key it was built for
   cudaGraphExec_t chain_graph = nullptr;
   cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot capture)
@@ -116,6 +131,7 @@ struct rssri_handle {
   int setup_arith = RSSRI_DD_FP64;
   bool gg_valid = false;  // GGhl holds the pair split of the current G, Gb
   bool pending_block = false;  // the enqueued sigma call rebuilt the block
+  int test_wait_polls = 0;     // rssri_options.test_wait_polls of the current call
   DevBuf sdd0;            // zeros: the block of the plain stochastic-RI estimator
   // the sliced (RSSRI_DD_OZ) block: pair index map, the exchange contraction's
   // left operand and the digits of K_P (setup); per-tau digit buffers
@@ -125,6 +141,7 @@ struct rssri_handle {
   };
   bool oz_ready = false;
   OzExch oz_geo;
+  DevBuf oz_gs, oz_gexp;  // G(tau) 2^-e(tau) as pairs, and e(tau), for K^Q G
   DevBuf oz_pidx, oz_tmp;
   OzBuf ozX, ozKP, ozKPt, ozGb, ozBig0, ozBig1, ozAtP, ozGam;
   rssri_stats stats{};
@@ -146,6 +163,10 @@ struct rssri_handle {
 };
 
 namespace {
+
+// Device flags (ints): [4] tensor-core chain timeout, [5] sliced-block timeout,
+// [8..10] the double-float range check (flag, running maximum, block count).
+int *range_flag(rssri_handle *h) { return h->flags.as<int>() + 8; }
 
 // ------------------------------------------------------------ profiling ----
 cudaEvent_t take_event(rssri_handle *h) {
@@ -227,6 +248,7 @@ int validate_options(const rssri_options *o, bool for_sigma) {
   if (o->dd_arith != RSSRI_DD_FP64 && o->dd_arith != RSSRI_DD_DF64 && o->dd_arith != RSSRI_DD_OZ)
     return RSSRI_ERR_INVALID_ARG;
   if (o->dd_arith == RSSRI_DD_OZ && !oz_available()) return RSSRI_ERR_INVALID_ARG;
+  if (o->test_wait_polls < 0 || o->test_fail_alloc < 0) return RSSRI_ERR_INVALID_ARG;
   if (for_sigma) {
     if (o->n_s < 2 || o->n_s > (1LL << 30) || o->xi_offset < 0 ||
         o->xi_offset + o->n_s >= (1LL << 40))
@@ -319,8 +341,8 @@ int metric_inv_sqrt(rssri_handle *h, int *rc, bool df64) {
     }
     {
       SPAN(RSSRI_PROF_OTHER, 0.0);
-      RS_TRY(to_df64(A, (long long)na * na, h->nsA2.as<float2>(), s));
-      RS_TRY(to_df64(B, (long long)na * na, h->nsB2.as<float2>(), s));
+      RS_TRY(to_df64(A, (long long)na * na, h->nsA2.as<float2>(), s, range_flag(h)));
+      RS_TRY(to_df64(B, (long long)na * na, h->nsB2.as<float2>(), s, range_flag(h)));
     }
     SPAN(RSSRI_PROF_SETUP_GEMM, 2.0 * na * (double)na * na * 1e-9);
     DfGemm g;
@@ -379,6 +401,7 @@ const char *rssri_status_string(int code) {
     case RSSRI_ERR_TIMEOUT: return "bounded device wait expired";
     case RSSRI_ERR_NOT_READY: return "rssri_setup has not completed on this handle";
     case RSSRI_ERR_NONFINITE: return "non-finite input or result";
+    case RSSRI_ERR_RANGE: return "a double-float operand lies outside the pairs' exponent range";
     default: return "unknown status";
   }
 }
@@ -424,10 +447,10 @@ void rssri_destroy(rssri_handle *h) {
                     &h->e_st, &h->sig_raw, &h->sdd, &h->PG, &h->At, &h->T, &h->AP, &h->Gam, &h->L,
                     &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
                     &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
-                    &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->Dhl,
+                    &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->hclt, &h->hfl, &h->Dhl,
                     &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->facHl, &h->xgHl, &h->cHl, &h->bHl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
-                    &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss, &h->sdd0};
+                    &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss, &h->sdd0, &h->oz_gs, &h->oz_gexp};
   for (DevBuf *b : bufs) release(*b);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -446,6 +469,8 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   rc = validate_options(o, false);
   if (rc) return rc;
   if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  AllocFailScope alloc_test(o->test_fail_alloc);
+  h->test_wait_polls = o->test_wait_polls;
   cudaStream_t s = h->stream;
   h->ready = false;
   h->have_sigma = false;
@@ -579,7 +604,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
     if (o->dd_arith != RSSRI_DD_FP64) {
       RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
       RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
-      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s)); }
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s, range_flag(h))); }
       {
         SPAN(RSSRI_PROF_SETUP_GEMM, 2.0 * P * (double)P * na * 1e-9);
         DfGemm g;
@@ -589,7 +614,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
         g.C64 = h->D.as<double>(); g.ldc = P;
         RS_CK(df_gemm(g, nullptr, 0, s));
       }
-      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s)); }
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s, range_flag(h))); }
       h->d_df64_ready = true;
     } else {
       GemmArgs g;
@@ -609,6 +634,11 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   if (rc) { if (rc == RSSRI_ERR_CUDA) h->broken = true; return rc; }
   RS_CK(cudaEventRecord(h->ev[1], s));
   RS_CK(cudaEventSynchronize(h->ev[1]));
+  {
+    int range = 0;
+    RS_CK(fetch(&range, range_flag(h), s));
+    if (range) return RSSRI_ERR_RANGE;
+  }
   float ms = 0;
   cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
   h->t_setup_ms = ms;
@@ -790,13 +820,13 @@ cudaError_t sigma_dd_tau_df64(rssri_handle *h, const float2 *Ghl, const float2 *
 }
 
 // ------------------------------------------- the sliced (RSSRI_DD_OZ) block --
-// A digit buffer for batch x rows x K values (rows padded to ld = K rounded up to 8).
+// A digit buffer for batch x rows x K values (rows padded to ld = K rounded up to 16).
 cudaError_t oz_make(rssri_handle::OzBuf &b, int batch, int rows, long long K) {
   OzDigits v;
   v.batch = batch;
   v.rows = rows;
   v.K = K;
-  v.ld = (K + 7) / 8 * 8;
+  v.ld = (K + 15) / 16 * 16;
   RS_TRY(ensure(b.d, oz_digit_elems(v) * sizeof(__nv_bfloat16)));
   RS_TRY(ensure(b.e, (size_t)batch * rows * sizeof(int)));
   v.d = b.d.as<__nv_bfloat16>();
@@ -811,7 +841,9 @@ cudaError_t oz_slice_p(rssri_handle *h, const OzView &v, const OzDigits &o) {
 }
 
 // An fp64-accurate product on the tensor cores, counted under `cls`.
-cudaError_t oz_gemm_p(rssri_handle *h, int cls, const OzGemm &g) {
+cudaError_t oz_gemm_p(rssri_handle *h, int cls, const OzGemm &g_in) {
+  OzGemm g = g_in;
+  g.wait_polls = h->test_wait_polls;
   const double alg = 2.0 * g.M * (double)g.N * g.A.K * g.batch;
   SPAN_T(cls, alg * 1e-9, oz_gemm_flops(g) * 1e-9);
   const size_t need = oz_gemm_work(g) * sizeof(double);
@@ -895,7 +927,7 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
   { OzView v; v.x = Gb; v.rs = n; v.cs2 = 1; v.k2pad = v.k2n = n; v.xlen = nn;
     RS_TRY(oz_slice_p(h, v, dGb)); }
   OzDigits dPGb = h->ozBig0.v;
-  dPGb.rows = (int)(n * (long long)na); dPGb.K = n; dPGb.ld = (n + 7) / 8 * 8;
+  dPGb.rows = (int)(n * (long long)na); dPGb.K = n; dPGb.ld = (n + 15) / 16 * 16;
   { OzView v; v.x2 = PGhl; v.rs = 1; v.cs2 = (long long)n * na; v.k2pad = v.k2n = n;
     v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dPGb)); }
@@ -909,10 +941,11 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
   OzDigits dAt = h->ozBig1.v;
   dAt.rows = na; dAt.K = (long long)n * x.ldl; dAt.ld = dAt.K;
   { OzView v; v.x = At; v.rs = 1; v.cs1 = (long long)n * na; v.cs2 = na; v.k2pad = x.ldl;
+    v.k2off = x.lsh;
     v.k2n = n; v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dAt)); }
   { SPAN_T(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9, oz_exch_flops(x) * 1e-9);
-    RS_TRY(oz_exch(x, h->ozX.v, dAt, T, nna, -1.0, err, s)); }
+    RS_TRY(oz_exch(x, h->ozX.v, dAt, T, nna, -1.0, err, s, h->test_wait_polls)); }
   // Gamma = K_P^T At_P (At_P: the rows of At at the kept pairs)
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
   { OzView v; v.x = h->AP.as<double>(); v.rs = 1; v.cs2 = na; v.k2pad = v.k2n = P;
@@ -940,12 +973,12 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
   // Sigma_DD[i][j] = sum_{(m,Q)} PG[i][m][Q] U[j][m][Q]
   OzDigits dU = h->ozBig0.v;
   const long long kmq = (long long)n * na;  // the contraction index (m, Q)
-  dU.rows = n; dU.K = kmq; dU.ld = (kmq + 7) / 8 * 8;
+  dU.rows = n; dU.K = kmq; dU.ld = (kmq + 15) / 16 * 16;
   { OzView v; v.x = T; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dU.K;
     v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dU)); }
   OzDigits dPGa = h->ozBig1.v;
-  dPGa.rows = n; dPGa.K = kmq; dPGa.ld = (kmq + 7) / 8 * 8;
+  dPGa.rows = n; dPGa.K = kmq; dPGa.ld = (kmq + 15) / 16 * 16;
   { OzView v; v.x2 = PGhl; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dPGa.K;
     v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dPGa)); }
@@ -976,8 +1009,8 @@ cudaError_t ensure_d_df64(rssri_handle *h) {
   RS_TRY(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
   RS_TRY(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
   SPAN(RSSRI_PROF_OTHER, 0.0);
-  RS_TRY(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), h->stream));
-  RS_TRY(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), h->stream));
+  RS_TRY(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), h->stream, range_flag(h)));
+  RS_TRY(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), h->stream, range_flag(h)));
   h->d_df64_ready = true;
   return cudaSuccess;
 }
@@ -988,8 +1021,13 @@ cudaError_t ensure_gg(rssri_handle *h) {
   const long long nn = (long long)h->n * h->n, nt = h->n_tau;
   RS_TRY(ensure(h->GGhl, (size_t)2 * nt * nn * sizeof(float2)));
   SPAN(RSSRI_PROF_OTHER, 0.0);
-  RS_TRY(to_df64(h->G.as<double>(), nt * nn, h->GGhl.as<float2>(), h->stream));
-  RS_TRY(to_df64(h->Gb.as<double>(), nt * nn, h->GGhl.as<float2>() + nt * nn, h->stream));
+  // one conversion per tau point: the range check holds per matrix
+  for (long long t = 0; t < nt; ++t) {
+    RS_TRY(to_df64(h->G.as<double>() + t * nn, nn, h->GGhl.as<float2>() + t * nn, h->stream,
+                   range_flag(h)));
+    RS_TRY(to_df64(h->Gb.as<double>() + t * nn, nn, h->GGhl.as<float2>() + (nt + t) * nn,
+                   h->stream, range_flag(h)));
+  }
   h->gg_valid = true;
   return cudaSuccess;
 }
@@ -1026,9 +1064,9 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
         const int rc = oz_setup(h);
         if (rc) return rc;
       }
-      // the largest per-tau digit operand: n*na rows of ld8(n), n rows of ld8(n*na), or
+      // the largest per-tau digit operand: n*na rows of ld16(n), n rows of ld16(n*na), or
       // na rows of n*ldl
-      const long long ld_n = (n + 7) / 8 * 8, ld_kmq = ((long long)n * na + 7) / 8 * 8;
+      const long long ld_n = (n + 15) / 16 * 16, ld_kmq = ((long long)n * na + 15) / 16 * 16;
       const long long big = std::max({(long long)n * na * ld_n, (long long)n * ld_kmq,
                                       (long long)na * n * h->oz_geo.ldl});
       RS_CK(oz_make(h->ozGb, 1, n, n));
@@ -1069,12 +1107,21 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
     RS_CK(build_green(h));
   }
   // S7 per tau
-  if (dd_df64 || dd_oz) RS_CK(ensure_gg(h));
+  if (dd_df64) RS_CK(ensure_gg(h));
+  if (dd_oz) {
+    // K^Q G in double-float on G(tau) 2^-e(tau); Sigma_DD is then 2^(2 e) times the result
+    RS_CK(ensure(h->oz_gs, (size_t)nt * nn * sizeof(float2)));
+    RS_CK(ensure(h->oz_gexp, (size_t)nt * sizeof(int)));
+    SPAN(RSSRI_PROF_OTHER, 0.0);
+    RS_CK(to_df64_scaled(G, nt, nn, h->oz_gs.as<float2>(), h->oz_gexp.as<int>(), s));
+  }
   for (int t = 0; t < nt; ++t) {
     double *out = h->sdd.as<double>() + t * nn;
-    if (dd_oz)
-      RS_CK(sigma_dd_tau_oz(h, h->GGhl.as<float2>() + t * nn, Gb + t * nn, out));
-    else if (dd_df64)
+    if (dd_oz) {
+      RS_CK(sigma_dd_tau_oz(h, h->oz_gs.as<float2>() + t * nn, Gb + t * nn, out));
+      SPAN(RSSRI_PROF_OTHER, 0.0);
+      RS_CK(scale_pow2(out, nn, h->oz_gexp.as<int>() + t, 2, s));
+    } else if (dd_df64)
       RS_CK(sigma_dd_tau_df64(h, h->GGhl.as<float2>() + t * nn,
                               h->GGhl.as<float2>() + (nt + t) * nn, out));
     else
@@ -1102,21 +1149,97 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
 }
 
 // S8 on the tensor cores (bf16 or tf32 operands, fp32 accumulation), all
-// sample pairs at once, for every tau:
+// sample pairs at once, tau points in chunks of tc tau per stage:
 //   P = [R^S; R^L] G,  dC = P_S R' + P_L R'^S,  C^L = P_L R'^L,
 //   [X; Y] = [dC; C^L] Gb,  fold (traces, energy, 2 dt I - X, 2 t^L I - Y, C^T, dC^T),
 //   sum_x (2 dt I - X) C + (2 t^L I - Y) dC  (one contraction over the pairs).
 // sig[t] = sdd[t] + that sum / n_s.  e_st accumulates the pair energies.
+// Each stage of a chunk (all its tau points, all pairs) is one persistent
+// launch of tc_group: its products go into one device work queue of tiles.
 // The launches are issued into a CUDA graph once and the graph is replayed
 // while the shapes, buffers and tau weights stay the same.
 struct ChainBufs {
   int kind;  // TcKind of the operands
+  int wait_polls;  // testing (see TcGemm)
+  const double *cvc;  // coefficients c [n_tau][n][n] of the learned control variate, or null
+  void *clt;          // (C^L)^T operands [tc][ns][n][ldp] (control variate)
+  float *fl;          // F^L per pair [tc][ns][n][n] fp32 (control variate)
   size_t es;  // operand element size
+  int tc;     // tau points per chunk
+  // per chunk slot j < tc (buffers hold tc slots):
   void *xsl, *y3, *gh, *gbh, *P, *dcl, *a6, *ct, *dct;
   float *dc32, *cl32, *xy32, *part;
   double *fold;
   int bpc, groups;
 };
+
+// The products of the chain's stages for tau points [t0, t0 + c) (slot j = t - t0).
+void chain_stage_probs(rssri_handle *h, const ChainBufs &b, int ns, int t0, int c, int stage,
+                       std::vector<TcProb> &out) {
+  const int n = h->n;
+  const int ldp = (n + 7) / 8 * 8;
+  const long long nn = (long long)n * n, mat = (long long)n * ldp;
+  auto at = [&](void *p, long long e) { return static_cast<void *>(static_cast<char *>(p) + e * b.es); };
+  auto op = [&](const void *p, long long sb, int rows) {
+    TcOperand t;
+    t.ptr = p;
+    t.ld = ldp;
+    t.sb = sb;
+    t.rows = rows;
+    return t;
+  };
+  out.clear();
+  if (stage == 0) {  // P = [R^S; R^L] G for every tau of the chunk: batch over tau
+    TcProb g;
+    g.M = 2 * ns * n; g.N = n; g.K[0] = n; g.batch = c;
+    g.A[0] = op(b.xsl, 0, 2 * ns * n); g.B[0] = op(at(b.gh, (long long)t0 * mat), mat, n);
+    g.cop = b.P; g.ldcop = ldp;
+    out.push_back(g);
+  } else if (stage == 1) {  // dC = P_S R' + P_L R'^S and C^L = P_L R'^L per tau
+    for (int j = 0; j < c; ++j) {
+      void *Pj = at(b.P, (long long)j * 2 * ns * mat);
+      TcProb g;
+      g.M = n; g.N = n; g.batch = ns; g.nseg = 2; g.K[0] = g.K[1] = n;
+      g.A[0] = op(Pj, mat, n); g.B[0] = op(b.y3, mat, n);
+      g.A[1] = op(at(Pj, ns * mat), mat, n); g.B[1] = op(at(b.y3, ns * mat), mat, n);
+      g.c32 = b.dc32 + (long long)j * ns * nn;
+      g.cop = at(b.dcl, (long long)j * 2 * ns * mat); g.ldcop = ldp;
+      out.push_back(g);
+      TcProb l;
+      l.M = n; l.N = n; l.batch = ns; l.K[0] = n;
+      l.A[0] = op(at(Pj, ns * mat), mat, n); l.B[0] = op(at(b.y3, 2 * ns * mat), mat, n);
+      l.c32 = b.cl32 + (long long)j * ns * nn;
+      l.cop = at(b.dcl, ((long long)j * 2 * ns + ns) * mat); l.ldcop = ldp;
+      out.push_back(l);
+    }
+  } else if (stage == 2) {  // [X; Y] = [dC; C^L] Gb for every tau: batch over tau
+    TcProb g;
+    g.M = 2 * ns * n; g.N = n; g.K[0] = n; g.batch = c;
+    g.A[0] = op(b.dcl, 2 * ns * mat, 2 * ns * n);
+    g.B[0] = op(at(b.gbh, (long long)t0 * mat), mat, n);
+    g.c32 = b.xy32;
+    out.push_back(g);
+  } else if (stage == 3) {  // sum over pairs of (2 dt I - X) C + (2 t^L I - Y) dC per tau
+    for (int j = 0; j < c; ++j) {
+      void *A6 = at(b.a6, (long long)j * 2 * ns * mat);
+      TcProb g;
+      g.M = n; g.N = n; g.batch = ns; g.bpc = b.bpc; g.nseg = 2; g.K[0] = g.K[1] = n;
+      g.A[0] = op(A6, mat, n); g.B[0] = op(at(b.ct, (long long)j * ns * mat), mat, n);
+      g.A[1] = op(at(A6, ns * mat), mat, n); g.B[1] = op(at(b.dct, (long long)j * ns * mat), mat, n);
+      g.c32 = b.part + (long long)j * b.groups * nn;
+      out.push_back(g);
+    }
+  } else {  // F^L = (2 t^L I - Y) C^L per pair and tau (learned control variate)
+    for (int j = 0; j < c; ++j) {
+      TcProb g;
+      g.M = n; g.N = n; g.batch = ns; g.K[0] = n;
+      g.A[0] = op(at(b.a6, ((long long)j * 2 * ns + ns) * mat), mat, n);
+      g.B[0] = op(at(b.clt, (long long)j * ns * mat), mat, n);
+      g.c32 = b.fl + (long long)j * ns * nn;
+      out.push_back(g);
+    }
+  }
+}
 
 cudaError_t issue_chain_tc(rssri_handle *h, cudaStream_t s, int ns, const double *G,
                            const double *Gb, const double *sdd, double *sig, int *err,
@@ -1128,94 +1251,83 @@ cudaError_t issue_chain_tc(rssri_handle *h, cudaStream_t s, int ns, const double
   RS_TRY(chain_matrices(b.kind, G, nt, n, ldp, b.gh, s));
   RS_TRY(chain_matrices(b.kind, Gb, nt, n, ldp, b.gbh, s));
   const double ne = 2.0 * h->n_occ;
-  // element offset e into operand buffer p
   auto at = [&](void *p, long long e) { return static_cast<void *>(static_cast<char *>(p) + e * b.es); };
-  auto op = [&](void *p, long long sb, int rows) {
-    TcOperand t;
-    t.ptr = p;
-    t.ld = ldp;
-    t.sb = sb;
-    t.rows = rows;
-    return t;
-  };
-  for (int t = 0; t < nt; ++t) {
-    void *gt = at(b.gh, t * mat), *gbt = at(b.gbh, t * mat);
-    {  // P = [R^S; R^L] G (stacked rows of all pairs)
-      TcGemm g;
-      g.kind = b.kind;
-      g.M = 2 * ns * n; g.N = n; g.K[0] = n;
-      g.A[0] = op(b.xsl, 0, 2 * ns * n); g.B[0] = op(gt, 0, n);
-      g.cop = b.P; g.ldcop = ldp; g.err = err;
-      RS_TRY(tc_gemm(g, s));
+  std::vector<TcProb> probs;
+  for (int t0 = 0; t0 < nt; t0 += b.tc) {
+    const int c = std::min(b.tc, nt - t0);
+    for (int stage = 0; stage < 3; ++stage) {
+      chain_stage_probs(h, b, ns, t0, c, stage, probs);
+      RS_TRY(tc_group(b.kind, probs.data(), (int)probs.size(), err, s, b.wait_polls));
     }
-    {  // dC = P_S R' + P_L R'^S
-      TcGemm g;
-      g.kind = b.kind;
-      g.M = n; g.N = n; g.batch = ns; g.nseg = 2; g.K[0] = g.K[1] = n;
-      g.A[0] = op(b.P, mat, n); g.B[0] = op(b.y3, mat, n);
-      g.A[1] = op(at(b.P, ns * mat), mat, n); g.B[1] = op(at(b.y3, ns * mat), mat, n);
-      g.c32 = b.dc32; g.cop = b.dcl; g.ldcop = ldp; g.err = err;
-      RS_TRY(tc_gemm(g, s));
+    for (int j = 0; j < c; ++j)
+      RS_TRY(fold_tc(b.kind, b.xy32 + (long long)j * 2 * ns * nn, b.dc32 + (long long)j * ns * nn,
+                     b.cl32 + (long long)j * ns * nn, ns, n, ldp, h->h_tau_w[t0 + j], ne,
+                     at(b.a6, (long long)j * 2 * ns * mat), at(b.ct, (long long)j * ns * mat),
+                     at(b.dct, (long long)j * ns * mat),
+                     b.cvc ? at(b.clt, (long long)j * ns * mat) : nullptr, h->e_st.as<double>(),
+                     b.fold + (long long)j * ns * ceil_div(n, 32) * 4, s));
+    chain_stage_probs(h, b, ns, t0, c, 3, probs);
+    RS_TRY(tc_group(b.kind, probs.data(), (int)probs.size(), err, s, b.wait_polls));
+    for (int j = 0; j < c; ++j)
+      RS_TRY(reduce_tc(b.part + (long long)j * b.groups * nn, b.groups, n, sdd + (t0 + j) * nn,
+                       (double)ns, sig + (t0 + j) * nn, s));
+    if (b.cvc) {
+      chain_stage_probs(h, b, ns, t0, c, 4, probs);
+      RS_TRY(tc_group(b.kind, probs.data(), (int)probs.size(), err, s, b.wait_polls));
+      for (int j = 0; j < c; ++j)
+        RS_TRY(cv_tc_apply(b.fl + (long long)j * ns * nn, ns, n, b.cvc + (t0 + j) * nn,
+                           sdd + (t0 + j) * nn, Gb + (t0 + j) * nn, h->h_tau_w[t0 + j], ne,
+                           sig + (t0 + j) * nn, h->e_st.as<double>(), s));
     }
-    {  // C^L = P_L R'^L
-      TcGemm g;
-      g.kind = b.kind;
-      g.M = n; g.N = n; g.batch = ns; g.K[0] = n;
-      g.A[0] = op(at(b.P, ns * mat), mat, n); g.B[0] = op(at(b.y3, 2 * ns * mat), mat, n);
-      g.c32 = b.cl32; g.cop = at(b.dcl, ns * mat); g.ldcop = ldp; g.err = err;
-      RS_TRY(tc_gemm(g, s));
-    }
-    {  // [X; Y] = [dC; C^L] Gb
-      TcGemm g;
-      g.kind = b.kind;
-      g.M = 2 * ns * n; g.N = n; g.K[0] = n;
-      g.A[0] = op(b.dcl, 0, 2 * ns * n); g.B[0] = op(gbt, 0, n);
-      g.c32 = b.xy32; g.err = err;
-      RS_TRY(tc_gemm(g, s));
-    }
-    RS_TRY(fold_tc(b.kind, b.xy32, b.dc32, b.cl32, ns, n, ldp, h->h_tau_w[t], ne, b.a6, b.ct,
-                   b.dct, h->e_st.as<double>(), b.fold, s));
-    {  // sum over pairs of (2 dt I - X) C + (2 t^L I - Y) dC
-      TcGemm g;
-      g.kind = b.kind;
-      g.M = n; g.N = n; g.batch = ns; g.bpc = b.bpc; g.nseg = 2; g.K[0] = g.K[1] = n;
-      g.A[0] = op(b.a6, mat, n); g.B[0] = op(b.ct, mat, n);
-      g.A[1] = op(at(b.a6, ns * mat), mat, n); g.B[1] = op(b.dct, mat, n);
-      g.c32 = b.part; g.err = err;
-      RS_TRY(tc_gemm(g, s));
-    }
-    RS_TRY(reduce_tc(b.part, b.groups, n, sdd + t * nn, (double)ns,
-                       sig + t * nn, s));
   }
   return cudaSuccess;
 }
 
 cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const double *Gb,
-                     const double *sdd, double *sig, int *err) {
+                     const double *sdd, double *sig, int *err, const double *cvc) {
   cudaStream_t s = h->stream;
   const int n = h->n, nt = h->n_tau;
   const int ldp = (n + 7) / 8 * 8;
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
   ChainBufs b;
   b.kind = kind;
+  b.wait_polls = h->test_wait_polls;
+  b.cvc = cvc;
+  b.clt = nullptr;
+  b.fl = nullptr;
   b.es = kind == TC_BF16 ? sizeof(__nv_bfloat16) : sizeof(float);
   const size_t b16 = b.es;
   b.bpc = std::max(1, ceil_div(ns, 152));
   b.groups = ceil_div(ns, b.bpc);
+  // tau points per chunk: as many as fit a scratch budget of 8 GB (at least 1)
+  const size_t per_tau = 2 * ns * mat * b16 /*P*/ + 2 * ns * nn * 4 /*dC, C^L fp32*/ +
+                         2 * ns * mat * b16 /*dcl*/ + 2 * ns * nn * 4 /*X, Y*/ +
+                         2 * ns * mat * b16 /*a6*/ + 2 * ns * mat * b16 /*ct, dct*/ +
+                         (size_t)b.groups * nn * 4 /*part*/ +
+                         (cvc ? ns * mat * b16 + ns * nn * 4 : 0);
+  b.tc = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(nt, 12),
+                                                   ((size_t)8 << 30) / per_tau));
+  const int tc = b.tc;
   RS_TRY(ensure(h->hxsl, 2 * ns * mat * b16));
   RS_TRY(ensure(h->hy3, 3 * ns * mat * b16));
   RS_TRY(ensure(h->hg, nt * mat * b16));
   RS_TRY(ensure(h->hgb, nt * mat * b16));
-  RS_TRY(ensure(h->hP, 2 * ns * mat * b16));
-  RS_TRY(ensure(h->hdc32, ns * nn * sizeof(float)));
-  RS_TRY(ensure(h->hcl32, ns * nn * sizeof(float)));
-  RS_TRY(ensure(h->hdcl16, 2 * ns * mat * b16));
-  RS_TRY(ensure(h->hxy32, 2 * ns * nn * sizeof(float)));
-  RS_TRY(ensure(h->ha6, 2 * ns * mat * b16));
-  RS_TRY(ensure(h->hct, ns * mat * b16));
-  RS_TRY(ensure(h->hdct, ns * mat * b16));
-  RS_TRY(ensure(h->hpart, b.groups * nn * sizeof(float)));
-  RS_TRY(ensure(h->hfold, (size_t)ns * ceil_div(n, 32) * 4 * sizeof(double)));
+  RS_TRY(ensure(h->hP, (size_t)tc * 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hdc32, (size_t)tc * ns * nn * sizeof(float)));
+  RS_TRY(ensure(h->hcl32, (size_t)tc * ns * nn * sizeof(float)));
+  RS_TRY(ensure(h->hdcl16, (size_t)tc * 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hxy32, (size_t)tc * 2 * ns * nn * sizeof(float)));
+  RS_TRY(ensure(h->ha6, (size_t)tc * 2 * ns * mat * b16));
+  RS_TRY(ensure(h->hct, (size_t)tc * ns * mat * b16));
+  RS_TRY(ensure(h->hdct, (size_t)tc * ns * mat * b16));
+  RS_TRY(ensure(h->hpart, (size_t)tc * b.groups * nn * sizeof(float)));
+  RS_TRY(ensure(h->hfold, (size_t)tc * ns * ceil_div(n, 32) * 4 * sizeof(double)));
+  if (cvc) {
+    RS_TRY(ensure(h->hclt, (size_t)tc * ns * mat * b16));
+    RS_TRY(ensure(h->hfl, (size_t)tc * ns * nn * sizeof(float)));
+    b.clt = h->hclt.p;
+    b.fl = h->hfl.as<float>();
+  }
   b.xsl = h->hxsl.p; b.y3 = h->hy3.p; b.gh = h->hg.p; b.gbh = h->hgb.p; b.P = h->hP.p;
   b.dcl = h->hdcl16.p; b.a6 = h->ha6.p; b.ct = h->hct.p; b.dct = h->hdct.p;
   b.dc32 = h->hdc32.as<float>(); b.cl32 = h->hcl32.as<float>(); b.xy32 = h->hxy32.as<float>();
@@ -1223,8 +1335,10 @@ cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const d
   b.fold = h->hfold.as<double>();
   RS_TRY(tc_prepare());
   // the graph is keyed on every pointer and value baked into its launches
-  std::vector<uintptr_t> key = {(uintptr_t)kind, (uintptr_t)ns, (uintptr_t)n, (uintptr_t)nt, (uintptr_t)h->n_occ,
+  std::vector<uintptr_t> key = {(uintptr_t)kind, (uintptr_t)b.wait_polls, (uintptr_t)ns, (uintptr_t)n,
+                                (uintptr_t)nt, (uintptr_t)h->n_occ, (uintptr_t)tc,
                                 (uintptr_t)G, (uintptr_t)Gb, (uintptr_t)sig, (uintptr_t)err,
+                                (uintptr_t)cvc, (uintptr_t)b.clt, (uintptr_t)b.fl,
                                 (uintptr_t)h->fac.p, (uintptr_t)h->e_st.p, (uintptr_t)sdd};
   for (DevBuf *d : {&h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32, &h->hdcl16,
                     &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold})
@@ -1232,6 +1346,17 @@ cudaError_t chain_tc(rssri_handle *h, int kind, int ns, const double *G, const d
   if (!h->chain_graph || key != h->chain_key_ptr || h->h_tau_w != h->chain_key_w) {
     if (h->chain_graph) cudaGraphExecDestroy(h->chain_graph);
     h->chain_graph = nullptr;
+    // tune the N tile of every stage's product shape (outside the capture;
+    // each shape is tuned once per process)
+    if (!b.wait_polls) {
+      std::vector<TcProb> probs;
+      for (int stage = 0; stage < (cvc ? 5 : 4); ++stage) {
+        chain_stage_probs(h, b, ns, 0, std::min(tc, nt), stage, probs);
+        tc_group_tune(kind, probs[0], err, s);
+      }
+      RS_TRY(cudaStreamSynchronize(s));
+      RS_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    }
     cudaGraph_t graph = nullptr;
     if (!h->cap_stream) RS_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     RS_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1265,7 +1390,7 @@ constexpr int CV_CHUNK = 65536;
 
 size_t cv_work_floats(int batch) {
   const int m = std::max(batch, 2048);
-  return std::max({sgemm_work_floats(CV_HIDDEN, CV_HIDDEN, m),
+  return cv_tc_work_floats() + std::max({sgemm_work_floats(CV_HIDDEN, CV_HIDDEN, m),
                    sgemm_work_floats(CV_HIDDEN, CV_NFEAT, m), sgemm_work_floats(1, CV_HIDDEN, m),
                    (size_t)1024});
 }
@@ -1406,12 +1531,13 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   if (rc) return rc;
   if (!sigma && !collect_stats) return RSSRI_ERR_INVALID_ARG;
   const bool use_cv = o->cv != 0;
-  if ((use_cv || collect_stats) &&
-      ((o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_DF64) ||
-       o->estimator != RSSRI_EST_CV))
+  if ((use_cv || collect_stats) && o->estimator != RSSRI_EST_CV) return RSSRI_ERR_INVALID_ARG;
+  if (collect_stats && o->precision != RSSRI_PREC_FP64 && o->precision != RSSRI_PREC_DF64)
     return RSSRI_ERR_INVALID_ARG;
   if (use_cv && !h->cv_ready) return RSSRI_ERR_NOT_READY;
   if (cudaSetDevice(h->device) != cudaSuccess) return RSSRI_ERR_CUDA;
+  AllocFailScope alloc_test(o->test_fail_alloc);
+  h->test_wait_polls = o->test_wait_polls;
   cudaStream_t s = h->stream;
   const int n = h->n, na = h->n_aux, nt = h->n_tau;
   const int ns = (int)o->n_s;
@@ -1445,6 +1571,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   h->recs.clear();
   h->ev_used = 0;
   h->prof_on = o->profile != 0;
+  RS_CK(cudaMemsetAsync(range_flag(h), 0, 3 * sizeof(int), s));
   RS_CK(cudaEventRecord(h->ev[2], s));
   // ---- buffers
   RS_CK(ensure(h->sig_raw, (size_t)nt * nn * sizeof(double)));
@@ -1522,8 +1649,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
     RS_CK(ensure(h->ut_hl, (size_t)2 * ns * na * sizeof(float2)));
     {
       SPAN(RSSRI_PROF_OTHER, 0.0);
-      RS_CK(to_df64(h->eri3, nn * na, h->eri_hl.as<float2>(), s));
-      RS_CK(to_df64(Ut, 2LL * ns * na, h->ut_hl.as<float2>(), s));
+      RS_CK(to_df64(h->eri3, nn * na, h->eri_hl.as<float2>(), s, range_flag(h)));
+      RS_CK(to_df64(Ut, 2LL * ns * na, h->ut_hl.as<float2>(), s, range_flag(h)));
     }
     SPAN(RSSRI_PROF_FACTOR_GEMM, 2.0 * 2 * ns * (double)nn * na * 1e-9);
     DfGemm g;
@@ -1546,7 +1673,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   }
   if (P > 0 && fac_df64) {
     // theta is +-1, exact as a pair; K_P was split at setup
-    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(theta, 2LL * ns * na, h->ut_hl.as<float2>(), s)); }
+    { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(theta, 2LL * ns * na, h->ut_hl.as<float2>(), s, range_flag(h))); }
     SPAN(RSSRI_PROF_FACTOR_GEMM, 2.0 * 2 * ns * (double)P * na * 1e-9);
     DfGemm g;
     g.M = ns; g.N = P; g.K = na; g.batch = 2;
@@ -1570,7 +1697,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
 
   if (chain_df64) {
     SPAN(RSSRI_PROF_OTHER, 0.0);
-    RS_CK(to_df64(fac, 4LL * ns * nn, h->facHl.as<float2>(), s));
+    RS_CK(to_df64(fac, 4LL * ns * nn, h->facHl.as<float2>(), s, range_flag(h)));
   }
 
   // ---- learned control variate: coefficients, or statistics for training
@@ -1591,7 +1718,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   int *tc_err = h->flags.as<int>() + 4;
   if (bf16) {
     RS_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
-    RS_CK(chain_tc(h, tc_kind, ns, G, Gb, sdd, h->sig_raw.as<double>(), tc_err));
+    RS_CK(chain_tc(h, tc_kind, ns, G, Gb, sdd, h->sig_raw.as<double>(), tc_err,
+                   use_cv ? h->cv_c.as<double>() : nullptr));
   }
   for (int t = 0; t < nt && !bf16; ++t) {
     const double *Gt = G + t * nn, *Gbt = Gb + t * nn;
@@ -1698,6 +1826,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   RS_CK(cudaMemcpyAsync(h->host_res, h->res.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   RS_CK(cudaMemcpyAsync(reinterpret_cast<int *>(h->host_res + 4), tc_err, sizeof(int),
                         cudaMemcpyDeviceToHost, s));
+  RS_CK(cudaMemcpyAsync(reinterpret_cast<int *>(h->host_res + 5), range_flag(h), sizeof(int),
+                        cudaMemcpyDeviceToHost, s));
   RS_CK(cudaEventRecord(h->ev[5], s));
   h->pending = true;
   h->pending_tc = bf16;
@@ -1720,6 +1850,7 @@ int finish_sigma(rssri_handle *h, double *e_corr, double *e_stderr, rssri_stats 
   const double *res = h->host_res;
   const int tc_flag = *reinterpret_cast<const int *>(h->host_res + 4);
   if (h->pending_tc && tc_flag) return RSSRI_ERR_TIMEOUT;
+  if (*reinterpret_cast<const int *>(h->host_res + 5)) return RSSRI_ERR_RANGE;
   h->last_ns = h->pending_ns;
   h->have_sigma = true;
   float t_dd = 0, t_samp = 0;

@@ -145,8 +145,8 @@ template <class T>
 __global__ void __launch_bounds__(256) fold_operands_kernel(
     const float *__restrict__ xy, const float *__restrict__ dc, const float *__restrict__ cl, int ns,
     int n, int ldp, const double *__restrict__ part, double w, double ne, T *__restrict__ a6,
-    T *__restrict__ ct, T *__restrict__ dct, double *__restrict__ e_st) {
-  __shared__ float ta[32][33], tb[32][33];
+    T *__restrict__ ct, T *__restrict__ dct, T *__restrict__ clt, double *__restrict__ e_st) {
+  __shared__ float ta[32][33], tb[32][33], tl32[32][33];
   __shared__ double sums[4];
   const int bi = blockIdx.x, x = blockIdx.y, nt = gridDim.x;
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
       const bool in = i < n && j < n;
       ta[r][tx] = in ? CL[(long long)i * n + j] + DC[(long long)i * n + j] : 0.f;
       tb[r][tx] = in ? DC[(long long)i * n + j] : 0.f;
+      tl32[r][tx] = in ? CL[(long long)i * n + j] : 0.f;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
@@ -193,13 +194,45 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
         const long long o = (long long)i * ldp + j;
         put(&Ct[o], j < n ? (double)ta[tx][r] : 0.0);
         put(&Dt[o], j < n ? (double)tb[tx][r] : 0.0);
+        if (clt) put(&clt[x * mat + o], j < n ? (double)tl32[tx][r] : 0.0);
       }
     }
+    __syncthreads();
   }
   if (bi == 0 && threadIdx.x == 0) {
     const double de = 2.0 * dt * (2.0 * tl + dt) - sums[2] - 2.0 * sums[3];
     e_st[x] += -w * de / ne;
   }
+}
+
+// sig[e] += (1 - c[e]) (mean_x fl[x][e] - sdd[e])
+__global__ void cv_tc_sigma_kernel(const float *__restrict__ fl, int ns, long long nn,
+                                   const double *__restrict__ c, const double *__restrict__ sdd,
+                                   double *__restrict__ sig) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int x = 0; x < ns; ++x) acc += (double)fl[(long long)x * nn + e];
+    sig[e] += (1.0 - c[e]) * (acc / ns - sdd[e]);
+  }
+}
+
+// e_st[x] += -(w / ne) sum_ij (1 - c_ij) fl[x]_ij gb_ji, one block per pair
+__global__ void __launch_bounds__(256) cv_tc_energy_kernel(const float *__restrict__ fl, int n,
+                                                           const double *__restrict__ c,
+                                                           const double *__restrict__ gb,
+                                                           double w, double ne,
+                                                           double *__restrict__ e_st) {
+  const int x = blockIdx.x;
+  const long long nn = (long long)n * n;
+  const float *F = fl + x * nn;
+  double q = 0.0;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    q += (1.0 - c[e]) * (double)F[e] * gb[j * n + i];
+  }
+  q = block_sum_d(q);
+  if (threadIdx.x == 0) e_st[x] += -w * q / ne;
 }
 
 __global__ void reduce_tc_kernel(const float *__restrict__ part, int groups, long long nn,
@@ -240,8 +273,8 @@ cudaError_t chain_matrices(int kind, const double *src, int cnt, int n, int ldp,
 }
 
 cudaError_t fold_tc(int kind, const float *xy, const float *dc, const float *cl, int ns, int n,
-                    int ldp, double w, double ne, void *a6, void *ct, void *dct, double *e_st,
-                    double *part, cudaStream_t s) {
+                    int ldp, double w, double ne, void *a6, void *ct, void *dct, void *clt,
+                    double *e_st, double *part, cudaStream_t s) {
   dim3 grid((n + 31) / 32, ns);
   fold_traces_kernel<<<grid, 256, 0, s>>>(xy, ns, n, part);
   ++launch_counter();
@@ -250,11 +283,25 @@ cudaError_t fold_tc(int kind, const float *xy, const float *dc, const float *cl,
     fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne,
                                               static_cast<__nv_bfloat16 *>(a6),
                                               static_cast<__nv_bfloat16 *>(ct),
-                                              static_cast<__nv_bfloat16 *>(dct), e_st);
+                                              static_cast<__nv_bfloat16 *>(dct),
+                                              static_cast<__nv_bfloat16 *>(clt), e_st);
   else
     fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne,
                                               static_cast<float *>(a6), static_cast<float *>(ct),
-                                              static_cast<float *>(dct), e_st);
+                                              static_cast<float *>(dct),
+                                              static_cast<float *>(clt), e_st);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t cv_tc_apply(const float *fl, int ns, int n, const double *c, const double *sdd,
+                        const double *gb, double w, double ne, double *sig, double *e_st,
+                        cudaStream_t s) {
+  const long long nn = (long long)n * n;
+  cv_tc_sigma_kernel<<<grid_cap(nn, 256), 256, 0, s>>>(fl, ns, nn, c, sdd, sig);
+  ++launch_counter();
+  RS_TRY(cudaGetLastError());
+  cv_tc_energy_kernel<<<ns, 256, 0, s>>>(fl, n, c, gb, w, ne, e_st);
   ++launch_counter();
   return cudaGetLastError();
 }

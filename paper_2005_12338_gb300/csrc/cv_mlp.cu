@@ -7,9 +7,15 @@
 // of the draws it is used with, and per element its variance is smallest at
 // c* = Cov(F, F^L) / Var(F^L).  The network maps features of (i, j, tau) to
 // c = 1 + y and is fitted on an independent training run by minimising
-// sum w (c - c*)^2 / sum w with w = Var(F^L).  fp32 arithmetic, fixed-order
-// reductions.
+// sum w (c - c*)^2 / sum w with w = Var(F^L).  The products of the two hidden
+// 256 x 256 layers, forward and backward, run on the tensor cores with bf16
+// operands and fp32 accumulation (tcgen05); the 10-wide input layer, the
+// 1-wide output layer, activations, loss and Adam are fp32.  Fixed-order
+// reductions throughout.
+#include <cuda_bf16.h>
+
 #include "cv_mlp.cuh"
+#include "tc_gemm.cuh"
 
 namespace rssri {
 namespace {
@@ -114,6 +120,36 @@ __global__ void silu_back_kernel(const float *__restrict__ dA, const float *__re
     const float z = Z[e];
     const float s = 1.f / (1.f + __expf(-z));
     dZ[e] = dA[e] * s * (1.f + z * (1.f - s));
+  }
+}
+
+// dst = bf16(src), elementwise
+__global__ void to_bf16_kernel(const float *__restrict__ src, long long n,
+                               __nv_bfloat16 *__restrict__ dst) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+// dst[c][r] = bf16(src[r][c]) for r < rows, c < cols (dst row stride ldd,
+// columns rows..ldd-1 set to zero), through 32 x 32 shared-memory tiles
+__global__ void transpose_bf16_kernel(const float *__restrict__ src, int rows, int cols,
+                                      long long lds, __nv_bfloat16 *__restrict__ dst,
+                                      long long ldd) {
+  __shared__ float t[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = ty; k < 32; k += blockDim.x >> 5) {
+    const long long r = r0 + k;
+    const int c = c0 + tx;
+    t[k][tx] = (r < rows && c < cols) ? src[r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += blockDim.x >> 5) {
+    const int c = c0 + k;
+    const long long r = r0 + tx;
+    if (c < cols && r < ldd) dst[(long long)c * ldd + r] = __float2bfloat16_rn(t[tx][k]);
   }
 }
 
@@ -438,7 +474,126 @@ constexpr long long O_W0 = 0, O_B0 = O_W0 + CV_HIDDEN * CV_NFEAT, O_W1 = O_B0 + 
 static_assert(O_B3 + 1 == CV_NPARAM, "parameter layout");
 }  // namespace
 
-size_t cv_act_floats(int m) { return (size_t)m * (6 * CV_HIDDEN + 4); }
+// Split of a contraction over the m rows into g chunks of kc (a multiple of
+// 64): the tensor-core weight-gradient products take the chunks as batch
+// entries of strided views of one transposed buffer of row stride g kc.
+void tc_split(int m, int *g, int *kc) {
+  int gg = std::max(1, std::min(8, m / 2048));
+  int k = (ceil_div(m, gg) + 63) / 64 * 64;
+  *g = gg;
+  *kc = k;
+}
+
+long long tc_ldt(int m) {
+  int g, kc;
+  tc_split(m, &g, &kc);
+  return (long long)g * kc;
+}
+
+// act layout (floats): Z0 A0 Z1 A1 Z2 A2 [m][256] fp32, y [m], dy [m], 2 spare,
+// then bf16: H0, H1 [m][256] (bf16 activations / gradient rows), T0, T1
+// [256][ldt] (transposes for the weight gradients)
+size_t cv_act_floats(int m) {
+  // tc_ldt(m) <= m + 8 * 63: sized with m + 512 so that the size grows with m
+  return (size_t)m * (6 * CV_HIDDEN + 4) + (size_t)m * CV_HIDDEN +
+         (size_t)CV_HIDDEN * ((size_t)m + 512);
+}
+
+// work layout (floats): bf16 W1, W2, W1^T, W2^T (4 x 256 x 256), the weight
+// gradient partials [8][256][256] fp32, then the fp32 products' split-K scratch
+size_t cv_tc_work_floats() {
+  return 2LL * CV_HIDDEN * CV_HIDDEN + 8LL * CV_HIDDEN * CV_HIDDEN;
+}
+
+namespace {
+struct Bf16Bufs {
+  __nv_bfloat16 *h0, *h1, *t0, *t1, *w[2], *wt[2];
+  float *part;
+  float *work;  // fp32 split-K scratch
+  long long ldt;
+};
+
+Bf16Bufs bf16_bufs(const float *params, float *act, float *work, int m) {
+  const int H = CV_HIDDEN;
+  Bf16Bufs b;
+  float *base = act + (long long)m * (6 * H + 4);
+  b.h0 = reinterpret_cast<__nv_bfloat16 *>(base);
+  b.h1 = b.h0 + (long long)m * H;
+  b.ldt = tc_ldt(m);
+  b.t0 = b.h1 + (long long)m * H;
+  b.t1 = b.t0 + (long long)H * b.ldt;
+  __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(work);
+  b.w[0] = wb;
+  b.w[1] = wb + H * H;
+  b.wt[0] = wb + 2 * H * H;
+  b.wt[1] = wb + 3 * H * H;
+  b.part = work + 2 * H * H;
+  b.work = b.part + 8 * H * H;
+  (void)params;
+  return b;
+}
+
+TcOperand tco(const void *p, long long ld, long long sb, int rows) {
+  TcOperand t;
+  t.ptr = p;
+  t.ld = ld;
+  t.sb = sb;
+  t.rows = rows;
+  return t;
+}
+
+// C [M][N] fp32 = A [M][K] B^T, A and B bf16 K-contiguous (tensor cores)
+cudaError_t tc_mm(const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                  int M, int N, int K, float *C, cudaStream_t s) {
+  TcGemm g;
+  g.kind = TC_BF16;
+  g.M = M;
+  g.N = N;
+  g.K[0] = K;
+  g.A[0] = tco(A, lda, 0, M);
+  g.B[0] = tco(B, ldb, 0, N);
+  g.c32 = C;
+  return tc_gemm(g, s);
+}
+
+// dW [N][M]... : out[o][i] = sum_r At[o][r] Bt[i][r] over r < m, split into g
+// chunks (batch entries of strided views), partials reduced in order
+cudaError_t tc_wgrad(const __nv_bfloat16 *At, const __nv_bfloat16 *Bt, long long ldt, int m,
+                     float *part, float *out, cudaStream_t s) {
+  const int H = CV_HIDDEN;
+  int g, kc;
+  tc_split(m, &g, &kc);
+  TcGemm t;
+  t.kind = TC_BF16;
+  t.M = H;
+  t.N = H;
+  t.batch = g;
+  t.bpc = 1;
+  t.K[0] = kc;
+  t.A[0] = tco(At, ldt, kc, H);
+  t.B[0] = tco(Bt, ldt, kc, H);
+  t.c32 = part;
+  RS_TRY(tc_gemm(t, s));
+  sreduce_kernel<<<grid_cap((long long)H * H, 256), 256, 0, s>>>(part, g, H, H, out, H, 1.f);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t to_bf16(const float *src, long long n, __nv_bfloat16 *dst, cudaStream_t s) {
+  to_bf16_kernel<<<grid_cap(n, 256), 256, 0, s>>>(src, n, dst);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+// dst [cols][ldd] = bf16 src[rows][cols]^T (zero beyond rows)
+cudaError_t transpose_bf16(const float *src, int rows, int cols, long long lds,
+                           __nv_bfloat16 *dst, long long ldd, cudaStream_t s) {
+  dim3 grid((unsigned)((ldd + 31) / 32), (unsigned)ceil_div(cols, 32));
+  transpose_bf16_kernel<<<grid, 256, 0, s>>>(src, rows, cols, lds, dst, ldd);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t cv_forward(const float *params, const float *X, int m, float *act, float *work,
                        cudaStream_t s) {
@@ -446,19 +601,26 @@ cudaError_t cv_forward(const float *params, const float *X, int m, float *act, f
   float *Z0 = act, *A0 = Z0 + (long long)m * H, *Z1 = A0 + (long long)m * H,
         *A1 = Z1 + (long long)m * H, *Z2 = A1 + (long long)m * H, *A2 = Z2 + (long long)m * H,
         *y = A2 + (long long)m * H;
-  const float *in = X;
-  int kin = CV_NFEAT;
-  const long long ow[3] = {O_W0, O_W1, O_W2}, ob[3] = {O_B0, O_B1, O_B2};
-  float *Zs[3] = {Z0, Z1, Z2}, *As[3] = {A0, A1, A2};
-  for (int l = 0; l < 3; ++l) {
-    RS_TRY(sgemm(m, H, kin, in, kin, 0, params + ow[l], kin, 1, Zs[l], H, 1.f, 0.f, work, s));
-    bias_silu_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(Zs[l], params + ob[l], m, H,
-                                                                      As[l]);
-    RS_L();
-    in = As[l];
-    kin = H;
-  }
-  RS_TRY(sgemm(m, 1, H, A2, H, 0, params + O_W3, H, 1, y, 1, 1.f, 0.f, work, s));
+  Bf16Bufs b = bf16_bufs(params, act, work, m);
+  // bf16 copies of the hidden weights W1, W2 (the B operands: rows = outputs)
+  RS_TRY(to_bf16(params + O_W1, (long long)H * H, b.w[0], s));
+  RS_TRY(to_bf16(params + O_W2, (long long)H * H, b.w[1], s));
+  // layer 0 (10 inputs): fp32
+  RS_TRY(sgemm(m, H, CV_NFEAT, X, CV_NFEAT, 0, params + O_W0, CV_NFEAT, 1, Z0, H, 1.f, 0.f,
+               b.work, s));
+  bias_silu_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(Z0, params + O_B0, m, H, A0);
+  RS_L();
+  // layers 1, 2: tensor cores on bf16 activations
+  RS_TRY(to_bf16(A0, (long long)m * H, b.h0, s));
+  RS_TRY(tc_mm(b.h0, H, b.w[0], H, m, H, H, Z1, s));
+  bias_silu_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(Z1, params + O_B1, m, H, A1);
+  RS_L();
+  RS_TRY(to_bf16(A1, (long long)m * H, b.h1, s));
+  RS_TRY(tc_mm(b.h1, H, b.w[1], H, m, H, H, Z2, s));
+  bias_silu_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(Z2, params + O_B2, m, H, A2);
+  RS_L();
+  // output layer (1 output): fp32
+  RS_TRY(sgemm(m, 1, H, A2, H, 0, params + O_W3, H, 1, y, 1, 1.f, 0.f, b.work, s));
   bias_silu_kernel<<<grid_cap(m, 256), 256, 0, s>>>(y, params + O_B3, m, 1, nullptr);
   RS_L();
   return cudaSuccess;
@@ -471,38 +633,44 @@ cudaError_t cv_backward(const float *params, const float *X, int m, const float 
   float *Z0 = act, *A0 = Z0 + (long long)m * H, *Z1 = A0 + (long long)m * H,
         *A1 = Z1 + (long long)m * H, *Z2 = A1 + (long long)m * H, *A2 = Z2 + (long long)m * H,
         *y = A2 + (long long)m * H, *dy = y + m;
+  Bf16Bufs b = bf16_bufs(params, act, work, m);
+  // bf16 W1^T, W2^T (the B operands of dA = dZ W: rows = inputs)
+  RS_TRY(transpose_bf16(params + O_W1, H, H, H, b.wt[0], H, s));
+  RS_TRY(transpose_bf16(params + O_W2, H, H, H, b.wt[1], H, s));
   loss_kernel<<<1, 1024, 0, s>>>(y, target, weight, m, dy, loss);
   RS_L();
-  // layer 3: dW3 = dy^T A2, db3 = sum dy, dA2 = dy W3
-  RS_TRY(sgemm(1, H, m, dy, 1, 1, A2, H, 0, grad + O_W3, H, 1.f, 0.f, work, s));
+  // layer 3: dW3 = dy^T A2, db3 = sum dy, dA2 = dy W3 (fp32)
+  RS_TRY(sgemm(1, H, m, dy, 1, 1, A2, H, 0, grad + O_W3, H, 1.f, 0.f, b.work, s));
   colsum_kernel<<<1, 32, 0, s>>>(dy, m, 1, grad + O_B3);
   RS_L();
-  // dZ2 = (dy W3) * silu'(Z2): dy W3 goes into A2's buffer (A2 is no longer
-  // needed), dZ2 over Z2; the layers below reuse their buffers the same way
-  RS_TRY(sgemm(m, H, 1, dy, 1, 0, params + O_W3, H, 0, A2, H, 1.f, 0.f, work, s));
+  RS_TRY(sgemm(m, H, 1, dy, 1, 0, params + O_W3, H, 0, A2, H, 1.f, 0.f, b.work, s));
   silu_back_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(A2, Z2, (long long)m * H, Z2);
   RS_L();  // Z2 now holds dZ2
-  float *dZs[3] = {Z0, Z1, Z2};
-  float *Aprev[3] = {nullptr, A0, A1};
-  const long long ow[3] = {O_W0, O_W1, O_W2}, ob[3] = {O_B0, O_B1, O_B2};
-  for (int l = 2; l >= 0; --l) {
-    const float *in = l == 0 ? X : Aprev[l];
-    const int kin = l == 0 ? CV_NFEAT : H;
-    // dW_l = dZ_l^T in, db_l = colsum dZ_l
-    RS_TRY(sgemm(H, kin, m, dZs[l], H, 1, in, kin, 0, grad + ow[l], kin, 1.f, 0.f, work, s));
-    colsum_kernel<<<ceil_div(H, 128), 128, 0, s>>>(dZs[l], m, H, grad + ob[l]);
-    RS_L();
-    if (l > 0) {
-      // dA_{l-1} = dZ_l W_l, written over A_{l-1} (no longer needed), then
-      // dZ_{l-1} = dA_{l-1} * silu'(Z_{l-1}) written over Z_{l-1}
-      float *Ap = Aprev[l];
-      RS_TRY(sgemm(m, H, H, dZs[l], H, 0, params + ow[l], H, 0, Ap, H, 1.f, 0.f, work, s));
-      silu_back_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(Ap, dZs[l - 1],
-                                                                        (long long)m * H,
-                                                                        dZs[l - 1]);
-      RS_L();
-    }
-  }
+  // layer 2: dW2 = dZ2^T A1, db2; dA1 = dZ2 W2; dZ1 = dA1 silu'(Z1)
+  RS_TRY(transpose_bf16(Z2, m, H, H, b.t0, b.ldt, s));
+  RS_TRY(transpose_bf16(A1, m, H, H, b.t1, b.ldt, s));
+  RS_TRY(tc_wgrad(b.t0, b.t1, b.ldt, m, b.part, grad + O_W2, s));
+  colsum_kernel<<<ceil_div(H, 128), 128, 0, s>>>(Z2, m, H, grad + O_B2);
+  RS_L();
+  RS_TRY(to_bf16(Z2, (long long)m * H, b.h1, s));
+  RS_TRY(tc_mm(b.h1, H, b.wt[1], H, m, H, H, A1, s));
+  silu_back_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(A1, Z1, (long long)m * H, Z1);
+  RS_L();  // Z1 now holds dZ1
+  // layer 1: dW1 = dZ1^T A0, db1; dA0 = dZ1 W1; dZ0 = dA0 silu'(Z0)
+  RS_TRY(transpose_bf16(Z1, m, H, H, b.t0, b.ldt, s));
+  RS_TRY(transpose_bf16(A0, m, H, H, b.t1, b.ldt, s));
+  RS_TRY(tc_wgrad(b.t0, b.t1, b.ldt, m, b.part, grad + O_W1, s));
+  colsum_kernel<<<ceil_div(H, 128), 128, 0, s>>>(Z1, m, H, grad + O_B1);
+  RS_L();
+  RS_TRY(to_bf16(Z1, (long long)m * H, b.h0, s));
+  RS_TRY(tc_mm(b.h0, H, b.wt[0], H, m, H, H, A0, s));
+  silu_back_kernel<<<grid_cap((long long)m * H, 256), 256, 0, s>>>(A0, Z0, (long long)m * H, Z0);
+  RS_L();  // Z0 now holds dZ0
+  // layer 0 (10 inputs): dW0 = dZ0^T X, db0 (fp32)
+  RS_TRY(sgemm(H, CV_NFEAT, m, Z0, H, 1, X, CV_NFEAT, 0, grad + O_W0, CV_NFEAT, 1.f, 0.f, b.work,
+               s));
+  colsum_kernel<<<ceil_div(H, 128), 128, 0, s>>>(Z0, m, H, grad + O_B0);
+  RS_L();
   return cudaSuccess;
 }
 

@@ -19,8 +19,12 @@ cudaError_t sgemm(int M, int N, int K, const float *A, long long lda, int ta, co
                   long long ldb, int tb, float *C, long long ldc, float alpha, float beta,
                   float *work, cudaStream_t s);
 
-// Activations of m rows: [Z0 A0 Z1 A1 Z2 A2] (m x 256 each), y (m), dy (m).
+// Activations of m rows: [Z0 A0 Z1 A1 Z2 A2] (m x 256 each), y (m), dy (m),
+// then the bf16 operands of the tensor-core hidden layers.
 size_t cv_act_floats(int m);
+// Floats of `work` that the tensor-core hidden layers use (bf16 weights and
+// weight-gradient partials); the fp32 products' split-K scratch follows them.
+size_t cv_tc_work_floats();
 // Forward: y = MLP(X) - 1 in act (see cv_act_floats), X [m][10].
 cudaError_t cv_forward(const float *params, const float *X, int m, float *act, float *work,
                        cudaStream_t s);

@@ -17,13 +17,77 @@ int grid_cap(long long work, int threads) {
   return (int)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
 }
 
-__global__ void to_df64_kernel(const double *__restrict__ x, long long len, float2 *__restrict__ y) {
+// range[0] |= 1 when the largest magnitude of x lies outside [2^-40, 2^40]
+// (zero arrays pass): the block maxima of the exponent field go to range[1],
+// and the last block to finish (range[2] counts them) checks and resets both.
+__global__ void to_df64_kernel(const double *__restrict__ x, long long len, float2 *__restrict__ y,
+                               int *__restrict__ range) {
+  int mx = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
        e += (long long)gridDim.x * blockDim.x) {
     const double v = x[e];
     const float hi = __double2float_rn(v);
     y[e] = make_float2(hi, __double2float_rn(v - (double)hi));
+    mx = max(mx, (int)((__double_as_longlong(v) >> 52) & 0x7FF));
   }
+  if (!range) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ int smax;
+  __shared__ bool last;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicMax(&smax, mx);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&range[1], smax);
+    __threadfence();
+    last = atomicAdd(&range[2], 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const int m = atomicExch(&range[1], 0);
+    // the exponent field of 2^k is 1023 + k
+    if (m != 0 && (m < 1023 - 40 || m > 1023 + 40)) atomicOr(&range[0], 1);
+    atomicExch(&range[2], 0);
+  }
+}
+
+// One block per segment c of len values: e[c] = the exponent of the segment's
+// largest magnitude (2^e <= max < 2^(e+1); 0 for a zero segment) and
+// y = pairs of x 2^-e (an exact power-of-two scaling).
+__global__ void __launch_bounds__(1024) to_df64_scaled_kernel(const double *__restrict__ x,
+                                                              long long len,
+                                                              float2 *__restrict__ y,
+                                                              int *__restrict__ e_out) {
+  const long long base = (long long)blockIdx.x * len;
+  int mx = 0;
+  for (long long i = threadIdx.x; i < len; i += blockDim.x)
+    mx = max(mx, (int)((__double_as_longlong(x[base + i]) >> 52) & 0x7FF));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ int smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicMax(&smax, mx);
+  __syncthreads();
+  const int e = smax ? smax - 1023 : 0;
+  if (threadIdx.x == 0) e_out[blockIdx.x] = e;
+  for (long long i = threadIdx.x; i < len; i += blockDim.x) {
+    const double v = scalbn(x[base + i], -e);
+    const float hi = __double2float_rn(v);
+    y[base + i] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
+// x *= 2^(mult e[0])
+__global__ void scale_pow2_kernel(double *__restrict__ x, long long len,
+                                  const int *__restrict__ e, int mult) {
+  const int k = mult * e[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = scalbn(x[i], k);
 }
 
 // ------------------------------------------------- double-float products --
@@ -242,9 +306,24 @@ __global__ void gather_rows_f2_kernel(const float2 *__restrict__ src, const int 
 }
 }  // namespace
 
-cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s) {
+cudaError_t to_df64_scaled(const double *x, int segments, long long len, float2 *y, int *e,
+                           cudaStream_t s) {
+  if (segments <= 0 || len <= 0) return cudaSuccess;
+  to_df64_scaled_kernel<<<segments, 1024, 0, s>>>(x, len, y, e);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t scale_pow2(double *x, long long len, const int *e, int mult, cudaStream_t s) {
   if (len <= 0) return cudaSuccess;
-  to_df64_kernel<<<grid_cap(len, 256), 256, 0, s>>>(x, len, y);
+  scale_pow2_kernel<<<grid_cap(len, 256), 256, 0, s>>>(x, len, e, mult);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s, int *range) {
+  if (len <= 0) return cudaSuccess;
+  to_df64_kernel<<<grid_cap(len, 256), 256, 0, s>>>(x, len, y, range);
   ++launch_counter();
   return cudaGetLastError();
 }

@@ -5,8 +5,20 @@
 
 namespace rssri {
 
-// y[e] = (hi, lo) with hi = fl32(x[e]), lo = fl32(x[e] - hi).
-cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s);
+// y[e] = (hi, lo) with hi = fl32(x[e]), lo = fl32(x[e] - hi).  A pair keeps
+// ~48 bits only inside fp32's exponent range (normal numbers from 2^-126, and
+// products whose error terms stay normal), so when range is given (3 ints,
+// range[1..2] zero before the first call) range[0] |= 1 if the largest
+// magnitude of x lies outside [2^-40, 2^40].
+cudaError_t to_df64(const double *x, long long len, float2 *y, cudaStream_t s,
+                    int *range = nullptr);
+// Per segment c of len values: e[c] such that the largest magnitude lies in
+// [2^e, 2^(e+1)), and y = pairs of x 2^-e (exact scaling, so that the pairs
+// sit in the middle of fp32's exponent range whatever x's magnitude).
+cudaError_t to_df64_scaled(const double *x, int segments, long long len, float2 *y, int *e,
+                           cudaStream_t s);
+// x *= 2^(mult e[0]), e read on the device.
+cudaError_t scale_pow2(double *x, long long len, const int *e, int mult, cudaStream_t s);
 // T[m][q][j] = sum_{a in row m} sum_{b in row j} D[a*P+b] * At[(col[a]*n+col[b])*naux+q],
 // D and At in double-float, T in fp64.
 cudaError_t dd_exchange_spmm_df64(const int *rowptr, const int *pcol, const float2 *D, int P,

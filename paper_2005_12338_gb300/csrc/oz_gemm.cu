@@ -2,9 +2,12 @@
 // error-free digit slicing; see oz_gemm.cuh for the number scheme.
 //
 // Kernel layout (one 128 x 128 output tile per CTA, 18 warps):
-//   warp 0 lane 0  TMA producer: per K step of 16, the six digit tiles of A
-//                  and of B (128 rows x 32 bytes each, 32-byte swizzle) into a
-//                  ring of shared-memory stages;
+//   warp 0 lane 0  TMA producer: per K step of 16, the digits of A and of B
+//                  into a ring of shared-memory stages, per operand digits
+//                  0-3 as one 128 x 128-byte tile (128-byte swizzle) and
+//                  digits 4-5 as one 128 x 64-byte tile (64-byte swizzle):
+//                  the digit layout interleaves the digits of each block of
+//                  16 columns, so every TMA row is 128 or 64 bytes wide;
 //   warp 1 lane 0  MMA issuer: per K step, the 21 digit products p + q <= 5
 //                  (tcgen05.mma kind::f16, M = N = 128, K = 16) into four fp32
 //                  accumulators in tensor memory, one per level p + q = 0, 1,
@@ -35,8 +38,10 @@ namespace rssri {
 namespace {
 
 constexpr int BM = 128, BN = 128, KS = 16;   // tile rows, columns; K per step (32 bytes of bf16)
-constexpr int TILE = BM * KS * 2;            // bytes of one digit tile
-constexpr int STAGE = OZ_S * 2 * TILE;       // A and B digits of one K step
+constexpr int TILE0 = BM * 64 * 2;           // digits 0-3 of one K step: 128 rows x 128 bytes
+constexpr int TILE1 = BM * 32 * 2;           // digits 4-5: 128 rows x 64 bytes
+constexpr int OPB = TILE0 + TILE1;           // one operand's digits of one K step
+constexpr int STAGE = 2 * OPB;               // A and B digits of one K step
 constexpr int STAGES = 4;
 constexpr int CHUNK = 16;                    // K steps between drains (256 terms)
 constexpr int EPI = 16;                      // drain warps (4 per tensor-memory lane quarter)
@@ -65,7 +70,7 @@ __device__ __noinline__ void check_fail(int code, int line, long long idx) {
 #endif
 
 struct OzParams {
-  CUtensorMap ta, tb;
+  CUtensorMap ta0, ta1, tb0, tb1;  // digits 0-3 and 4-5 of A and B
   int M, N;          // dense: C rows / columns per batch; exchange: n, n_aux
   int kst;           // K steps per CTA
   int ksplit;        // dense: K splits (blockIdx.z = batch * ksplit + split)
@@ -75,9 +80,10 @@ struct OzParams {
   double alpha;
   double *C;
   long long ldc, sC;
-  int bk, nl16, jtiles;  // exchange geometry
+  int bk, nl16, jtiles, lb0;  // exchange geometry
   int *err;
   long long ccap, efa_cap, efb_cap;  // bounds of C and the exponent arrays (checks)
+  int wait_polls;  // 0: normal; > 0: test mode (see OzGemm)
 };
 
 // ------------------------------------------------------------ PTX helpers --
@@ -105,14 +111,26 @@ __device__ __forceinline__ uint32_t bar_try(uint64_t *b, uint32_t parity) {
       : "memory");
   return ok;
 }
-// Bounded wait: gives up after ~2^22 polls, or at once when another thread of
-// the launch has already flagged an error.
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, int *err, int code) {
-  for (int i = 0; i < (1 << 22); ++i) {
+// Bounded wait: gives up after ~2^22 polls (`polls` when positive), or at
+// once when another thread of the launch has already flagged an error.
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, int *err, int code,
+                                         int polls = 0) {
+  const int lim = polls > 0 ? polls : (1 << 22);
+  for (int i = 0; i < lim; ++i) {
     if (bar_try(b, parity)) return true;
     if ((i & 1023) == 1023 && err && *(volatile int *)err) return false;
   }
   if (err) atomicExch(err, code);
+  return false;
+}
+// Test mode: the producer waits (bounded) until a consumer has flagged its
+// expired wait, and then issues nothing.  Returns true when it may proceed.
+__device__ __forceinline__ bool test_mode_gate(int polls, int *err) {
+  if (polls <= 0) return true;
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (err && *(volatile int *)err) return false;
+    __nanosleep(64);
+  }
   return false;
 }
 __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *m, uint64_t *bar, int x,
@@ -123,15 +141,22 @@ __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *m, uint6
       "l"(m), "r"(s_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
       : "memory");
 }
-// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, rows of
-// 32 bytes in groups of 8 (256 bytes between groups).
-__device__ __forceinline__ uint64_t smem_desc32(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand in rows of 128 bytes
+// (128-byte swizzle, layout code 2, 1024 bytes between groups of 8 rows) or
+// of 64 bytes (64-byte swizzle, code 4, 512 bytes between groups).
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr, uint32_t sbo, uint32_t layout) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)(sbo >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)6 << 61;
+  d |= (uint64_t)layout << 61;
   return d;
+}
+// Digit p of an operand's stage slot at `base`: its 16 columns start 32 p
+// bytes into the 128-byte rows (p < 4) or 32 (p - 4) into the 64-byte rows.
+__device__ __forceinline__ uint64_t digit_desc(uint32_t base, int p) {
+  return p < 4 ? smem_desc_sw(base + 32 * p, 1024, 2)
+               : smem_desc_sw(base + TILE0 + 32 * (p - 4), 512, 4);
 }
 // Instruction descriptor: D fp32, A and B bf16, both K-major, M = N = 128.
 __device__ __forceinline__ uint32_t instr_desc_bf16() {
@@ -203,6 +228,41 @@ __device__ __forceinline__ double f32_scaled(float f, int E) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)e64 << 52) | mant));
 }
 
+// (hi + lo) 2^E as fp64 with integer operations only (the fp64 pipe runs at
+// 1/64 of the fp32 rate here): hi's 53-bit significand plus lo in units of
+// hi's fp64 ulp, renormalised by at most one bit.  (hi, lo) comes from a
+// TwoSum, so |lo| <= ulp_f32(hi) / 2 and lo moves the significand by less
+// than 2^29 units; lo's bits below one unit are dropped and a renormalising
+// right shift truncates, so the result is within 2 ulp of the exact sum,
+// far inside the 2^-48 rounding of the running totals.  Tiny, huge,
+// non-finite or out-of-pattern operands take one fp64 add instead.
+__device__ __forceinline__ double df_to_f64(float hi, float lo, int E) {
+  const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const int eh = (int)((uh >> 23) & 0xFF), el = (int)((ul >> 23) & 0xFF);
+  const int e64 = eh - 127 + 1023 + E;
+  const int sh = el - eh + 29;  // lo's unit shift relative to hi's fp64 ulp
+  const bool lo_zero = (ul << 1) == 0;
+  if (eh < 64 || eh == 255 || e64 < 2 || e64 > 2045 || (!lo_zero && (el == 0 || sh > 6)))
+    return f32_scaled(hi, E) + f32_scaled(lo, E);
+  long long S = (long long)((1u << 23) | (uh & 0x7FFFFFu)) << 29;
+  if (!lo_zero) {
+    const long long ml = (long long)((1u << 23) | (ul & 0x7FFFFFu));
+    const long long u = sh >= 0 ? ml << sh : (sh > -40 ? ml >> -sh : 0LL);
+    S += ((uh ^ ul) >> 31) ? -u : u;
+  }
+  int e = e64;
+  if (S >= (1LL << 53)) {
+    S >>= 1;
+    ++e;
+  } else if (S < (1LL << 52)) {
+    S <<= 1;
+    --e;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(uh >> 31) << 63) |
+                                          ((unsigned long long)e << 52) |
+                                          ((unsigned long long)S & 0xFFFFFFFFFFFFFull)));
+}
+
 __device__ __forceinline__ int row_scale(int ef) { return max(ef, 1) - 1022; }
 
 // ------------------------------------------------------------- the GEMM ----
@@ -256,32 +316,35 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
         mt = rt / p.jtiles;
         jt = rt % p.jtiles;
       }
-      for (int st = 0; st < kst; ++st) {
+      const bool go = test_mode_gate(p.wait_polls, p.err);
+      for (int st = 0; st < kst && go; ++st) {
         const int s = st % STAGES;
-        if (st >= STAGES && !bar_wait(&empty[s], ((st / STAGES) - 1) & 1, p.err, 1)) break;
+        if (st >= STAGES && !bar_wait(&empty[s], ((st / STAGES) - 1) & 1, p.err, 1, p.wait_polls))
+          break;
         bar_expect(&full[s], STAGE);
-        uint8_t *sa = smem + s * STAGE, *sb = sa + OZ_S * TILE;
-        int ax, ay, az, bx, by, bz;
+        uint8_t *sa = smem + s * STAGE, *sb = sa + OPB;
+        // coordinates (inner, 16-column block, ...): dense (0, kb, row, batch);
+        // exchange A (0, st, 0, tile), B (0, l block, k, q)
+        int ay, az, by, bz, bw;
         if (MODE == 0) {
-          ax = bx = (split * kst + st) * KS;
-          ay = m0;
-          az = zb;
-          by = n0;
-          bz = p.bshared ? 0 : zb;
+          ay = by = split * kst + st;
+          az = m0;
+          bz = n0;
+          bw = p.bshared ? 0 : zb;
+          tma_load4(sa, &p.ta0, &full[s], 0, ay, az, zb);
+          tma_load4(sa + TILE0, &p.ta1, &full[s], 0, ay, az, zb);
         } else {
           const int kidx = st / p.nl16, ls = st % p.nl16;
-          ax = st * KS;
-          ay = 0;
-          az = rt;
-          bx = ((jt * 16 - p.bk) & ~7) + ls * KS;  // l (rounded down to 8: 16-byte TMA start)
-          by = mt * 8 - p.bk + kidx;               // k
-          bz = n0;                                 // q
+          ay = st;
+          az = 0;
+          by = jt + p.lb0 + ls;         // block of l' (may lie outside: zeros)
+          bz = mt * 8 - p.bk + kidx;    // k (may lie outside: zeros)
+          bw = n0;                      // q
+          tma_load4(sa, &p.ta0, &full[s], 0, ay, az, rt);
+          tma_load4(sa + TILE0, &p.ta1, &full[s], 0, ay, az, rt);
         }
-#pragma unroll
-        for (int d = 0; d < OZ_S; ++d) {
-          tma_load4(sa + d * TILE, &p.ta, &full[s], ax, ay, az, d);
-          tma_load4(sb + d * TILE, &p.tb, &full[s], bx, by, bz, d);
-        }
+        tma_load4(sb, &p.tb0, &full[s], 0, by, bz, bw);
+        tma_load4(sb + TILE0, &p.tb1, &full[s], 0, by, bz, bw);
       }
     }
   } else if (warp == 1) {
@@ -292,18 +355,18 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
       for (int st = 0; st < kst && ok; ++st) {
         const int s = st % STAGES, cs = st % CHUNK;
         if (cs == 0 && st > 0) {
-          if (!bar_wait(acce, ((st / CHUNK) - 1) & 1, p.err, 2)) {
+          if (!bar_wait(acce, ((st / CHUNK) - 1) & 1, p.err, 2, p.wait_polls)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
         }
-        if (!bar_wait(&full[s], (st / STAGES) & 1, p.err, 3)) {
+        if (!bar_wait(&full[s], (st / STAGES) & 1, p.err, 3, p.wait_polls)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t base_a = s_u32(smem + s * STAGE), base_b = base_a + OZ_S * TILE;
+        const uint32_t base_a = s_u32(smem + s * STAGE), base_b = base_a + OPB;
 #pragma unroll
         for (int pa = 0; pa < OZ_S; ++pa)
 #pragma unroll
@@ -311,8 +374,8 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
             const int acc = min(pa + pb, 3);
             // the first product into each accumulator in a chunk overwrites it
             const uint32_t en = (cs > 0 || !(pa == 0 && pb <= 3)) ? 1u : 0u;
-            mma_bf16(tmem + (uint32_t)(acc * 128), smem_desc32(base_a + pa * TILE),
-                     smem_desc32(base_b + pb * TILE), idesc, en);
+            mma_bf16(tmem + (uint32_t)(acc * 128), digit_desc(base_a, pa),
+                     digit_desc(base_b, pb), idesc, en);
           }
         mma_commit(&empty[s]);
         if (cs == CHUNK - 1 || st == kst - 1) mma_commit(accf);
@@ -331,7 +394,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
     for (int c = 0; c < DC; ++c) hi[c] = lo[c] = 0.f;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
-      if (!bar_wait(accf, c & 1, p.err, 4) || (p.err && *(volatile int *)p.err)) {
+      if (!bar_wait(accf, c & 1, p.err, 4, p.wait_polls) || (p.err && *(volatile int *)p.err)) {
         ok = false;
         break;
       }
@@ -377,20 +440,24 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
       const int ncol = p.N;
       if (valid) {
         const int j0 = n0 + cq * DC;
+        // alpha = +-1 (every product of the block) flips the sign bit only;
+        // any other alpha takes one fp64 multiply per output
         const bool neg = p.alpha == -1.0, plain = p.alpha == 1.0 || neg;
+        const unsigned long long sgn = neg ? (1ull << 63) : 0ull;
+        const long long eb_off = MODE == 0 && !p.bshared ? zb * p.efb_bs : 0;
 #pragma unroll
         for (int c = 0; c < DC; ++c) {
           const int j = j0 + c;
           if (j < ncol) {
-            const long long ie = (MODE == 0 && !p.bshared ? zb * p.efb_bs : 0) + j;
+            const long long ie = eb_off + j;
             if (!OZ_IN(ie, p.efb_cap, 12)) continue;
             if (!OZ_IN((long long)(dst + j - p.C), p.ccap, 13)) continue;
-            const int eb = row_scale(p.efb[ie]);
-            const int E = ea + eb - 14;
-            double v = f32_scaled(hi[c], E) + f32_scaled(lo[c], E);
-            if (neg) v = -v;
-            else if (!plain) v *= p.alpha;
-            dst[j] = v;
+            const int E = ea + row_scale(p.efb[ie]) - 14;
+            const double v = df_to_f64(hi[c], lo[c], E);
+            if (plain)
+              dst[j] = __longlong_as_double((long long)((unsigned long long)__double_as_longlong(v) ^ sgn));
+            else
+              dst[j] = v * p.alpha;
           }
         }
       }
@@ -427,7 +494,8 @@ constexpr int SR = 32, SK = 64;
 // Element (b, r, kk) of the view, kk = k1 k2pad + k2 given as (k1, k2).
 __device__ __forceinline__ double view_at(const OzView &v, int b, long long r, long long k1,
                                           long long k2) {
-  if (k2 >= v.k2n) return 0.0;
+  k2 -= v.k2off;
+  if (k2 < 0 || k2 >= v.k2n) return 0.0;
   const long long o = b * v.bs + r * v.rs + k1 * v.cs1 + k2 * v.cs2;
 #ifdef RSSRI_CHECKS
   if (v.xlen > 0 && (o < 0 || o >= v.xlen)) {
@@ -446,31 +514,35 @@ __device__ __forceinline__ double view_at(const OzView &v, int b, long long r, l
   return v.x[o];
 }
 
-// Load a 32 x 64 tile of the view into s[r][k] (zeros outside).
+// Load a 32 x 64 tile of the view into s[r][k] (zeros outside); blockDim.x
+// == 256, eight values per thread, all eight loads issued before the stores.
+constexpr int SLICE_THREADS = 256, SLICE_PER = SR * SK / SLICE_THREADS;
 __device__ __forceinline__ void load_tile(const OzView &v, int b, long long r0, long long k0,
                                           int rows, long long K, double (*s)[SK + 1]) {
   const bool rmaj = v.rs == 1;
   const long long k1_0 = k0 / v.k2pad, k2_0 = k0 - k1_0 * v.k2pad;  // once per tile
-  for (int idx = threadIdx.x; idx < SR * SK; idx += blockDim.x) {
-    int r, k;
-    if (rmaj) {
-      r = idx % SR;
-      k = idx / SR;
-    } else {
-      k = idx % SK;
-      r = idx / SK;
-    }
+  double val[SLICE_PER];
+#pragma unroll
+  for (int i = 0; i < SLICE_PER; ++i) {
+    const int idx = threadIdx.x + i * SLICE_THREADS;
+    const int r = rmaj ? idx % SR : idx / SK, k = rmaj ? idx / SR : idx % SK;
     const long long rr = r0 + r;
-    double val = 0.0;
+    val[i] = 0.0;
     if (rr < rows && k0 + k < K) {
       long long k1 = k1_0, k2 = k2_0 + k;
-      while (k2 >= v.k2pad) {
-        k2 -= v.k2pad;
-        ++k1;
+      if (k2 >= v.k2pad) {
+        const long long q = k2 / v.k2pad;
+        k1 += q;
+        k2 -= q * v.k2pad;
       }
-      val = view_at(v, b, rr, k1, k2);
+      val[i] = view_at(v, b, rr, k1, k2);
     }
-    s[r][k] = val;
+  }
+#pragma unroll
+  for (int i = 0; i < SLICE_PER; ++i) {
+    const int idx = threadIdx.x + i * SLICE_THREADS;
+    const int r = rmaj ? idx % SR : idx / SK, k = rmaj ? idx / SR : idx % SK;
+    s[r][k] = val[i];
   }
 }
 
@@ -494,7 +566,7 @@ __global__ void __launch_bounds__(256) oz_rowmax_kernel(OzView v, int rows, long
   }
 }
 
-// The five balanced base-256 digits of x relative to the row scale 2^e.
+// The OZ_S balanced base-256 digits of x relative to the row scale 2^e.
 __device__ __forceinline__ void digits_of(double x, int e, float *d) {
   const long long bits = __double_as_longlong(x);
   const int efx = (int)((bits >> 52) & 0x7FF);
@@ -521,10 +593,17 @@ __device__ __forceinline__ void digits_of(double x, int e, float *d) {
   for (int p = 0; p < OZ_S; ++p) d[p] = sgn * (float)dd[p] * sc[p];
 }
 
+// Offsets of column kk of row br (= b rows + r) in the interleaved digit
+// layout (see OzDigits): digit p < 4 at blk 64 + 16 p + u, p >= 4 at
+// g1 + blk 32 + 16 (p - 4) + u, blk = br KB + kk / 16, u = kk mod 16.
+__device__ __forceinline__ long long digit_off(long long blk, int u, int p, long long g1) {
+  return p < 4 ? blk * 64 + 16 * p + u : g1 + blk * 32 + 16 * (p - 4) + u;
+}
+
 __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long long K,
                                                         const int *__restrict__ ef,
                                                         __nv_bfloat16 *__restrict__ out,
-                                                        long long ld, long long plane) {
+                                                        long long ld, long long g1) {
   __shared__ double s[SR][SK + 1];
   const int b = blockIdx.z;
   const long long r0 = (long long)blockIdx.y * SR, k0 = (long long)blockIdx.x * SK;
@@ -537,10 +616,111 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
     const int e = row_scale(ef[(long long)b * rows + rr]);
     float d[OZ_S];
     digits_of(s[r][k], e, d);
-    const long long o = ((long long)b * rows + rr) * ld + kk;
-    if (!OZ_IN(o, plane, 31)) continue;
+    const long long blk = ((long long)b * rows + rr) * (ld / 16) + (kk >> 4);
+    if (!OZ_IN(blk * 64 + 63, g1, 31)) continue;
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) out[p * plane + o] = __float2bfloat16_rn(d[p]);
+    for (int p = 0; p < OZ_S; ++p)
+      out[digit_off(blk, (int)(kk & 15), p, g1)] = __float2bfloat16_rn(d[p]);
+  }
+}
+
+// ---------------------------------------- K-contiguous sources (fast path) --
+// Views whose rows are contiguous along K (cs2 == 1, one k1 segment), with
+// 16-byte aligned rows: each thread takes 8 consecutive columns of one row
+// (four 16-byte loads) and, in the digit pass, writes 16 bytes to each of the
+// six digit slots.  No shared-memory transpose.
+constexpr int KC = 8;  // columns per thread
+
+__device__ __forceinline__ void load8(const OzView &v, int b, long long r, long long k0,
+                                      long long K, double *x) {
+  const long long o = b * v.bs + r * v.rs + k0;
+  if (!OZ_IN(o + std::min<long long>(KC, K - k0) - 1, v.xlen, 33)) {
+#pragma unroll
+    for (int u = 0; u < KC; ++u) x[u] = 0.0;
+    return;
+  }
+  if (k0 + KC <= K) {
+    if (v.x2) {
+      const float4 *p = reinterpret_cast<const float4 *>(v.x2 + o);
+#pragma unroll
+      for (int u = 0; u < KC / 2; ++u) {
+        const float4 f = p[u];
+        x[2 * u] = (double)f.x + (double)f.y;
+        x[2 * u + 1] = (double)f.z + (double)f.w;
+      }
+    } else {
+      const double2 *p = reinterpret_cast<const double2 *>(v.x + o);
+#pragma unroll
+      for (int u = 0; u < KC / 2; ++u) {
+        const double2 d = p[u];
+        x[2 * u] = d.x;
+        x[2 * u + 1] = d.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < KC; ++u)
+      x[u] = k0 + u < K ? (v.x2 ? (double)v.x2[o + u].x + (double)v.x2[o + u].y : v.x[o + u])
+                        : 0.0;
+  }
+}
+
+// ef[b][r] = max biased exponent over the row; grid (ceil(K / 2048), rows, batch).
+__global__ void __launch_bounds__(256) oz_rowmax_kc_kernel(OzView v, int rows, long long K,
+                                                           int *__restrict__ ef) {
+  __shared__ int wm[8];
+  const int b = blockIdx.z, r = blockIdx.y;
+  const long long k0 = ((long long)blockIdx.x * 256 + threadIdx.x) * KC;
+  int m = 0;
+  if (k0 < K) {
+    double x[KC];
+    load8(v, b, r, k0, K, x);
+#pragma unroll
+    for (int u = 0; u < KC; ++u) m = max(m, ef_of(x[u]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = max(m, wm[w]);
+    if (m > 0) atomicMax(&ef[(long long)b * rows + r], m);
+  }
+}
+
+// Digits of 8 consecutive columns per thread over [batch][rows][ld] (zeros in K..ld).
+__global__ void __launch_bounds__(256) oz_digits_kc_kernel(OzView v, int rows, long long K,
+                                                           const int *__restrict__ ef,
+                                                           __nv_bfloat16 *__restrict__ out,
+                                                           long long ld, long long g1) {
+  // g1 = batch rows ld 4 values: the chunks of 8 columns are g1 / 32
+  const long long cpr = ld / KC, total = g1 / 32;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long br = c / cpr, k0 = (c - br * cpr) * KC;
+    const int b = (int)(br / rows);
+    const long long r = br - (long long)b * rows;
+    double x[KC];
+    load8(v, b, r, k0, K, x);
+    const int e = row_scale(ef[br]);
+    uint32_t w[OZ_S][KC / 2];
+#pragma unroll
+    for (int u = 0; u < KC; u += 2) {
+      float d0[OZ_S], d1[OZ_S];
+      digits_of(x[u], e, d0);
+      digits_of(x[u + 1], e, d1);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[p], d1[p]);
+        w[p][u / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+      }
+    }
+    const long long blk = br * (ld / 16) + (k0 >> 4);
+    if (!OZ_IN(blk * 64 + 63, g1, 32)) continue;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p)
+      *reinterpret_cast<uint4 *>(out + digit_off(blk, (int)(k0 & 15), p, g1)) =
+          make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
   }
 }
 
@@ -600,31 +780,42 @@ void load_encode() {
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
 }
 
-// 4D bf16 map, 32-byte swizzle; dims d[0..3] (elements), strides s[0..2] (bytes, of dims 1..3),
-// box (b0, b1, b2, 1).
+// 4D bf16 map: dims d[0..3] (elements), strides s[0..2] (bytes, of dims 1..3),
+// box b[0..3], swizzle of 128 bytes (b[0] = 64) or 64 bytes (b[0] = 32).
 cudaError_t make_map4(CUtensorMap *m, const void *base, const cuuint64_t d[4],
-                      const cuuint64_t s[3], cuuint32_t b0, cuuint32_t b1, cuuint32_t b2) {
+                      const cuuint64_t s[3], const cuuint32_t b[4]) {
   if (!g_encode) return cudaErrorNotSupported;
   if ((uintptr_t)base % 16) return cudaErrorInvalidValue;
   for (int k = 0; k < 3; ++k)
     if (s[k] % 16) return cudaErrorInvalidValue;
+  if (b[0] != 64 && b[0] != 32) return cudaErrorInvalidValue;
   cuuint64_t dims[4] = {d[0], d[1], d[2], d[3]};
   cuuint64_t strides[3] = {s[0], s[1], s[2]};
-  cuuint32_t box[4] = {b0, b1, b2, 1};
+  cuuint32_t box[4] = {b[0], b[1], b[2], b[3]};
   cuuint32_t es[4] = {1, 1, 1, 1};
   const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base),
                               dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              b[0] == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Map of a digit operand: dims (K, rows, batch, digit), box 16 x 128.
-cudaError_t digit_map(CUtensorMap *m, const OzDigits &o) {
-  const cuuint64_t d[4] = {(cuuint64_t)o.K, (cuuint64_t)o.rows, (cuuint64_t)o.batch, OZ_S};
-  const cuuint64_t s[3] = {(cuuint64_t)o.ld * 2, (cuuint64_t)o.ld * 2 * o.rows,
-                           (cuuint64_t)o.ld * 2 * o.rows * o.batch};
-  return make_map4(m, o.d, d, s, KS, BM, 1);
+// The two maps of a digit operand (digits 0-3 and 4-5, see OzDigits): dims
+// (slot width, K blocks, rows, batch), box (width, 1, 128, 1).
+cudaError_t digit_maps(CUtensorMap *m0, CUtensorMap *m1, const OzDigits &o) {
+  const cuuint64_t kb = (cuuint64_t)(o.ld / 16);
+  const __nv_bfloat16 *g1 = o.d + (long long)o.batch * o.rows * o.ld * 4;
+  {
+    const cuuint64_t d[4] = {64, kb, (cuuint64_t)o.rows, (cuuint64_t)o.batch};
+    const cuuint64_t st[3] = {128, kb * 128, kb * 128 * o.rows};
+    const cuuint32_t b[4] = {64, 1, BM, 1};
+    RS_TRY(make_map4(m0, o.d, d, st, b));
+  }
+  const cuuint64_t d[4] = {32, kb, (cuuint64_t)o.rows, (cuuint64_t)o.batch};
+  const cuuint64_t st[3] = {64, kb * 64, kb * 64 * o.rows};
+  const cuuint32_t b[4] = {32, 1, BM, 1};
+  return make_map4(m1, g1, d, st, b);
 }
 
 cudaError_t prepare() {
@@ -691,17 +882,33 @@ bool oz_available() {
 
 cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
   if (out.rows <= 0 || out.K <= 0 || out.batch <= 0) return cudaSuccess;
-  if (out.ld < out.K || (out.ld % 8) || v.k2pad <= 0) return cudaErrorInvalidValue;
+  if (out.ld < out.K || (out.ld % 16) || v.k2pad <= 0) return cudaErrorInvalidValue;
+  // start of the digits 4-5 group (see OzDigits)
+  const long long g1 = (long long)out.batch * out.rows * out.ld * 4;
   RS_TRY(cudaMemsetAsync(out.ef, 0, (size_t)out.batch * out.rows * sizeof(int), s));
   if ((out.rows + SR - 1) / SR > 65535 || out.batch > 65535) return cudaErrorInvalidValue;
+  // rows contiguous along K, 16-byte aligned: the vectorised path
+  const uintptr_t base = v.x2 ? (uintptr_t)v.x2 : (uintptr_t)v.x;
+  const bool kc = v.cs2 == 1 && v.k2off == 0 && v.k2pad >= out.K && v.k2n >= out.K &&
+                  base % 16 == 0 && v.rs % 2 == 0 && v.bs % 2 == 0 && out.rows <= 65535;
+  if (kc) {
+    dim3 gm((unsigned)ceil_div(out.K, 256LL * KC), out.rows, out.batch);
+    oz_rowmax_kc_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
+    ++launch_counter();
+    RS_TRY(cudaGetLastError());
+    const long long chunks = (long long)out.batch * out.rows * out.ld / KC;
+    const int grid = (int)std::min<long long>(ceil_div(chunks, 256LL), 152LL * 16);
+    oz_digits_kc_kernel<<<grid, 256, 0, s>>>(v, out.rows, out.K, out.ef, out.d, out.ld, g1);
+    ++launch_counter();
+    return cudaGetLastError();
+  }
   dim3 gm(ceil_div(out.K, SK), ceil_div(out.rows, SR), out.batch);
   oz_rowmax_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
   ++launch_counter();
   RS_TRY(cudaGetLastError());
   // the digit pass covers the padding columns K..ld too (zeros)
   dim3 gd(ceil_div(out.ld, SK), ceil_div(out.rows, SR), out.batch);
-  oz_digits_kernel<<<gd, 256, 0, s>>>(v, out.rows, out.K, out.ef, out.d, out.ld,
-                                      (long long)out.batch * out.rows * out.ld);
+  oz_digits_kernel<<<gd, 256, 0, s>>>(v, out.rows, out.K, out.ef, out.d, out.ld, g1);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -732,8 +939,9 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   if ((long long)g.batch * ks > 65535 || ceil_div(g.M, BM) > 65535) return cudaErrorInvalidValue;
   OzParams p;
   std::memset(&p, 0, sizeof(p));
-  RS_TRY(digit_map(&p.ta, g.A));
-  RS_TRY(digit_map(&p.tb, g.B));
+  if (g.A.ld % 16 || g.B.ld % 16) return cudaErrorInvalidValue;
+  RS_TRY(digit_maps(&p.ta0, &p.ta1, g.A));
+  RS_TRY(digit_maps(&p.tb0, &p.tb1, g.B));
   p.M = g.M;
   p.N = g.N;
   p.kst = kst;
@@ -751,6 +959,7 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   p.ccap = ks > 1 ? (long long)ks * g.batch * g.M * g.N : g.ccap;
   p.efa_cap = (long long)g.A.batch * g.A.rows;
   p.efb_cap = (long long)g.B.batch * g.B.rows;
+  p.wait_polls = g.wait_polls;
   RS_TRY(prepare());
   dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.batch * ks);
   oz_gemm_kernel<0><<<grid, THREADS, SMEM, s>>>(p);
@@ -790,13 +999,16 @@ OzExch oz_exch_geometry(int n, int na, int bk) {
   x.na = na;
   x.bk = bk;
   // l window of the 16-wide j tile at j0 (a multiple of 16): from
-  // floor8(j0 - bk) = j0 - ceil8(bk) (a 16-byte aligned TMA start) to j0 + 15 + bk
+  // floor8(j0 - bk) = j0 - ceil8(bk) to j0 + 15 + bk, in nl16 steps of 16
   const int c8 = (bk + 7) / 8 * 8;
   x.nl16 = ceil_div(16 + bk + c8, KS);
   x.mtiles = ceil_div(n, 8);
   x.jtiles = ceil_div(n, 16);
   x.kx = (long long)(8 + 2 * bk) * x.nl16 * KS;
-  x.ldl = ((long long)n + 7) / 8 * 8;
+  // l' = l + lsh puts every window start j0 - c8 on a 16-column block
+  x.lsh = (16 - c8 % 16) % 16;
+  x.lb0 = (x.lsh - c8) / 16;  // exact: lsh - c8 is a multiple of 16
+  x.ldl = ((long long)n + x.lsh + 15) / 16 * 16;
   return x;
 }
 
@@ -816,21 +1028,28 @@ cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *p
 }
 
 cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
-                    long long tcap, double alpha, int *err, cudaStream_t s) {
+                    long long tcap, double alpha, int *err, cudaStream_t s, int wait_polls) {
   if (!oz_available()) return cudaErrorNotSupported;
   const int tiles = x.mtiles * x.jtiles;
   if (X.batch != tiles || X.rows != BM || X.K != x.kx || At.rows != x.na ||
-      At.K != (long long)x.n * x.ldl || At.batch != 1 || tiles > 65535)
+      At.K != (long long)x.n * x.ldl || At.ld != At.K || At.batch != 1 || tiles > 65535 ||
+      X.ld % 16 || x.ldl % 16)
     return cudaErrorInvalidValue;
   OzParams p;
   std::memset(&p, 0, sizeof(p));
-  RS_TRY(digit_map(&p.ta, X));
+  RS_TRY(digit_maps(&p.ta0, &p.ta1, X));
   {
-    // right operand as (l, k, q, digit): l padded to ldl, dims n so that l >= n reads zeros
-    const cuuint64_t d[4] = {(cuuint64_t)x.n, (cuuint64_t)x.n, (cuuint64_t)x.na, OZ_S};
-    const cuuint64_t st[3] = {(cuuint64_t)x.ldl * 2, (cuuint64_t)x.ldl * 2 * x.n,
-                              (cuuint64_t)x.ldl * 2 * x.n * x.na};
-    RS_TRY(make_map4(&p.tb, At.d, d, st, KS, 1, BM));
+    // right operand as (slot, l' block, k, q): a box is one l' block of 128 q rows
+    const cuuint64_t lb = (cuuint64_t)(x.ldl / 16);
+    const __nv_bfloat16 *g1 = At.d + (long long)x.na * x.n * x.ldl * 4;
+    const cuuint64_t d0[4] = {64, lb, (cuuint64_t)x.n, (cuuint64_t)x.na};
+    const cuuint64_t s0[3] = {128, lb * 128, lb * 128 * x.n};
+    const cuuint32_t b0[4] = {64, 1, 1, BM};
+    RS_TRY(make_map4(&p.tb0, At.d, d0, s0, b0));
+    const cuuint64_t d1[4] = {32, lb, (cuuint64_t)x.n, (cuuint64_t)x.na};
+    const cuuint64_t s1[3] = {64, lb * 64, lb * 64 * x.n};
+    const cuuint32_t b1[4] = {32, 1, 1, BM};
+    RS_TRY(make_map4(&p.tb1, g1, d1, s1, b1));
   }
   p.M = x.n;
   p.N = x.na;
@@ -841,12 +1060,14 @@ cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, doub
   p.alpha = alpha;
   p.C = T;
   p.bk = x.bk;
+  p.lb0 = x.lb0;
   p.nl16 = x.nl16;
   p.jtiles = x.jtiles;
   p.err = err;
   p.ccap = tcap;
   p.efa_cap = (long long)X.batch * X.rows;
   p.efb_cap = (long long)At.batch * At.rows;
+  p.wait_polls = wait_polls;
   RS_TRY(prepare());
   dim3 grid(ceil_div(x.na, BN), 1, tiles);
   oz_gemm_kernel<1><<<grid, THREADS, SMEM, s>>>(p);

@@ -31,9 +31,14 @@ namespace rssri {
 constexpr int OZ_S = 6;  // digits per fp64 value
 constexpr int OZ_PRODUCTS = OZ_S * (OZ_S + 1) / 2;  // digit products kept (p + q < OZ_S)
 
-// Digits of an fp64 matrix, K-major: d[p][b][r][ld] (bf16, p < OZ_S), and the
-// biased fp64 exponent field of each row's largest magnitude, ef[b][r]
-// (the row scale is e = max(ef, 1) - 1022).  ld >= K is a multiple of 8.
+// Digits of an fp64 matrix, K-major, interleaved by blocks of 16 columns so
+// that every TMA row the products load is 128 or 64 bytes wide: with
+// KB = ld / 16 blocks per row and column k = 16 kb + u,
+//   digits 0-3:  d[((b rows + r) KB + kb) 64 + 16 p + u]            (p < 4)
+//   digits 4-5:  d[G1 + ((b rows + r) KB + kb) 32 + 16 (p - 4) + u]  (p >= 4)
+// with G1 = batch rows KB 64 (bf16, 6 batch rows ld values in all); and the
+// biased fp64 exponent field of each row's largest magnitude, ef[b][r] (the
+// row scale is e = max(ef, 1) - 1022).  ld >= K is a multiple of 16.
 struct OzDigits {
   __nv_bfloat16 *d = nullptr;
   int *ef = nullptr;
@@ -45,8 +50,8 @@ inline size_t oz_digit_elems(const OzDigits &o) {
 }
 
 // An fp64 source for the slicer: digit column kk of row r in batch b reads
-//   k1 = kk / k2pad, k2 = kk % k2pad,
-//   x[b*bs + r*rs + k1*cs1 + k2*cs2]   if k2 < k2n, else 0.
+//   k1 = kk / k2pad, k2 = kk % k2pad - k2off,
+//   x[b*bs + r*rs + k1*cs1 + k2*cs2]   if 0 <= k2 < k2n, else 0.
 // (A plain row-major matrix: cs2 = 1, k2pad = k2n = K, cs1 unused.)
 // A double-float source (x2, pairs (hi, lo) with value hi + lo) may replace x.
 struct OzView {
@@ -54,6 +59,7 @@ struct OzView {
   const float2 *x2 = nullptr;
   long long bs = 0, rs = 0, cs1 = 0, cs2 = 1;
   long long k2pad = 0, k2n = 0;
+  long long k2off = 0;  // k2 in [k2off, k2off + k2n) reads index k2 - k2off
   long long xlen = 0;  // elements of the source (bounds checks of RSSRI_CHECKS builds)
 };
 
@@ -72,6 +78,9 @@ struct OzGemm {
   long long ccap = 0;  // elements of C (bounds checks of RSSRI_CHECKS builds)
   double alpha = 1.0;
   int *err = nullptr;  // device flag, set non-zero if a bounded wait gives up
+  // testing only: > 0 issues no copy or product and gives up every wait after
+  // this many polls (the error path with nothing in flight); 0 = normal
+  int wait_polls = 0;
 };
 size_t oz_gemm_work(const OzGemm &g);
 cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream_t s);
@@ -84,11 +93,15 @@ double oz_gemm_flops(const OzGemm &g);  // tensor flops issued (digit products, 
 // around its m and of l around its j (half-width bk).  The left operand
 // (built once from D by oz_exch_build) holds, per tile, the 128 rows x
 // (8 + 2 bk) (16 nl16) values of D; the right operand is At sliced with
-// digit rows q and columns (k, l) (l padded to ldl = n rounded up to 8).
+// digit rows q and columns (k, l'), l' = l + lsh (lsh in {0, 8}, so that every
+// tile's window of l starts on a 16-column block) and l' padded to ldl, a
+// multiple of 16: the slicer view of At takes k2pad = ldl, k2off = lsh.
 struct OzExch {
   int n = 0, na = 0, bk = 0, nl16 = 0, mtiles = 0, jtiles = 0;
   long long kx = 0;  // K of a tile: (8 + 2 bk) * nl16 * 16
   long long ldl = 0;
+  int lsh = 0;  // column shift of l in the right operand's digits
+  int lb0 = 0;  // first 16-column block of j tile jt's window is jt + lb0
 };
 OzExch oz_exch_geometry(int n, int na, int bk);
 // fp64 left operand [tiles][128][kx] of the exchange contraction (tiles =
@@ -96,9 +109,9 @@ OzExch oz_exch_geometry(int n, int na, int bk);
 cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *pidx,
                            double *xs, long long xs_cap, cudaStream_t s);
 // T[(j*n + m)*na + q] = alpha * the contraction, fp64.  X: digits [tiles][128][kx];
-// At: digits [1][na][n*ldl] (k major, l minor).
+// At: digits [1][na][n*ldl] (k major, l' minor).
 cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
-                    long long tcap, double alpha, int *err, cudaStream_t s);
+                    long long tcap, double alpha, int *err, cudaStream_t s, int wait_polls = 0);
 double oz_exch_flops(const OzExch &x);
 
 // pidx[i*n + j] = index of pair (i, j) among the P kept pairs (linear

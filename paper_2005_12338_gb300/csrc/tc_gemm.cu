@@ -22,22 +22,12 @@
 #include <cstring>
 #include <mutex>
 
-#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace rssri {
 namespace {
 
-constexpr int TBM = 128, SLAB = 128;  // rows per CTA tile; bytes of K per stage and row
-constexpr int A_STAGE = TBM * SLAB;
-
-// Element size and K elements per stage / per instruction of each kind.
-template <int KIND> struct KindT;
-template <> struct KindT<TC_BF16> {
-  static constexpr int ES = 2, TBK = SLAB / 2, KMMA = 16;
-};
-template <> struct KindT<TC_TF32> {
-  static constexpr int ES = 4, TBK = SLAB / 4, KMMA = 8;
-};
+using namespace tcx;
 
 struct TcParams {
   CUtensorMap ta[2];
@@ -49,69 +39,8 @@ struct TcParams {
   void *cop;
   long long ldcop;
   int *err;
+  int wait_polls;  // 0: normal; > 0: test mode (see TcGemm)
 };
-
-__device__ __forceinline__ uint32_t s_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t c) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(c));
-}
-__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ uint32_t bar_try(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(s_u32(b)), "r"(parity)
-      : "memory");
-  return ok;
-}
-// Bounded wait (each try_wait may suspend for a while): ~2^22 polls.
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, int *err, int code) {
-  for (int i = 0; i < (1 << 22); ++i)
-    if (bar_try(b, parity)) return true;
-  if (err) atomicExch(err, code);
-  return false;
-}
-__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *m, uint64_t *bar, int x,
-                                          int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(s_u32(dst)),
-      "l"(m), "r"(s_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
-// of 128 bytes grouped by 8 (stride 1024 bytes between groups).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-// Instruction descriptor: D fp32, A and B of the same type (bf16 = 1 under
-// kind::f16, tf32 = 2 under kind::tf32), both K-major, M = 128, N = n.
-template <int KIND>
-__device__ __forceinline__ uint32_t instr_desc(int n) {
-  constexpr uint32_t ab = KIND == TC_BF16 ? 1u : 2u;
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(TBM >> 4) << 24);
-}
-
-// fp32 rounded to the nearest tf32 (10 stored mantissa bits), kept in fp32.
-__device__ __forceinline__ float round_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
@@ -153,12 +82,12 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   if (threadIdx.x == 0) {
     // producer: the same (b, segment, k-block) sequence as the MMA issuer
     int it = 0;
-    bool ok = true;
+    bool ok = test_mode_gate(p.wait_polls, p.err);
     for (int b = b_lo; b < b_hi && ok; ++b)
       for (int s = 0; s < p.nseg && ok; ++s)
         for (int k0 = 0; k0 < p.K[s]; k0 += TBK, ++it) {
           const int st = it % S;
-          if (it >= S && !bar_wait(&empty[st], ((it / S) - 1) & 1, p.err, 1)) {
+          if (it >= S && !bar_wait(&empty[st], ((it / S) - 1) & 1, p.err, 1, p.wait_polls)) {
             ok = false;
             break;
           }
@@ -174,7 +103,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
       for (int s = 0; s < p.nseg && ok; ++s)
         for (int k0 = 0; k0 < p.K[s]; k0 += TBK, ++it) {
           const int st = it % S;
-          if (!bar_wait(&full[st], (it / S) & 1, p.err, 2)) {
+          if (!bar_wait(&full[st], (it / S) & 1, p.err, 2, p.wait_polls)) {
             ok = false;
             break;
           }
@@ -210,7 +139,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         : "memory");
   }
   __syncwarp();
-  const bool ready = bar_wait(accum, 0, p.err, 3);
+  const bool ready = bar_wait(accum, 0, p.err, 3, p.wait_polls);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ready && b_lo < b_hi) {
     const int row = m0 + warp * 32 + lane;
@@ -303,8 +232,10 @@ void load_encode() {
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
 }
 
-cudaError_t make_map(CUtensorMap *m, int kind, const TcOperand &op, int K, int batch,
-                     int box_rows) {
+}  // namespace
+
+cudaError_t tc_make_map(CUtensorMap *m, int kind, const TcOperand &op, int K, int batch,
+                        int box_rows) {
   if (!g_encode) return cudaErrorNotSupported;
   const int es_bytes = kind == TC_BF16 ? 2 : 4;
   const int per16 = 16 / es_bytes;  // elements per 16 bytes
@@ -323,7 +254,6 @@ cudaError_t make_map(CUtensorMap *m, int kind, const TcOperand &op, int K, int b
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-}  // namespace
 
 bool tc_available() {
   std::call_once(g_encode_once, load_encode);
@@ -364,8 +294,8 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s) {
   long long iters = 0;
   for (int s2 = 0; s2 < g.nseg; ++s2) {
     if (g.K[s2] <= 0) return cudaErrorInvalidValue;
-    RS_TRY(make_map(&p.ta[s2], g.kind, g.A[s2], g.K[s2], g.batch, TBM));
-    RS_TRY(make_map(&p.tb[s2], g.kind, g.B[s2], g.K[s2], g.batch, BN));
+    RS_TRY(tc_make_map(&p.ta[s2], g.kind, g.A[s2], g.K[s2], g.batch, TBM));
+    RS_TRY(tc_make_map(&p.tb[s2], g.kind, g.B[s2], g.K[s2], g.batch, BN));
     p.K[s2] = g.K[s2];
     iters += ceil_div(g.K[s2], tbk);
   }
@@ -383,6 +313,7 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s) {
   p.cop = g.cop;
   p.ldcop = g.ldcop ? g.ldcop : g.N;
   p.err = g.err;
+  p.wait_polls = g.wait_polls;
   size_t smem = 1024 + (size_t)p.stages * (A_STAGE + BN * SLAB) + 256;
   // at most two CTAs per SM, so that their tensor memory (<= 2 x 256 columns) always fits
   smem = std::max<size_t>(smem, 80 * 1024);

@@ -38,6 +38,9 @@ struct TcGemm {
   void *cop = nullptr;
   long long ldcop = 0;
   int *err = nullptr;  // device flag, set non-zero if a bounded wait gives up
+  // testing only: > 0 issues no copy or product and gives up every wait after
+  // this many polls (the error path with nothing in flight); 0 = normal
+  int wait_polls = 0;
 };
 
 cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s);

@@ -26,13 +26,10 @@ def test_time_to_target_model():
     assert bench.time_to_target(res, 300, 1.0)["pairs_needed"] == 2.0
 
 
-def test_peaks():
-    assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.2586, rel=1e-3)
-    assert bench.DF64_PEAK_TFLOPS == pytest.approx(6.7123, rel=1e-3)
-    p = {"bf16_tflops": 1914.7}
-    assert bench.tensor_peak(p, "bf16") == 1914.7
-    assert bench.tensor_peak(p, "tf32") == pytest.approx(957.35)
-    assert bench.tensor_peak({}, "bf16") == bench.FALLBACK_PEAKS["bf16_tflops"]
+def test_forms():
+    assert bench.FORMS["plain"] == ("fp64", "fp64")
+    assert bench.FORMS["chosen"] == ("bf16", "oz")
+    assert set(bench.FORMS) == {"plain", "chosen", "df64"}
 
 
 def test_traffic_figures_go_stale_with_their_source(tmp_path, monkeypatch):
@@ -43,12 +40,12 @@ def test_traffic_figures_go_stale_with_their_source(tmp_path, monkeypatch):
     src.write_text("kernel v1\n")
     sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
-        {"dd_spmm/df64": {"source": "k.cu", "source_sha": sha, "bytes_per_launch": 123}}))
+        {"plain/dd_spmm": {"source": "k.cu", "source_sha": sha, "bytes_per_launch": 123}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_for("dd_spmm/df64") == 123
-    assert bench.traffic_for("dd_gemm/df64") is None
+    assert bench.traffic_for("dd_spmm", "plain") == 123
+    assert bench.traffic_for("dd_gemm", "plain") is None
     src.write_text("kernel v2\n")
-    assert bench.traffic_for("dd_spmm/df64") is None
+    assert bench.traffic_for("dd_spmm", "plain") is None
 
 
 def test_many_sizes():
