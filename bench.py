@@ -66,15 +66,19 @@ def parse():
     ap.add_argument("--n-tau", type=int, default=None,
                     help="override the number of tau points of the workload (for one-off "
                          "measurements on the largest workload; not the benchmark line)")
-    ap.add_argument("--cv", action="store_true",
-                    help="also train the learned control variate on an independent run and "
-                         "report its estimate (fp64 chain)")
+    ap.add_argument("--no-cv", action="store_true",
+                    help="skip the learned control variate report (training on an independent "
+                         "run, then the chosen form with and without it on the same draws)")
     ap.add_argument("--literal", action="store_true",
                     help="also run the literal Eq. 25 estimator (fp64 chain, exact-D cross "
                          "terms) on the first timed seed and report its cost and stderr")
     ap.add_argument("--many", type=int, default=0,
                     help="also time K independent chains of uneven size (N from 64 to 256) "
                          "one by one and batched on K streams (rssri_sigma_batch)")
+    ap.add_argument("--c4", type=int, default=0, metavar="K",
+                    help="instead of the benchmark line, run the many-chain workload: the "
+                         "first K of its 64 chains (N 100..800, N_aux 3N, 64 tau, 200 pairs), "
+                         "each set up and sampled in turn in --form, and print its own line")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -325,6 +329,67 @@ def many_systems(args, binding, torch, prec, dd):
             **res, "speedup": res["one_by_one"]["s_per_pass"] / res["batched"]["s_per_pass"]}
 
 
+def c4_run(args):
+    """The many-chain workload (64 chains of uneven size N_k = 100 + round(700 k/63),
+    n_occ = N/2, N_aux = 3N, 64 tau points, 200 sample pairs, eps = 1e-3), one
+    chain after another: inputs drawn on the device, setup (S1-S3, S6, S7) and
+    rssri_sigma (S4, S5, S8-S10) timed with a device synchronisation on both
+    sides, the handle and inputs freed before the next chain (the chains'
+    (ij|A) alone would be 225 GB).  A chain of N = 100 is run first, untimed,
+    to take the one-time tile tuning and graph capture out of the numbers."""
+    import torch
+    from paper_2005_12338_gb300 import binding, build
+    build.build()
+    pr, dd = FORMS[args.form]
+    prec = {"bf16": binding.RSSRI_PREC_BF16, "fp64": binding.RSSRI_PREC_FP64,
+            "df64": binding.RSSRI_PREC_DF64}[pr]
+    dd = {"fp64": binding.RSSRI_DD_FP64, "df64": binding.RSSRI_DD_DF64,
+          "oz": binding.RSSRI_DD_OZ}[dd]
+    m = dict(synth.C4)
+    sizes = synth.many_sizes(m["k"], m["n_min"], m["n_max"])[:args.c4]
+    opts = binding.Handle.options(m["eps_prime"], m["eps"], m["n_s"], 5, precision=prec,
+                                  dd_arith=dd)
+
+    def one(n, seed):
+        s = synth.make_system_torch(n, n // 2, 3 * n, m["n_tau"], input_seed=seed)
+        sig = torch.empty((m["n_tau"], n, n), dtype=torch.float64, device="cuda")
+        h = binding.Handle(torch.cuda.current_device())
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.setup(s.eri3, s.metric, s.orb_e, s.orb_c, s.tau, s.tau_w, n_occ=s.n_occ,
+                    mu=s.mu, beta=s.beta, opts=opts)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e, se, st = h.sigma(opts, sig)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+        finally:
+            h.close()
+        del s, sig
+        torch.cuda.empty_cache()
+        return {"n": n, "setup_s": t1 - t0, "sample_s": t2 - t1, "e_corr": e, "stderr": se,
+                "pairs_kept": st["n_pairs_large"]}
+
+    one(100, 1000)
+    chains = [one(n, k) for k, n in enumerate(sizes)]
+    units = len(chains) * m["n_s"] * m["n_tau"]
+    t_setup = sum(c["setup_s"] for c in chains)
+    t_samp = sum(c["sample_s"] for c in chains)
+    out = {"metric": "Sigma(tau) units/s (unit = one sample pair x one tau point)",
+           "value": units / (t_setup + t_samp), "unit": "units/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": {"plain": "f64", "chosen": "bf16+f64", "df64": "df64"}[args.form],
+           "data": "synthetic",
+           "config": {"workload": f"c4_many_chains: {len(chains)} of 64 chains, N {sizes[0]}.."
+                                  f"{sizes[-1]}, N_aux=3N, N_tau={m['n_tau']}, "
+                                  f"N_s={m['n_s']}, eps={m['eps']}", "form": args.form,
+                      "timed": "setup + rssri_sigma per chain, host clock around device "
+                               "synchronisations; chains one after another"},
+           "units": units, "setup_s_total": t_setup, "sampling_s_total": t_samp,
+           "sampling_units_per_s": units / t_samp, "chains": chains}
+    print(json.dumps(out), flush=True)
+
+
 def pipe_peaks(binding, device):
     """Measured fp64 and fp32 pipe peaks of this GPU, TFLOP/s: the library's
     DFMA, DMMA and FFMA micro-benchmarks, and (fp64, for reference only: not
@@ -518,26 +583,42 @@ def our_arm(args):
     # learned control variate (fp64 chain): train on an independent run, then
     # estimate with it on the first timed seed, next to the plain estimate
     cv_report = None
-    if args.cv:
+    if not args.no_cv:
+        # the learned control variate on the chosen form: trained on an independent
+        # run (seed 777; statistics need the fp64-accurate double-float chain),
+        # then the same draws (seeds[0]) with and without it
         tr = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 777),
-                                    dd_arith=binding.RSSRI_DD_DF64,
+                                    dd_arith=binding.RSSRI_DD_OZ,
                                     precision=binding.RSSRI_PREC_DF64)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=tr)
         c0 = time.perf_counter()
         lb, la = h.cv_train(tr, synth.mlp_init(0), 400, 4096, 1e-3)
+        torch.cuda.synchronize()
         t_train = time.perf_counter() - c0
-        o_p = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seeds[0],
-                                     dd_arith=binding.RSSRI_DD_DF64,
-                                     precision=binding.RSSRI_PREC_DF64)
-        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o_p)
-        e_cv, se_cv, _ = h.sigma(o_p, sig, ep)
-        o_cv = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seeds[0],
-                                      dd_arith=binding.RSSRI_DD_DF64, cv=1,
-                                      precision=binding.RSSRI_PREC_DF64)
-        e_l, se_l, _ = h.sigma(o_cv, sig, ep)
-        cv_report = {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
-                     "e_corr_plain": e_cv, "stderr_plain": se_cv, "e_corr_learned": e_l,
-                     "stderr_learned": se_l, "stderr_ratio_plain_over_learned": se_cv / se_l}
+        pr, dd = FORMS["chosen"]
+        rows = {}
+        for name, cvf in (("chosen", 0), ("chosen+cv", 1)):
+            o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seeds[0],
+                                       dd_arith=dd_code[dd], precision=prec_code[pr], cv=cvf)
+            h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
+            h.sigma(o, sig, ep)  # warm-up: graph capture, tile tuning
+            torch.cuda.synchronize()
+            e_, se_, st_ = h.sigma(o, sig, ep)
+            torch.cuda.synchronize()
+            rows[name] = (e_, se_, st_["t_setup_ms"] + st_["t_green_dd_ms"], st_["t_sample_ms"],
+                          ep.cpu().numpy().copy())
+        a, b = rows["chosen"][4], rows["chosen+cv"][4]
+        cv_report = {"form": "chosen (bf16 chain, sliced block)", "eps": cfg["eps"],
+                     "fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
+                     "e_corr_plain": rows["chosen"][0], "stderr_plain": rows["chosen"][1],
+                     "e_corr_learned": rows["chosen+cv"][0],
+                     "stderr_learned": rows["chosen+cv"][1],
+                     "stderr_ratio_plain_over_learned": rows["chosen"][1] / rows["chosen+cv"][1],
+                     "paired_sd_ratio": float(np.std(a) / np.std(b)),
+                     "sampling_ms": {k: v[3] for k, v in rows.items()},
+                     "time_to_1mEh": {k: time_to_target([v[:4]], ns, 1e-3)
+                                      for k, v in rows.items()},
+                     "note": "time_to_1mEh of chosen+cv excludes the one-time training (train_s)"}
 
     many_report = None
     if args.many > 0:
@@ -712,6 +793,8 @@ def main():
         print(json.dumps({k: r[k] for k in ("value", "unit", "cores")}), flush=True)
     elif args.impl == "reference":
         reference_arm(args)
+    elif args.c4 > 0:
+        c4_run(args)
     else:
         our_arm(args)
 

@@ -724,6 +724,92 @@ __global__ void __launch_bounds__(256) oz_digits_kc_kernel(OzView v, int rows, l
   }
 }
 
+// --------------------------------------- row-contiguous sources (rs == 1) --
+// ef of rows whose source is contiguous across rows: one thread per row walks
+// RK columns (loads coalesced across the warp, no shared memory); grid
+// (ceil(rows / 256), ceil(K / RK), batch).
+constexpr int RK = 64;
+__global__ void __launch_bounds__(256) oz_rowmax_rmaj_kernel(OzView v, int rows, long long K,
+                                                             int *__restrict__ ef) {
+  const int b = blockIdx.z;
+  const long long r = (long long)blockIdx.x * 256 + threadIdx.x;
+  const long long k0 = (long long)blockIdx.y * RK;
+  if (r >= rows) return;
+  long long k1 = k0 / v.k2pad, k2 = k0 - k1 * v.k2pad;
+  const int kn = (int)(K - k0 < RK ? K - k0 : RK);
+  int m = 0;
+#pragma unroll 8
+  for (int u = 0; u < kn; ++u) {
+    m = max(m, ef_of(view_at(v, b, r, k1, k2)));
+    if (++k2 == v.k2pad) {
+      k2 = 0;
+      ++k1;
+    }
+  }
+  if (m > 0) atomicMax(&ef[(long long)b * rows + r], m);
+}
+
+// Short rows (K <= SHORT_K, one K segment) of a row-contiguous source in one
+// pass: a block stages 16 whole rows in shared memory (coalesced 128-byte
+// reads across the rows), takes each row's maximum there and writes the
+// digits along K in 16-byte stores; ef is written, not accumulated.
+constexpr int SHORT_K = 256, SHORT_R = 16;
+__global__ void __launch_bounds__(256) oz_slice_short_kernel(OzView v, int rows, long long K,
+                                                             int *__restrict__ ef,
+                                                             __nv_bfloat16 *__restrict__ out,
+                                                             long long ld, long long g1) {
+  __shared__ double s[SHORT_K][SHORT_R + 1];
+  __shared__ int wm[256 / SHORT_R][SHORT_R];
+  __shared__ int es[SHORT_R];
+  const int b = blockIdx.z;
+  const long long r0 = (long long)blockIdx.x * SHORT_R;
+  const int t = threadIdx.x, kn = (int)K;
+#pragma unroll 4
+  for (int idx = t; idx < SHORT_R * kn; idx += 256) {
+    const int r = idx % SHORT_R, kk = idx / SHORT_R;
+    s[kk][r] = r0 + r < rows ? view_at(v, b, r0 + r, 0, kk) : 0.0;
+  }
+  __syncthreads();
+  {
+    const int r = t % SHORT_R, part = t / SHORT_R;
+    int m = 0;
+    for (int kk = part; kk < kn; kk += 256 / SHORT_R) m = max(m, ef_of(s[kk][r]));
+    wm[part][r] = m;
+  }
+  __syncthreads();
+  if (t < SHORT_R) {
+    int m = 0;
+    for (int q = 0; q < 256 / SHORT_R; ++q) m = max(m, wm[q][t]);
+    es[t] = m;
+    if (r0 + t < rows) ef[(long long)b * rows + r0 + t] = m;
+  }
+  __syncthreads();
+  const int cpr = (int)(ld / KC);
+  for (int c = t; c < SHORT_R * cpr; c += 256) {
+    const int r = c / cpr, k0 = (c - r * cpr) * KC;
+    if (r0 + r >= rows) continue;
+    const int e = row_scale(es[r]);
+    uint32_t w[OZ_S][KC / 2];
+#pragma unroll
+    for (int u = 0; u < KC; u += 2) {
+      float d0[OZ_S], d1[OZ_S];
+      digits_of(k0 + u < kn ? s[k0 + u][r] : 0.0, e, d0);
+      digits_of(k0 + u + 1 < kn ? s[k0 + u + 1][r] : 0.0, e, d1);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[p], d1[p]);
+        w[p][u / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+      }
+    }
+    const long long blk = ((long long)b * rows + r0 + r) * (ld / 16) + (k0 >> 4);
+    if (!OZ_IN(blk * 64 + 63, g1, 34)) continue;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p)
+      *reinterpret_cast<uint4 *>(out + digit_off(blk, k0 & 15, p, g1)) =
+          make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+}
+
 // ---------------------------------------------------- exchange operand -----
 __global__ void oz_exch_gather_kernel(int n, int bk, int nl16, int jtiles, long long kx,
                                       const double *__restrict__ D, int P,
@@ -902,8 +988,20 @@ cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
     ++launch_counter();
     return cudaGetLastError();
   }
-  dim3 gm(ceil_div(out.K, SK), ceil_div(out.rows, SR), out.batch);
-  oz_rowmax_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
+  if (v.rs == 1 && v.k2off == 0 && v.k2pad >= out.K && out.K <= SHORT_K && out.ld <= SHORT_K) {
+    dim3 g(ceil_div(out.rows, SHORT_R), 1, out.batch);
+    oz_slice_short_kernel<<<g, 256, 0, s>>>(v, out.rows, out.K, out.ef, out.d, out.ld, g1);
+    ++launch_counter();
+    return cudaGetLastError();
+  }
+  if (v.rs == 1) {
+    if (ceil_div(out.K, RK) > 65535) return cudaErrorInvalidValue;
+    dim3 gm(ceil_div(out.rows, 256), ceil_div(out.K, RK), out.batch);
+    oz_rowmax_rmaj_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
+  } else {
+    dim3 gm(ceil_div(out.K, SK), ceil_div(out.rows, SR), out.batch);
+    oz_rowmax_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
+  }
   ++launch_counter();
   RS_TRY(cudaGetLastError());
   // the digit pass covers the padding columns K..ld too (zeros)

@@ -255,6 +255,24 @@ cudaError_t tc_make_map(CUtensorMap *m, int kind, const TcOperand &op, int K, in
 }
 
 
+cudaError_t tc_make_out_map(CUtensorMap *m, void *base, int elem_bytes, long long cols,
+                            long long rows, long long batch, long long ld) {
+  if (!g_encode) return cudaErrorNotSupported;
+  if ((elem_bytes != 4 && elem_bytes != 2) || (uintptr_t)base % 16 || (ld * elem_bytes) % 16 ||
+      cols <= 0 || rows <= 0 || batch <= 0 || cols > ld)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * elem_bytes), (cuuint64_t)(ld * rows * elem_bytes)};
+  cuuint32_t box[3] = {16, 32, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = g_encode(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                              3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 bool tc_available() {
   std::call_once(g_encode_once, load_encode);
   return g_encode != nullptr;

@@ -12,8 +12,11 @@
 //                  so that the products of tile i+1 run while the epilogue
 //                  drains tile i;
 //   warps 2-5      epilogue: tcgen05.ld of the accumulator (warp w reads lanes
-//                  32 (w mod 4) ...), stores of fp32 and/or operand-type
-//                  outputs, then release of the accumulator.
+//                  32 (w mod 4) ...), 16 columns at a time, staged through a
+//                  double-buffered 32-row x 16-column box in shared memory
+//                  and written by TMA bulk tensor stores (fp32 and/or
+//                  operand-type outputs; plain stores where an output's rows
+//                  are not 16-byte aligned), then release of the accumulator.
 // Every mbarrier wait is bounded; on expiry the kernel records an error code
 // in a device flag and stops; before tensor memory is freed the epilogue
 // waits (bounded) for every product the issuer started.
@@ -33,6 +36,11 @@ using namespace tcx;
 
 constexpr int GTHREADS = 192;  // 6 warps
 constexpr int ACC_COLS = 256;  // per accumulator (max N tile)
+// epilogue staging per warp and buffer: 32 x 16 fp32 (c32) + 32 x 16 fp32
+// or bf16 (operand-type output)
+constexpr int STG_HALF = 32 * 16 * 4;
+constexpr int STG_BUF = 2 * STG_HALF;
+constexpr int STG_WARP = 2 * STG_BUF;
 
 struct GProb {
   CUtensorMap ta[2], tb[2];
@@ -42,6 +50,8 @@ struct GProb {
   float *c32;
   void *cop;
   long long ldcop;
+  CUtensorMap t32, top;  // output maps (valid where tma bit 0 / bit 1 is set)
+  int tma;
 };
 
 struct GParams {
@@ -67,11 +77,12 @@ __device__ __forceinline__ Tile decode(const GParams &p, int q) {
   return t;
 }
 
+// Plain stores of one row's 16 columns (the outputs whose tma bit is clear).
 template <int KIND>
 __device__ void epilogue_store(const GProb &P, int z, int row, int col0, const uint32_t *r) {
   const long long MN = (long long)P.M * P.N;
   const bool full16 = col0 + 16 <= P.N;
-  if (P.c32) {
+  if (P.c32 && !(P.tma & 1)) {
     float *dst = P.c32 + z * MN + (long long)row * P.N + col0;
     if (full16 && (P.N % 4) == 0) {
 #pragma unroll
@@ -85,7 +96,7 @@ __device__ void epilogue_store(const GProb &P, int z, int row, int col0, const u
         if (col0 + j < P.N) dst[j] = __uint_as_float(r[j]);
     }
   }
-  if (P.cop && KIND == TC_BF16) {
+  if (P.cop && !(P.tma & 2) && KIND == TC_BF16) {
     __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(P.cop) + z * (long long)P.M * P.ldcop +
                          (long long)row * P.ldcop + col0;
     if (full16 && (P.ldcop % 8) == 0) {
@@ -107,7 +118,7 @@ __device__ void epilogue_store(const GProb &P, int z, int row, int col0, const u
         if (col0 + j < P.N) dst[j] = __float2bfloat16_rn(__uint_as_float(r[j]));
     }
   }
-  if (P.cop && KIND == TC_TF32) {
+  if (P.cop && !(P.tma & 2) && KIND == TC_TF32) {
     float *dst = static_cast<float *>(P.cop) + z * (long long)P.M * P.ldcop +
                  (long long)row * P.ldcop + col0;
 #pragma unroll
@@ -131,6 +142,7 @@ __global__ void __launch_bounds__(GTHREADS, 1) tc_group_kernel(const __grid_cons
   uint64_t *acce = accf + 2;   // [2] accumulator drained
   uint64_t *done = acce + 2;   // every product of this CTA completed
   uint32_t *tslot = (uint32_t *)(done + 1);
+  uint8_t *stg = sB + S * B_STAGE + 1024;  // epilogue staging, 1024-byte aligned
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -244,8 +256,9 @@ __global__ void __launch_bounds__(GTHREADS, 1) tc_group_kernel(const __grid_cons
   } else {
     // epilogue warps 2-5
     const int lq = warp & 3;
+    uint8_t *wst = stg + (warp - 2) * STG_WARP;
     bool ok = true;
-    int lt = 0;
+    int lt = 0, sc = 0;  // tiles and staged chunks of this warp
     for (int q = blockIdx.x; q < p.total && ok; q += gridDim.x, ++lt) {
       const Tile t = decode(p, q);
       const GProb &P = p.p[t.pi];
@@ -255,8 +268,8 @@ __global__ void __launch_bounds__(GTHREADS, 1) tc_group_kernel(const __grid_cons
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int row = t.m0 + lq * 32 + lane;
-      for (int c0 = 0; c0 < P.BN; c0 += 16) {
+      const int row0 = t.m0 + lq * 32, row = row0 + lane;
+      for (int c0 = 0; c0 < P.BN && t.n0 + c0 < P.N; c0 += 16) {
         uint32_t r[16];
         const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * ACC_COLS + c0);
         asm volatile(
@@ -267,12 +280,61 @@ __global__ void __launch_bounds__(GTHREADS, 1) tc_group_kernel(const __grid_cons
               "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < P.M && t.n0 + c0 < P.N) epilogue_store<KIND>(P, t.z, row, t.n0 + c0, r);
+        if (P.tma && row0 < P.M) {
+          // this row into the staging box, then one bulk store per output
+          uint8_t *sbuf = wst + (sc & 1) * STG_BUF;
+          if (sc >= 2) {
+            if (lane == 0) bulk_wait_read1();  // the box two chunks back has been read
+            __syncwarp();
+          }
+          if (P.tma & 1) {
+            uint4 *d = reinterpret_cast<uint4 *>(sbuf + lane * 64);
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              d[v] = make_uint4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+          }
+          if (P.tma & 2) {
+            if (KIND == TC_BF16) {
+              uint4 *d = reinterpret_cast<uint4 *>(sbuf + STG_HALF + lane * 32);
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                uint32_t w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const __nv_bfloat162 h2 = __floats2bfloat162_rn(
+                      __uint_as_float(r[8 * v + 2 * u]), __uint_as_float(r[8 * v + 2 * u + 1]));
+                  w[u] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                d[v] = make_uint4(w[0], w[1], w[2], w[3]);
+              }
+            } else {
+              float4 *d = reinterpret_cast<float4 *>(sbuf + STG_HALF + lane * 64);
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                d[v] = make_float4(round_tf32(__uint_as_float(r[4 * v])),
+                                   round_tf32(__uint_as_float(r[4 * v + 1])),
+                                   round_tf32(__uint_as_float(r[4 * v + 2])),
+                                   round_tf32(__uint_as_float(r[4 * v + 3])));
+            }
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            if (P.tma & 1) tma_store3(&P.t32, sbuf, t.n0 + c0, row0, t.z);
+            if (P.tma & 2) tma_store3(&P.top, sbuf + STG_HALF, t.n0 + c0, row0, t.z);
+            bulk_commit();
+          }
+          ++sc;
+        }
+        if (row < P.M && (P.tma & 3) != 3) epilogue_store<KIND>(P, t.z, row, t.n0 + c0, r);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(&acce[buf])) : "memory");
     }
+    // the bulk stores are complete (and done reading shared memory)
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
     // every product the issuer started is complete before tensor memory is freed
     bar_wait(done, 0, p.err, 5, p.wait_polls);
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -285,7 +347,8 @@ __global__ void __launch_bounds__(GTHREADS, 1) tc_group_kernel(const __grid_cons
 }
 
 size_t group_smem(int stages) {
-  return 1024 + (size_t)stages * (A_STAGE + ACC_COLS * SLAB) + 256;
+  // alignment slack, stages, barriers (1024), epilogue staging
+  return 1024 + (size_t)stages * (A_STAGE + ACC_COLS * SLAB) + 1024 + 4 * STG_WARP;
 }
 
 cudaError_t group_prepare() {
@@ -374,6 +437,13 @@ cudaError_t launch_group(int kind, const TcProb *probs, int np, int *err, cudaSt
     P.c32 = t.c32;
     P.cop = t.cop;
     P.ldcop = t.ldcop ? t.ldcop : t.N;
+    // outputs whose rows are 16-byte aligned are written by TMA stores
+    P.tma = 0;
+    const long long zc = ceil_div(t.batch, t.bpc);
+    if (t.c32 && tc_make_out_map(&P.t32, t.c32, 4, t.N, t.M, zc, t.N) == cudaSuccess) P.tma |= 1;
+    if (t.cop && tc_make_out_map(&P.top, t.cop, kind == TC_BF16 ? 2 : 4, t.N, t.M, zc,
+                                 P.ldcop) == cudaSuccess)
+      P.tma |= 2;
     const long long tiles = (long long)P.mtiles * P.ntiles * ceil_div(t.batch, t.bpc);
     if (total + tiles > (1LL << 30)) return cudaErrorInvalidValue;
     total += (int)tiles;

@@ -74,6 +74,30 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *m, uint6
       "l"(m), "r"(s_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+// Bulk tensor store of a shared-memory box to global (bulk-group tracked).
+__device__ __forceinline__ void tma_store3(const CUtensorMap *m, const void *src, int x, int y,
+                                           int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(m),
+      "r"(s_u32(src)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until at most one committed group still reads shared memory.
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+// Waits until every committed group has completed.
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+// Orders this thread's generic-proxy shared-memory writes before later
+// async-proxy (TMA) reads of them.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
 // of 128 bytes grouped by 8 (stride 1024 bytes between groups).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
@@ -106,5 +130,10 @@ __device__ __forceinline__ float round_tf32(float x) {
 // contiguous) for 128-byte swizzled slabs of box_rows rows.
 cudaError_t tc_make_map(CUtensorMap *m, int kind, const TcOperand &op, int K, int batch,
                         int box_rows);
+// Tensor map of an output [batch][rows][ld] (elements of elem_bytes = 4:
+// fp32, 2: bf16; cols <= ld valid per row) for stores of 32-row x 16-column
+// boxes, no swizzle.  ld * elem_bytes and the base must be 16-byte aligned.
+cudaError_t tc_make_out_map(CUtensorMap *m, void *base, int elem_bytes, long long cols,
+                            long long rows, long long batch, long long ld);
 
 }  // namespace rssri

@@ -27,7 +27,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["System", "make_system", "tau_grid", "CONFIGS", "MANY", "many_sizes"]
+__all__ = ["System", "make_system", "make_system_torch", "tau_grid", "CONFIGS", "MANY", "C4",
+           "many_sizes"]
 
 
 @dataclass
@@ -90,6 +91,41 @@ def make_system(n: int, n_occ: int, n_aux: int, n_tau: int, input_seed: int = 0,
                   mu=0.5 * (gap_lo + gap_hi), beta=beta, tau=tau, tau_w=tau_w)
 
 
+def make_system_torch(n: int, n_occ: int, n_aux: int, n_tau: int, input_seed: int = 0,
+                      device: str = "cuda", beta: float = 50.0, tau_s: float = 0.5,
+                      decay: float = 3.0, gap_lo: float = -0.2, gap_hi: float = 0.2) -> System:
+    """The recipe of make_system drawn on `device` with a seeded torch
+    generator (other numbers than make_system's, the same distribution and
+    structure): for the many-chain workload, whose largest (ij|A) (12 GB at
+    N = 800) would take minutes to draw and copy from the host.  Arrays are
+    float64 torch tensors on `device`; tau and its weights as in tau_grid."""
+    import torch
+
+    if not (0 < n_occ < n):
+        raise ValueError("need 0 < n_occ < n")
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(input_seed))
+    f64 = dict(dtype=torch.float64, device=device)
+    eri3 = torch.randn((n, n, n_aux), generator=gen, **f64)
+    iu, ju = torch.triu_indices(n, n, 1, device=device)
+    eri3[ju, iu, :] = eri3[iu, ju, :]
+    idx = torch.arange(n, **f64)
+    damp = torch.exp(-torch.abs(idx[:, None] - idx[None, :]) / decay) / float(np.sqrt(n_aux))
+    eri3 *= damp[:, :, None]
+    b = torch.randn((n_aux, n_aux), generator=gen, **f64)
+    metric = b @ b.T / n_aux + 0.5 * torch.eye(n_aux, **f64)
+    metric = (0.5 * (metric + metric.T)).contiguous()
+    del b
+    orb_e = torch.cat([torch.linspace(-1.0, gap_lo, n_occ, **f64),
+                       torch.linspace(gap_hi, 2.0, n - n_occ, **f64)])
+    q, r = torch.linalg.qr(torch.randn((n, n), generator=gen, **f64))
+    q = (q * torch.sign(torch.diagonal(r))[None, :]).contiguous()
+    tau, tau_w = tau_grid(n_tau, beta, tau_s)
+    return System(n=n, n_occ=n_occ, n_aux=n_aux, eri3=eri3.contiguous(), metric=metric,
+                  orb_e=orb_e.contiguous(), orb_c=q, mu=0.5 * (gap_lo + gap_hi), beta=beta,
+                  tau=torch.from_numpy(tau).to(device), tau_w=torch.from_numpy(tau_w).to(device))
+
+
 def mlp_init(seed: int = 0, zero_output: bool = True) -> np.ndarray:
     """Initial parameters of the control-variate network as the flat float32
     layout W0[256][10] b0[256] W1[256][256] b1 W2[256][256] b2 W3[1][256] b3[1]:
@@ -136,6 +172,9 @@ CONFIGS = {
 # of minutes): K chains with N_k spread evenly over [n_min, n_max], N_aux = 3N,
 # n_occ = N/2, input seed k.
 MANY = dict(k=16, n_min=64, n_max=256, n_tau=16, n_s=64, eps=1e-3, eps_prime=0.02)
+# The many-chain workload: 64 chains, N_k = 100 + round(700 k / 63), n_occ = N/2,
+# N_aux = 3N, 64 tau points, 200 sample pairs each, eps = 1e-3.
+C4 = dict(k=64, n_min=100, n_max=800, n_tau=64, n_s=200, eps=1e-3, eps_prime=0.02)
 
 
 def many_sizes(k: int, n_min: int, n_max: int):

@@ -161,3 +161,43 @@ def test_cv_estimator_tensor_core_chain_against_oracle(B, prec):
     e_ref = energy(tr)
     scale = abs(energy(tr_chain)) + abs(energy(tr_cv))
     assert abs(got["e"] - e_ref) < 5 * u * scale, (got["e"], e_ref, scale)
+
+
+def test_learned_cv_lowers_the_stderr_on_independent_draws(B):
+    """Trained on one run (seed 777), the network's c lowers the spread of the
+    per-pair energies, and so the standard error of E_corr, on independent
+    draws: the same draws with and without it, for three seeds, on the N=200
+    workload at the paper's eps = 0.1 (Sec. IV), where the large part leaves
+    most of the variance to the stochastic remainder.  (At eps = 1e-3 the
+    deterministic part takes almost all of it and c = 1 is already near
+    optimal.)  bf16 chain and sliced block, as in the chosen form."""
+    cfg = synth.CONFIGS["c2_n200"]
+    s = synth.make_system(cfg["n"], cfg["n_occ"], cfg["n_aux"], cfg["n_tau"], input_seed=0)
+    dev = [torch.from_numpy(a).cuda() for a in (s.eri3, s.metric, s.orb_e, s.orb_c, s.tau,
+                                                 s.tau_w)]
+    ns, epsp, eps = cfg["n_s"], cfg["eps_prime"], 0.1
+    h = B.Handle(0)
+    try:
+        tr = B.Handle.options(epsp, eps, ns, 777, precision=B.RSSRI_PREC_DF64,
+                              dd_arith=B.RSSRI_DD_OZ)
+        h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=tr)
+        before, after = h.cv_train(tr, synth.mlp_init(0), 400, 4096, 1e-3)
+        assert after < 0.5 * before, (before, after)
+        sig = torch.empty((s.n_tau, s.n, s.n), dtype=torch.float64, device="cuda")
+        ep = torch.empty(ns, dtype=torch.float64, device="cuda")
+        ratios = []
+        for seed in (5, 6, 7):
+            out = {}
+            for cvf in (0, 1):
+                o = B.Handle.options(epsp, eps, ns, seed, precision=B.RSSRI_PREC_BF16,
+                                     dd_arith=B.RSSRI_DD_OZ, cv=cvf)
+                e, se, _ = h.sigma(o, sig, ep)
+                out[cvf] = (e, se, ep.cpu().numpy().copy())
+            ratios.append(np.std(out[0][2]) / np.std(out[1][2]))
+            # both estimates are of the same mean: within their combined error
+            assert abs(out[0][0] - out[1][0]) < 4 * (out[0][1] ** 2 + out[1][1] ** 2) ** 0.5
+        print("paired per-pair-energy sd ratios plain / learned:", ratios)
+        # measured on this workload: 1.077, 1.131, 1.054
+        assert min(ratios) > 1.02 and np.mean(ratios) > 1.04, ratios
+    finally:
+        h.close()
