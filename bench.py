@@ -372,7 +372,12 @@ def c4_run(args):
                 "pairs_kept": st["n_pairs_large"]}
 
     one(100, 1000)
-    chains = [one(n, k) for k, n in enumerate(sizes)]
+    chains = []
+    for k, n in enumerate(sizes):
+        chains.append(one(n, k))
+        c = chains[-1]
+        print(f"chain {k} N={n}: setup {c['setup_s']:.3f} s, sampling {c['sample_s']:.3f} s",
+              file=sys.stderr, flush=True)
     units = len(chains) * m["n_s"] * m["n_tau"]
     t_setup = sum(c["setup_s"] for c in chains)
     t_samp = sum(c["sample_s"] for c in chains)

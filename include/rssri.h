@@ -271,6 +271,11 @@ RSSRI_API void rssri_destroy(rssri_handle *h);
 /* Static description of a status code. */
 RSSRI_API const char *rssri_status_string(int code);
 
+/* Name of the last CUDA runtime error that made a call of this thread return
+ * RSSRI_ERR_CUDA or RSSRI_ERR_OOM (cudaGetErrorName), or "" if none has;
+ * for diagnostics.  The string is static. */
+RSSRI_API const char *rssri_last_cuda_error(void);
+
 /* ----------------------------------------------------------- the path */
 
 /* Steps that depend only on the system, the thresholds and G:

@@ -75,6 +75,7 @@ SIGNATURES = {
     "rssri_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "rssri_destroy": (None, [C.c_void_p]),
     "rssri_status_string": (C.c_char_p, [C.c_int]),
+    "rssri_last_cuda_error": (C.c_char_p, []),
     "rssri_setup": (C.c_int, [C.c_void_p, C.POINTER(rssri_problem), C.POINTER(rssri_options)]),
     "rssri_sigma": (C.c_int, [C.c_void_p, C.POINTER(rssri_options), C.c_void_p, C.c_void_p,
                               C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -128,6 +129,8 @@ def lib() -> C.CDLL:
 class RssriError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = lib().rssri_status_string(code).decode()
+        if code in (-4, -5):  # OOM, CUDA: name the runtime error
+            msg += ": " + lib().rssri_last_cuda_error().decode()
         super().__init__(f"{where}: {STATUS.get(code, code)} ({msg})")
         self.code = code
 

@@ -18,6 +18,18 @@
 using namespace rssri;
 
 namespace {
+thread_local char g_err_site[96] = "";
+}  // namespace
+
+namespace rssri {
+void note_error_site(const char *file, int line) {
+  if (g_err_site[0]) return;
+  const char *base = std::strrchr(file, '/');
+  std::snprintf(g_err_site, sizeof g_err_site, "%s:%d", base ? base + 1 : file, line);
+}
+}  // namespace rssri
+
+namespace {
 
 struct DevBuf {
   void *p = nullptr;
@@ -55,8 +67,13 @@ void release(DevBuf &b) {
   b.bytes = 0;
 }
 
+thread_local char g_last_cuda[192] = "";
+
 int map_err(cudaError_t e) {
   if (e == cudaSuccess) return RSSRI_OK;
+  std::snprintf(g_last_cuda, sizeof g_last_cuda, "%s%s%s", cudaGetErrorName(e),
+                g_err_site[0] ? " at " : "", g_err_site);
+  g_err_site[0] = 0;
   if (e == cudaErrorMemoryAllocation) return RSSRI_ERR_OOM;
   return RSSRI_ERR_CUDA;
 }
@@ -112,6 +129,7 @@ struct rssri_handle {
   // double-float chain: factor pairs, X G and C pairs, (2tI - B) pairs
   DevBuf facHl, xgHl, cHl, bHl;
   bool d_df64_ready = false;
+  bool kp_hl_ready = false;  // K_P as pairs (KPhl) made for this setup
   // bf16 chain buffers
   DevBuf hxsl, hy3, hg, hgb, hP, hdc32, hcl32, hdcl16, hxy32, ha6, hct, hdct, hpart, hfold;
   DevBuf hclt, hfl;  // learned control variate on the tensor-core chain: (C^L)^T, F^L per pair
@@ -144,6 +162,7 @@ struct rssri_handle {
   DevBuf oz_gs, oz_gexp;  // G(tau) 2^-e(tau) as pairs, and e(tau), for K^Q G
   DevBuf oz_pidx, oz_tmp;
   OzBuf ozX, ozKP, ozKPt, ozGb, ozBig0, ozBig1, ozAtP, ozGam;
+  OzBuf ozPA, ozPB;  // operands of the setup and factor products (RSSRI_DD_OZ)
   rssri_stats stats{};
 
   // per-class launch counts and (when profiling) event timings
@@ -298,6 +317,12 @@ cudaError_t gemm_p(rssri_handle *h, int cls, const GemmArgs &g) {
   return gemm(h, g);
 }
 
+cudaError_t oz_product(rssri_handle *h, int cls, const OzView &va, int batch, int M,
+                       const OzView *vb, int N, long long K, double *C, long long ldc,
+                       long long sC, int *err);
+OzView oz_rows(const double *x, long long ld, long long K, long long len);
+OzView oz_cols(const double *x, long long ld, long long K, long long len);
+
 // ------------------------------------------------------------ S1: V^-1/2 --
 // Coupled Newton-Schulz iteration for the inverse square root: with
 // Y_0 = V / c, Z_0 = I and T_k = (3 I - Z_k Y_k) / 2, Y_{k+1} = Y_k T_k and
@@ -313,7 +338,7 @@ int metric_inv_sqrt(rssri_handle *h, int *rc, bool df64) {
 #define RS_CK(x)                     \
   do {                               \
     e = (x);                         \
-    if (e != cudaSuccess) return map_err(e); \
+    if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); } \
   } while (0)
   RS_CK(ensure(h->W, bytes));
   RS_CK(ensure(h->nsY, bytes));
@@ -390,6 +415,8 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
 
 extern "C" {
 
+const char *rssri_last_cuda_error(void) { return g_last_cuda; }
+
 const char *rssri_status_string(int code) {
   switch (code) {
     case RSSRI_OK: return "ok";
@@ -428,7 +455,7 @@ int rssri_create(rssri_handle **out, int device, void *stream) {
   if (e == cudaSuccess) e = cudaMallocHost(&h->host_res, 8 * sizeof(double));
   if (e != cudaSuccess) {
     rssri_destroy(h);
-    return map_err(e);
+    { note_error_site(__FILE__, __LINE__); return map_err(e); }
   }
   *out = h;
   return RSSRI_OK;
@@ -452,6 +479,13 @@ void rssri_destroy(rssri_handle *h) {
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
                     &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss, &h->sdd0, &h->oz_gs, &h->oz_gexp};
   for (DevBuf *b : bufs) release(*b);
+  release(h->oz_pidx);
+  release(h->oz_tmp);
+  for (rssri_handle::OzBuf *o : {&h->ozX, &h->ozKP, &h->ozKPt, &h->ozGb, &h->ozBig0, &h->ozBig1,
+                                 &h->ozAtP, &h->ozGam, &h->ozPA, &h->ozPB}) {
+    release(o->d);
+    release(o->e);
+  }
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto e : h->evpool) cudaEventDestroy(e);
@@ -475,6 +509,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   h->ready = false;
   h->have_sigma = false;
   h->d_df64_ready = false;
+  h->kp_hl_ready = false;
   h->block_ok = false;
   h->gg_valid = false;
   h->oz_ready = false;
@@ -485,6 +520,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   do {                                                 \
     e = (x);                                           \
     if (e != cudaSuccess) {                            \
+      note_error_site(__FILE__, __LINE__);             \
       int _r = map_err(e);                             \
       if (_r == RSSRI_ERR_CUDA) h->broken = true;      \
       return _r;                                       \
@@ -571,6 +607,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   if (P_s > 0) {
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(eri_gather_rows(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime,
                           h->spairs.as<int>(), P_s, h->EL.as<double>(), s)); }
+    // in IEEE fp64 in every form: the cut of Eq. 13 compares these values
     GemmArgs g;
     g.M = P_s; g.N = na; g.K = na;
     g.A = h->EL.as<double>(); g.lda = na;
@@ -599,9 +636,16 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_int(h->spairs.as<int>(), h->lidx.as<int>(), P, h->pij.as<int>(), s)); }
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(gather_rows(h->KLs.as<double>(), h->lidx.as<int>(), P, na, h->KP.as<double>(), s)); }
     // D[a][b] = sum_Q K_P[a][Q] K_P[b][Q] = v^L for the pair of pairs (Eq. 8 on [K]^L),
-    // in the arithmetic the deterministic block is asked to use (double-float
-    // for the sliced block too)
-    if (o->dd_arith != RSSRI_DD_FP64) {
+    // in the arithmetic the deterministic block is asked to use
+    if (o->dd_arith == RSSRI_DD_OZ) {
+      RS_CK(oz_product(h, RSSRI_PROF_SETUP_GEMM,
+                       oz_rows(h->KP.as<double>(), na, na, (long long)P * na), 1, P, nullptr, P,
+                       na, h->D.as<double>(), P, 0, h->flags.as<int>() + 5));
+      // K_P as pairs for the block's one double-float product (K^Q G)
+      RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
+      { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s, range_flag(h))); }
+      h->kp_hl_ready = true;
+    } else if (o->dd_arith != RSSRI_DD_FP64) {
       RS_CK(ensure(h->Dhl, (size_t)P * P * sizeof(float2)));
       RS_CK(ensure(h->KPhl, (size_t)P * na * sizeof(float2)));
       { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), s, range_flag(h))); }
@@ -616,6 +660,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
       }
       { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s, range_flag(h))); }
       h->d_df64_ready = true;
+      h->kp_hl_ready = true;
     } else {
       GemmArgs g;
       g.M = P; g.N = P; g.K = na;
@@ -851,6 +896,44 @@ cudaError_t oz_gemm_p(rssri_handle *h, int cls, const OzGemm &g_in) {
   return oz_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
 }
 
+// C[b sC + i ldc + j] = sum_k A_b(i, k) B(j, k), fp64-accurate on the tensor
+// cores (digit slicing), for slicer views A (batch x M x K) and B (N x K,
+// shared by the batch; null: B is A with batch 1).  The digit buffers grow
+// as needed.  err: device flag of the bounded waits.
+cudaError_t oz_product(rssri_handle *h, int cls, const OzView &va, int batch, int M,
+                       const OzView *vb, int N, long long K, double *C, long long ldc,
+                       long long sC, int *err) {
+  RS_TRY(oz_make(h->ozPA, batch, M, K));
+  RS_TRY(oz_slice_p(h, va, h->ozPA.v));
+  OzGemm g;
+  g.A = h->ozPA.v;
+  if (vb) {
+    RS_TRY(oz_make(h->ozPB, 1, N, K));
+    RS_TRY(oz_slice_p(h, *vb, h->ozPB.v));
+    g.B = h->ozPB.v;
+  } else {
+    g.B = h->ozPA.v;
+  }
+  g.M = M; g.N = N; g.batch = batch;
+  g.C = C; g.ldc = ldc; g.sC = sC;
+  g.ccap = (long long)(batch - 1) * sC + (long long)(M - 1) * ldc + N;
+  g.err = err;
+  return oz_gemm_p(h, cls, g);
+}
+
+// Slicer views of a row-major matrix (rows of K at stride ld) and of the
+// transpose of one (element (j, k) = x[k ld + j]).
+OzView oz_rows(const double *x, long long ld, long long K, long long len) {
+  OzView v;
+  v.x = x; v.rs = ld; v.cs2 = 1; v.k2pad = v.k2n = K; v.xlen = len;
+  return v;
+}
+OzView oz_cols(const double *x, long long ld, long long K, long long len) {
+  OzView v;
+  v.x = x; v.rs = 1; v.cs2 = ld; v.k2pad = v.k2n = K; v.xlen = len;
+  return v;
+}
+
 // Setup of the sliced block: the pair index map, the band half-width, the
 // exchange contraction's left operand (from D) and the digits of K_P and K_P^T.
 int oz_setup(rssri_handle *h) {
@@ -860,7 +943,7 @@ int oz_setup(rssri_handle *h) {
 #define RS_CK(x)                     \
   do {                               \
     e = (x);                         \
-    if (e != cudaSuccess) return map_err(e); \
+    if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); } \
   } while (0)
   RS_CK(ensure(h->oz_pidx, (size_t)n * n * sizeof(int)));
   { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(oz_pair_index(h->pij.as<int>(), P, n, h->oz_pidx.as<int>(), s)); }
@@ -1012,6 +1095,18 @@ cudaError_t ensure_d_df64(rssri_handle *h) {
   RS_TRY(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), h->stream, range_flag(h)));
   RS_TRY(to_df64(h->KP.as<double>(), (long long)P * na, h->KPhl.as<float2>(), h->stream, range_flag(h)));
   h->d_df64_ready = true;
+  h->kp_hl_ready = true;
+  return cudaSuccess;
+}
+
+// K_P as pairs only (the sliced block's K^Q G product).
+cudaError_t ensure_kp_df64(rssri_handle *h) {
+  if (h->kp_hl_ready || h->P == 0) return cudaSuccess;
+  RS_TRY(ensure(h->KPhl, (size_t)h->P * h->n_aux * sizeof(float2)));
+  SPAN(RSSRI_PROF_OTHER, 0.0);
+  RS_TRY(to_df64(h->KP.as<double>(), (long long)h->P * h->n_aux, h->KPhl.as<float2>(), h->stream,
+                 range_flag(h)));
+  h->kp_hl_ready = true;
   return cudaSuccess;
 }
 
@@ -1047,7 +1142,7 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
 #define RS_CK(x)                     \
   do {                               \
     e = (x);                         \
-    if (e != cudaSuccess) return map_err(e); \
+    if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); } \
   } while (0)
   RS_CK(ensure(h->G, (size_t)nt * nn * sizeof(double)));
   RS_CK(ensure(h->Gb, (size_t)nt * nn * sizeof(double)));
@@ -1059,7 +1154,7 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
       RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
       RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
       RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
-      RS_CK(ensure_d_df64(h));
+      RS_CK(ensure_kp_df64(h));
       if (!h->oz_ready) {
         const int rc = oz_setup(h);
         if (rc) return rc;
@@ -1078,7 +1173,6 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
       h->ozBig1.v.ef = h->ozBig1.e.as<int>();
       RS_CK(oz_make(h->ozAtP, 1, na, P));
       RS_CK(oz_make(h->ozGam, 1, na, na));
-      RS_CK(cudaMemsetAsync(h->flags.as<int>() + 5, 0, sizeof(int), s));
     } else if (!dd_df64) {  // the double-float block keeps these as pairs
       RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
       RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
@@ -1562,6 +1656,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   do {                                                 \
     e = (x);                                           \
     if (e != cudaSuccess) {                            \
+      note_error_site(__FILE__, __LINE__);             \
       int _r = map_err(e);                             \
       if (_r == RSSRI_ERR_CUDA) h->broken = true;      \
       return _r;                                       \
@@ -1572,6 +1667,8 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   h->ev_used = 0;
   h->prof_on = o->profile != 0;
   RS_CK(cudaMemsetAsync(range_flag(h), 0, 3 * sizeof(int), s));
+  // bounded-wait flags of the tensor-core kernels: 4 sampling, 5 block
+  RS_CK(cudaMemsetAsync(h->flags.as<int>() + 4, 0, 2 * sizeof(int), s));
   RS_CK(cudaEventRecord(h->ev[2], s));
   // ---- buffers
   RS_CK(ensure(h->sig_raw, (size_t)nt * nn * sizeof(double)));
@@ -1633,7 +1730,21 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   double *theta = h->theta.as<double>(), *Ut = h->Ut.as<double>(), *fac = h->fac.as<double>();
   for (int set = 0; set < 2; ++set)
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(rademacher(o->seed, set, o->xi_offset, ns, na, theta + (long long)set * ns * na, s)); }
-  {
+  // the factor products in the block's arithmetic: IEEE fp64, double-float
+  // (operands split into pairs first), or sliced on the tensor cores
+  // (sliced only under a bf16 / tf32 chain, which rounds R and R^L to 8 or
+  // 11 bits anyway: the sliced products carry ~1e-12 of their row scales,
+  // which an fp64-accurate chain would see in R^S = R - R^L)
+  const bool fac_oz = o->dd_arith == RSSRI_DD_OZ && bf16;
+  const bool fac_df64 = o->dd_arith != RSSRI_DD_FP64 && !fac_oz;
+  int *tc_err = h->flags.as<int>() + 4;
+  if (fac_oz) {
+    OzView vt = oz_rows(theta, na, na, 2LL * ns * na);
+    vt.bs = (long long)ns * na;
+    const OzView vw = oz_cols(h->W.as<double>(), na, na, (long long)na * na);
+    RS_CK(oz_product(h, RSSRI_PROF_FACTOR_GEMM, vt, 2, ns, &vw, na, na, Ut, na,
+                     (long long)ns * na, tc_err));
+  } else {
     GemmArgs g;
     g.M = ns; g.N = na; g.K = na; g.batch = 2;
     g.A = theta; g.lda = na; g.sA = (long long)ns * na;
@@ -1642,9 +1753,28 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
     RS_CK(gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
   }
   // ---- S5: R[set][xi][ij] = sum_A U^T[xi][A] (ij|A); R^L from the kept pairs
-  // (in double-float when the block is: the operands split into pairs first)
-  const bool fac_df64 = o->dd_arith != RSSRI_DD_FP64;
-  if (fac_df64) {
+  if (fac_oz) {
+    // (ij|A) sliced in blocks of rows, so that its digits stay within ~3 GB
+    OzView vu = oz_rows(Ut, na, na, 2LL * ns * na);
+    vu.bs = (long long)ns * na;
+    RS_CK(oz_make(h->ozPA, 2, ns, na));
+    RS_CK(oz_slice_p(h, vu, h->ozPA.v));
+    const long long ldk = ((long long)na + 15) / 16 * 16;
+    const long long chunk = std::max<long long>(128, ((1LL << 28) / ldk) / 128 * 128);
+    for (long long r0 = 0; r0 < nn; r0 += chunk) {
+      const int rows = (int)std::min(chunk, nn - r0);
+      const OzView ve = oz_rows(h->eri3 + r0 * na, na, na, (long long)rows * na);
+      RS_CK(oz_make(h->ozPB, 1, rows, na));
+      RS_CK(oz_slice_p(h, ve, h->ozPB.v));
+      OzGemm g;
+      g.A = h->ozPA.v; g.B = h->ozPB.v;
+      g.M = ns; g.N = rows; g.batch = 2;
+      g.C = fac + r0; g.ldc = nn; g.sC = 2LL * ns * nn;  // kind 0 of each set
+      g.ccap = 4LL * ns * nn - r0;
+      g.err = tc_err;
+      RS_CK(oz_gemm_p(h, RSSRI_PROF_FACTOR_GEMM, g));
+    }
+  } else if (fac_df64) {
     RS_CK(ensure(h->eri_hl, (size_t)nn * na * sizeof(float2)));
     RS_CK(ensure(h->ut_hl, (size_t)2 * ns * na * sizeof(float2)));
     {
@@ -1671,7 +1801,13 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
     double *rl = fac + (2LL * set + 1) * ns * nn;
     RS_CK(cudaMemsetAsync(rl, 0, (size_t)ns * nn * sizeof(double), s));
   }
-  if (P > 0 && fac_df64) {
+  if (P > 0 && fac_oz) {
+    OzView vt = oz_rows(theta, na, na, 2LL * ns * na);
+    vt.bs = (long long)ns * na;
+    const OzView vk = oz_rows(h->KP.as<double>(), na, na, (long long)P * na);
+    RS_CK(oz_product(h, RSSRI_PROF_FACTOR_GEMM, vt, 2, ns, &vk, P, na, h->RLp.as<double>(), P,
+                     (long long)ns * P, tc_err));
+  } else if (P > 0 && fac_df64) {
     // theta is +-1, exact as a pair; K_P was split at setup
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(theta, 2LL * ns * na, h->ut_hl.as<float2>(), s, range_flag(h))); }
     SPAN(RSSRI_PROF_FACTOR_GEMM, 2.0 * 2 * ns * (double)P * na * 1e-9);
@@ -1715,9 +1851,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   const double ne = 2.0 * h->n_occ;
   double *XG = h->XG.as<double>(), *Cc = h->Cc.as<double>(), *Bm = h->Bm.as<double>(),
          *BC = h->BC.as<double>();
-  int *tc_err = h->flags.as<int>() + 4;
   if (bf16) {
-    RS_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
     RS_CK(chain_tc(h, tc_kind, ns, G, Gb, sdd, h->sig_raw.as<double>(), tc_err,
                    use_cv ? h->cv_c.as<double>() : nullptr));
   }
@@ -1849,7 +1983,7 @@ int finish_sigma(rssri_handle *h, double *e_corr, double *e_stderr, rssri_stats 
   }
   const double *res = h->host_res;
   const int tc_flag = *reinterpret_cast<const int *>(h->host_res + 4);
-  if (h->pending_tc && tc_flag) return RSSRI_ERR_TIMEOUT;
+  if (tc_flag) return RSSRI_ERR_TIMEOUT;
   if (*reinterpret_cast<const int *>(h->host_res + 5)) return RSSRI_ERR_RANGE;
   h->last_ns = h->pending_ns;
   h->have_sigma = true;
@@ -1981,7 +2115,7 @@ int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_pa
   ck(ensure(h->cv_bt, (size_t)std::max(batch, E) * sizeof(float)));
   ck(ensure(h->cv_bw, (size_t)std::max(batch, E) * sizeof(float)));
   ck(ensure(h->cv_loss, 4 * sizeof(float)));
-  if (e != cudaSuccess) return map_err(e);
+  if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); }
   float *P = h->cv_params.as<float>(), *X = h->cv_X.as<float>(), *T = h->cv_t.as<float>(),
         *Wt = h->cv_w.as<float>(), *act = h->cv_act.as<float>(), *work = h->cv_work.as<float>(),
         *bx = h->cv_bx.as<float>(), *bt = h->cv_bt.as<float>(), *bw = h->cv_bw.as<float>(),
@@ -2025,7 +2159,7 @@ int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_pa
     ck(cv_adam(P, grad, h->cv_m.as<float>(), h->cv_v.as<float>(), (int)CV_NPARAM, lr, step, s));
   }
   eval(loss_after);
-  if (e != cudaSuccess) return map_err(e);
+  if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); }
   h->cv_ready = true;
   return RSSRI_OK;
 }
@@ -2040,7 +2174,7 @@ int rssri_cv_set_params(rssri_handle *h, const float *params) {
                         h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) h->cv_ready = true;
-  return map_err(e);
+  { note_error_site(__FILE__, __LINE__); return map_err(e); }
 }
 
 int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, const float *weight,
@@ -2064,7 +2198,7 @@ int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, con
   ck(ensure(h->cv_bt, std::max(h->cv_bt.bytes, (size_t)m * sizeof(float))));
   ck(ensure(h->cv_bw, std::max(h->cv_bw.bytes, (size_t)m * sizeof(float))));
   ck(ensure(h->cv_loss, 4 * sizeof(float)));
-  if (e != cudaSuccess) return map_err(e);
+  if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); }
   ck(cudaMemcpyAsync(h->cv_ptmp.p, params, pb, cudaMemcpyHostToDevice, s));
   ck(cudaMemcpyAsync(h->cv_bx.p, x, (size_t)m * CV_NFEAT * sizeof(float), cudaMemcpyHostToDevice, s));
   ck(cudaMemcpyAsync(h->cv_bt.p, target, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -2077,7 +2211,7 @@ int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, con
   ck(cudaMemcpyAsync(loss, h->cv_loss.p, sizeof(float), cudaMemcpyDeviceToHost, s));
   ck(cudaMemcpyAsync(grad, h->cv_grad.p, pb, cudaMemcpyDeviceToHost, s));
   ck(cudaStreamSynchronize(s));
-  return map_err(e);
+  { note_error_site(__FILE__, __LINE__); return map_err(e); }
 }
 
 int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
@@ -2163,7 +2297,7 @@ int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_ki
     default: return RSSRI_ERR_INVALID_ARG;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return map_err(e);
+  { note_error_site(__FILE__, __LINE__); return map_err(e); }
 }
 
 }  // extern "C"

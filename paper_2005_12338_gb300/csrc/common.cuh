@@ -12,10 +12,17 @@ namespace rssri {
 
 // Error propagation: every launcher returns cudaError_t; the API layer maps
 // it to an rssri_status.
-#define RS_TRY(expr)                         \
-  do {                                       \
-    cudaError_t _e = (expr);                 \
-    if (_e != cudaSuccess) return _e;        \
+// Records the first source location of a failing call since the last error
+// was reported (diagnostics: rssri_last_cuda_error).
+void note_error_site(const char *file, int line);
+
+#define RS_TRY(expr)                                  \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) {                          \
+      ::rssri::note_error_site(__FILE__, __LINE__);   \
+      return _e;                                      \
+    }                                                 \
   } while (0)
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -1,7 +1,8 @@
 // fp64-accurate products on the bf16 tensor cores (tcgen05, TMA, TMEM) by
 // error-free digit slicing; see oz_gemm.cuh for the number scheme.
 //
-// Kernel layout (one 128 x 128 output tile per CTA, 18 warps):
+// Kernel layout (persistent: one CTA per SM walks the 128 x 128 output tiles
+// with a fixed stride; 18 warps):
 //   warp 0 lane 0  TMA producer: per K step of 16, the digits of A and of B
 //                  into a ring of shared-memory stages, per operand digits
 //                  0-3 as one 128 x 128-byte tile (128-byte swizzle) and
@@ -73,7 +74,7 @@ struct OzParams {
   CUtensorMap ta0, ta1, tb0, tb1;  // digits 0-3 and 4-5 of A and B
   int M, N;          // dense: C rows / columns per batch; exchange: n, n_aux
   int kst;           // K steps per CTA
-  int ksplit;        // dense: K splits (blockIdx.z = batch * ksplit + split)
+  int ksplit;        // dense: K splits (tile z = batch * ksplit + split)
   int bshared;       // dense: B has one batch entry
   const int *efa, *efb;
   long long efa_bs, efb_bs;
@@ -81,6 +82,7 @@ struct OzParams {
   double *C;
   long long ldc, sC;
   int bk, nl16, jtiles, lb0;  // exchange geometry
+  int tiles, ntiles, mtiles;  // the output tiles the persistent CTAs share
   int *err;
   long long ccap, efa_cap, efb_cap;  // bounds of C and the exponent arrays (checks)
   int wait_polls;  // 0: normal; > 0: test mode (see OzGemm)
@@ -266,6 +268,31 @@ __device__ __forceinline__ double df_to_f64(float hi, float lo, int E) {
 __device__ __forceinline__ int row_scale(int ef) { return max(ef, 1) - 1022; }
 
 // ------------------------------------------------------------- the GEMM ----
+// One output tile of a persistent CTA's queue (tile q = n tile + ntiles * rest):
+// dense: rest = m tile + mtiles * (batch * ksplit + split); exchange: rest = row tile.
+struct OzTile {
+  int n0, m0, zb, split, rt, mt, jt;
+};
+template <int MODE>
+__device__ __forceinline__ OzTile oz_tile(const OzParams &p, int q) {
+  OzTile t;
+  const int rest = q / p.ntiles;
+  t.n0 = (q - rest * p.ntiles) * BN;
+  if (MODE == 0) {
+    const int z = rest / p.mtiles;
+    t.m0 = (rest - z * p.mtiles) * BM;
+    t.zb = z / p.ksplit;
+    t.split = z - t.zb * p.ksplit;
+    t.rt = t.mt = t.jt = 0;
+  } else {
+    t.rt = rest;
+    t.mt = rest / p.jtiles;
+    t.jt = rest - t.mt * p.jtiles;
+    t.m0 = t.zb = t.split = 0;
+  }
+  return t;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -274,17 +301,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
   uint64_t *empty = full + STAGES;
   uint64_t *accf = empty + STAGES;  // a chunk's accumulators are complete
   uint64_t *acce = accf + 1;        // the drain warps have read them
-  uint32_t *tslot = (uint32_t *)(acce + 1);
+  uint64_t *done = acce + 1;        // every product this CTA issued has completed
+  uint32_t *tslot = (uint32_t *)(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN;
-  int m0 = 0, zb = 0, split = 0, rt = 0;
-  if (MODE == 0) {
-    m0 = blockIdx.y * BM;
-    zb = blockIdx.z / p.ksplit;
-    split = blockIdx.z % p.ksplit;
-  } else {
-    rt = blockIdx.z;
-  }
   const int kst = p.kst;
   const int nchunks = (kst + CHUNK - 1) / CHUNK;
 
@@ -295,6 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
     }
     bar_init(accf, 1);
     bar_init(acce, EPI);
+    bar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -310,41 +330,43 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer
-      int mt = 0, jt = 0;
-      if (MODE == 1) {
-        mt = rt / p.jtiles;
-        jt = rt % p.jtiles;
-      }
-      const bool go = test_mode_gate(p.wait_polls, p.err);
-      for (int st = 0; st < kst && go; ++st) {
-        const int s = st % STAGES;
-        if (st >= STAGES && !bar_wait(&empty[s], ((st / STAGES) - 1) & 1, p.err, 1, p.wait_polls))
-          break;
-        bar_expect(&full[s], STAGE);
-        uint8_t *sa = smem + s * STAGE, *sb = sa + OPB;
-        // coordinates (inner, 16-column block, ...): dense (0, kb, row, batch);
-        // exchange A (0, st, 0, tile), B (0, l block, k, q)
-        int ay, az, by, bz, bw;
-        if (MODE == 0) {
-          ay = by = split * kst + st;
-          az = m0;
-          bz = n0;
-          bw = p.bshared ? 0 : zb;
-          tma_load4(sa, &p.ta0, &full[s], 0, ay, az, zb);
-          tma_load4(sa + TILE0, &p.ta1, &full[s], 0, ay, az, zb);
-        } else {
-          const int kidx = st / p.nl16, ls = st % p.nl16;
-          ay = st;
-          az = 0;
-          by = jt + p.lb0 + ls;         // block of l' (may lie outside: zeros)
-          bz = mt * 8 - p.bk + kidx;    // k (may lie outside: zeros)
-          bw = n0;                      // q
-          tma_load4(sa, &p.ta0, &full[s], 0, ay, az, rt);
-          tma_load4(sa + TILE0, &p.ta1, &full[s], 0, ay, az, rt);
+      // producer: the K steps of this CTA's tiles, one after another
+      bool go = test_mode_gate(p.wait_polls, p.err);
+      int it = 0;  // K steps loaded so far (all tiles)
+      for (int q = blockIdx.x; q < p.tiles && go; q += gridDim.x) {
+        const OzTile t = oz_tile<MODE>(p, q);
+        for (int st = 0; st < kst; ++st, ++it) {
+          const int s = it % STAGES;
+          if (it >= STAGES &&
+              !bar_wait(&empty[s], ((it / STAGES) - 1) & 1, p.err, 1, p.wait_polls)) {
+            go = false;
+            break;
+          }
+          bar_expect(&full[s], STAGE);
+          uint8_t *sa = smem + s * STAGE, *sb = sa + OPB;
+          // coordinates (inner, 16-column block, ...): dense (0, kb, row, batch);
+          // exchange A (0, st, 0, tile), B (0, l block, k, q)
+          int ay, az, aw, by, bz, bw;
+          if (MODE == 0) {
+            ay = by = t.split * kst + st;
+            az = t.m0;
+            aw = t.zb;
+            bz = t.n0;
+            bw = p.bshared ? 0 : t.zb;
+          } else {
+            const int kidx = st / p.nl16, ls = st % p.nl16;
+            ay = st;
+            az = 0;
+            aw = t.rt;
+            by = t.jt + p.lb0 + ls;         // block of l' (may lie outside: zeros)
+            bz = t.mt * 8 - p.bk + kidx;    // k (may lie outside: zeros)
+            bw = t.n0;                      // q
+          }
+          tma_load4(sa, &p.ta0, &full[s], 0, ay, az, aw);
+          tma_load4(sa + TILE0, &p.ta1, &full[s], 0, ay, az, aw);
+          tma_load4(sb, &p.tb0, &full[s], 0, by, bz, bw);
+          tma_load4(sb + TILE0, &p.tb1, &full[s], 0, by, bz, bw);
         }
-        tma_load4(sb, &p.tb0, &full[s], 0, by, bz, bw);
-        tma_load4(sb + TILE0, &p.tb1, &full[s], 0, by, bz, bw);
       }
     }
   } else if (warp == 1) {
@@ -352,99 +374,112 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
       // MMA issuer
       const uint32_t idesc = instr_desc_bf16();
       bool ok = true;
-      for (int st = 0; st < kst && ok; ++st) {
-        const int s = st % STAGES, cs = st % CHUNK;
-        if (cs == 0 && st > 0) {
-          if (!bar_wait(acce, ((st / CHUNK) - 1) & 1, p.err, 2, p.wait_polls)) {
+      int it = 0, gc = 0;  // K steps and chunks issued so far (all tiles)
+      for (int q = blockIdx.x; q < p.tiles && ok; q += gridDim.x) {
+        for (int st = 0; st < kst; ++st, ++it) {
+          const int s = it % STAGES, cs = st % CHUNK;
+          if (cs == 0 && gc > 0) {
+            // the previous chunk's accumulators have been read
+            if (!bar_wait(acce, (gc - 1) & 1, p.err, 2, p.wait_polls)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+          }
+          if (!bar_wait(&full[s], (it / STAGES) & 1, p.err, 3, p.wait_polls)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-        }
-        if (!bar_wait(&full[s], (st / STAGES) & 1, p.err, 3, p.wait_polls)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t base_a = s_u32(smem + s * STAGE), base_b = base_a + OPB;
+          const uint32_t base_a = s_u32(smem + s * STAGE), base_b = base_a + OPB;
 #pragma unroll
-        for (int pa = 0; pa < OZ_S; ++pa)
+          for (int pa = 0; pa < OZ_S; ++pa)
 #pragma unroll
-          for (int pb = 0; pb < OZ_S - pa; ++pb) {
-            const int acc = min(pa + pb, 3);
-            // the first product into each accumulator in a chunk overwrites it
-            const uint32_t en = (cs > 0 || !(pa == 0 && pb <= 3)) ? 1u : 0u;
-            mma_bf16(tmem + (uint32_t)(acc * 128), digit_desc(base_a, pa),
-                     digit_desc(base_b, pb), idesc, en);
+            for (int pb = 0; pb < OZ_S - pa; ++pb) {
+              const int acc = min(pa + pb, 3);
+              // the first product into each accumulator in a chunk overwrites it
+              const uint32_t en = (cs > 0 || !(pa == 0 && pb <= 3)) ? 1u : 0u;
+              mma_bf16(tmem + (uint32_t)(acc * 128), digit_desc(base_a, pa),
+                       digit_desc(base_b, pb), idesc, en);
+            }
+          mma_commit(&empty[s]);
+          if (cs == CHUNK - 1 || st == kst - 1) {
+            mma_commit(accf);
+            ++gc;
           }
-        mma_commit(&empty[s]);
-        if (cs == CHUNK - 1 || st == kst - 1) mma_commit(accf);
+        }
       }
       // a drain that is still waiting sees its phase complete once the MMAs
       // issued so far are done (and then stops on the error flag)
       if (!ok) mma_commit(accf);
+      mma_commit(done);
     }
   } else {
     // drain warps
     const int lq = warp & 3;            // tensor-memory lanes this warp may access
     const int cq = (warp - 2) >> 2;     // column quarter of the tile
     const int row = lq * 32 + lane;
-    float hi[DC], lo[DC];
-#pragma unroll
-    for (int c = 0; c < DC; ++c) hi[c] = lo[c] = 0.f;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      if (!bar_wait(accf, c & 1, p.err, 4, p.wait_polls) || (p.err && *(volatile int *)p.err)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * DC);
+    int gc = 0;  // chunks drained so far (all tiles)
+    for (int q = blockIdx.x; q < p.tiles && ok; q += gridDim.x) {
+      const OzTile t = oz_tile<MODE>(p, q);
+      float hi[DC], lo[DC];
 #pragma unroll
-      for (int c0 = 0; c0 < DC; c0 += 4) {
-        uint32_t r0[4], r1[4], r2[4], r3[4];
-        tmem_ld4(tl + c0, r0);
-        tmem_ld4(tl + 128 + c0, r1);
-        tmem_ld4(tl + 256 + c0, r2);
-        tmem_ld4(tl + 384 + c0, r3);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int c = 0; c < DC; ++c) hi[c] = lo[c] = 0.f;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        if (!bar_wait(accf, gc & 1, p.err, 4, p.wait_polls) ||
+            (p.err && *(volatile int *)p.err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * DC);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          fold(hi[c0 + u], lo[c0 + u], __uint_as_float(r0[u]), __uint_as_float(r1[u]),
-               __uint_as_float(r2[u]), __uint_as_float(r3[u]));
+        for (int c0 = 0; c0 < DC; c0 += 4) {
+          uint32_t r0[4], r1[4], r2[4], r3[4];
+          tmem_ld4(tl + c0, r0);
+          tmem_ld4(tl + 128 + c0, r1);
+          tmem_ld4(tl + 256 + c0, r2);
+          tmem_ld4(tl + 384 + c0, r3);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            fold(hi[c0 + u], lo[c0 + u], __uint_as_float(r0[u]), __uint_as_float(r1[u]),
+                 __uint_as_float(r2[u]), __uint_as_float(r3[u]));
+        }
+        // the accumulators are free for the next chunk (of this tile or the next)
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) bar_arrive(acce);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) bar_arrive(acce);
-    }
-    if (ok) {
-      // assemble fp64: C = alpha 2^(eA + eB - 14) (hi + lo)
+      if (!ok) break;
+      // assemble fp64 (while the issuer runs the next tile): C = alpha 2^(eA + eB - 14) (hi + lo)
       int i = 0, valid;
       double *dst;
       int ea;
       if (MODE == 0) {
-        i = m0 + row;
+        i = t.m0 + row;
         valid = i < p.M;
-        if (valid && !OZ_IN(zb * p.efa_bs + i, p.efa_cap, 10)) valid = 0;
-        ea = valid ? row_scale(p.efa[zb * p.efa_bs + i]) : 0;
-        dst = p.ksplit > 1 ? p.C + (long long)blockIdx.z * p.M * p.N + (long long)i * p.N
-                           : p.C + zb * p.sC + (long long)i * p.ldc;
+        if (valid && !OZ_IN(t.zb * p.efa_bs + i, p.efa_cap, 10)) valid = 0;
+        ea = valid ? row_scale(p.efa[t.zb * p.efa_bs + i]) : 0;
+        dst = p.ksplit > 1
+                  ? p.C + (long long)(t.zb * p.ksplit + t.split) * p.M * p.N + (long long)i * p.N
+                  : p.C + t.zb * p.sC + (long long)i * p.ldc;
       } else {
-        const int mt = rt / p.jtiles, jt = rt % p.jtiles;
-        const int m = mt * 8 + (row >> 4), j = jt * 16 + (row & 15);
+        const int m = t.mt * 8 + (row >> 4), j = t.jt * 16 + (row & 15);
         valid = m < p.M && j < p.M;
-        if (!OZ_IN((long long)rt * BM + row, p.efa_cap, 11)) valid = 0;
-        ea = valid ? row_scale(p.efa[(long long)rt * BM + row]) : 0;
+        if (!OZ_IN((long long)t.rt * BM + row, p.efa_cap, 11)) valid = 0;
+        ea = valid ? row_scale(p.efa[(long long)t.rt * BM + row]) : 0;
         dst = p.C + ((long long)j * p.M + m) * p.N;
       }
       const int ncol = p.N;
       if (valid) {
-        const int j0 = n0 + cq * DC;
+        const int j0 = t.n0 + cq * DC;
         // alpha = +-1 (every product of the block) flips the sign bit only;
         // any other alpha takes one fp64 multiply per output
         const bool neg = p.alpha == -1.0, plain = p.alpha == 1.0 || neg;
         const unsigned long long sgn = neg ? (1ull << 63) : 0ull;
-        const long long eb_off = MODE == 0 && !p.bshared ? zb * p.efb_bs : 0;
+        const long long eb_off = MODE == 0 && !p.bshared ? t.zb * p.efb_bs : 0;
 #pragma unroll
         for (int c = 0; c < DC; ++c) {
           const int j = j0 + c;
@@ -462,6 +497,8 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
         }
       }
     }
+    // every product the issuer started is complete before tensor memory is freed
+    bar_wait(done, 0, p.err, 5, p.wait_polls);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -554,7 +591,9 @@ __global__ void __launch_bounds__(256) oz_rowmax_kernel(OzView v, int rows, long
                                                         int *__restrict__ ef) {
   __shared__ double s[SR][SK + 1];
   const int b = blockIdx.z;
-  const long long r0 = (long long)blockIdx.y * SR, k0 = (long long)blockIdx.x * SK;
+  // one tile per block: blockIdx.x = row tile + (rows / SR) * column tile
+  const long long rtiles = (rows + SR - 1) / SR;
+  const long long r0 = ((long long)blockIdx.x % rtiles) * SR, k0 = ((long long)blockIdx.x / rtiles) * SK;
   load_tile(v, b, r0, k0, rows, K, s);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -606,7 +645,9 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
                                                         long long ld, long long g1) {
   __shared__ double s[SR][SK + 1];
   const int b = blockIdx.z;
-  const long long r0 = (long long)blockIdx.y * SR, k0 = (long long)blockIdx.x * SK;
+  // one tile per block: blockIdx.x = row tile + (rows / SR) * column tile
+  const long long rtiles = (rows + SR - 1) / SR;
+  const long long r0 = ((long long)blockIdx.x % rtiles) * SR, k0 = ((long long)blockIdx.x / rtiles) * SK;
   load_tile(v, b, r0, k0, rows, K, s);
   __syncthreads();
   for (int idx = threadIdx.x; idx < SR * SK; idx += blockDim.x) {
@@ -665,12 +706,13 @@ __device__ __forceinline__ void load8(const OzView &v, int b, long long r, long 
   }
 }
 
-// ef[b][r] = max biased exponent over the row; grid (ceil(K / 2048), rows, batch).
+// ef[b][r] = max biased exponent over the row; grid (rows * ceil(K / 2048), 1, batch),
+// blockIdx.x = r + rows * (2048-column block).
 __global__ void __launch_bounds__(256) oz_rowmax_kc_kernel(OzView v, int rows, long long K,
                                                            int *__restrict__ ef) {
   __shared__ int wm[8];
-  const int b = blockIdx.z, r = blockIdx.y;
-  const long long k0 = ((long long)blockIdx.x * 256 + threadIdx.x) * KC;
+  const int b = blockIdx.z, r = (int)(blockIdx.x % (unsigned)rows);
+  const long long k0 = ((long long)(blockIdx.x / (unsigned)rows) * 256 + threadIdx.x) * KC;
   int m = 0;
   if (k0 < K) {
     double x[KC];
@@ -904,6 +946,17 @@ cudaError_t digit_maps(CUtensorMap *m0, CUtensorMap *m1, const OzDigits &o) {
   return make_map4(m1, g1, d, st, b);
 }
 
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 152;
+  }
+  return n;
+}
+
 cudaError_t prepare() {
   static std::mutex mu;
   static bool done[64] = {};
@@ -972,13 +1025,16 @@ cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
   // start of the digits 4-5 group (see OzDigits)
   const long long g1 = (long long)out.batch * out.rows * out.ld * 4;
   RS_TRY(cudaMemsetAsync(out.ef, 0, (size_t)out.batch * out.rows * sizeof(int), s));
-  if ((out.rows + SR - 1) / SR > 65535 || out.batch > 65535) return cudaErrorInvalidValue;
+  if (out.batch > 65535) return cudaErrorInvalidValue;
+  const long long rtiles = ((long long)out.rows + SR - 1) / SR;
   // rows contiguous along K, 16-byte aligned: the vectorised path
   const uintptr_t base = v.x2 ? (uintptr_t)v.x2 : (uintptr_t)v.x;
+  const long long kcb = (out.K + 256LL * KC - 1) / (256LL * KC);  // 2048-column blocks
   const bool kc = v.cs2 == 1 && v.k2off == 0 && v.k2pad >= out.K && v.k2n >= out.K &&
-                  base % 16 == 0 && v.rs % 2 == 0 && v.bs % 2 == 0 && out.rows <= 65535;
+                  base % 16 == 0 && v.rs % 2 == 0 && v.bs % 2 == 0 &&
+                  kcb * out.rows <= 0x7FFFFFFFLL;
   if (kc) {
-    dim3 gm((unsigned)ceil_div(out.K, 256LL * KC), out.rows, out.batch);
+    dim3 gm((unsigned)(kcb * out.rows), 1, out.batch);
     oz_rowmax_kc_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
     ++launch_counter();
     RS_TRY(cudaGetLastError());
@@ -999,13 +1055,17 @@ cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
     dim3 gm(ceil_div(out.rows, 256), ceil_div(out.K, RK), out.batch);
     oz_rowmax_rmaj_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
   } else {
-    dim3 gm(ceil_div(out.K, SK), ceil_div(out.rows, SR), out.batch);
+    const long long tiles = rtiles * ((out.K + SK - 1) / SK);
+    if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+    dim3 gm((unsigned)tiles, 1, out.batch);
     oz_rowmax_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
   }
   ++launch_counter();
   RS_TRY(cudaGetLastError());
   // the digit pass covers the padding columns K..ld too (zeros)
-  dim3 gd(ceil_div(out.ld, SK), ceil_div(out.rows, SR), out.batch);
+  const long long dtiles = rtiles * ((out.ld + SK - 1) / SK);
+  if (dtiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  dim3 gd((unsigned)dtiles, 1, out.batch);
   oz_digits_kernel<<<gd, 256, 0, s>>>(v, out.rows, out.K, out.ef, out.d, out.ld, g1);
   ++launch_counter();
   return cudaGetLastError();
@@ -1059,8 +1119,12 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   p.efb_cap = (long long)g.B.batch * g.B.rows;
   p.wait_polls = g.wait_polls;
   RS_TRY(prepare());
-  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.batch * ks);
-  oz_gemm_kernel<0><<<grid, THREADS, SMEM, s>>>(p);
+  p.ntiles = ceil_div(g.N, BN);
+  p.mtiles = ceil_div(g.M, BM);
+  const long long tiles = (long long)p.ntiles * p.mtiles * g.batch * ks;
+  if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  p.tiles = (int)tiles;
+  oz_gemm_kernel<0><<<(unsigned)std::min<long long>(tiles, sm_count()), THREADS, SMEM, s>>>(p);
   ++launch_counter();
   RS_TRY(cudaGetLastError());
   if (ks > 1) {
@@ -1167,8 +1231,10 @@ cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, doub
   p.efb_cap = (long long)At.batch * At.rows;
   p.wait_polls = wait_polls;
   RS_TRY(prepare());
-  dim3 grid(ceil_div(x.na, BN), 1, tiles);
-  oz_gemm_kernel<1><<<grid, THREADS, SMEM, s>>>(p);
+  p.ntiles = ceil_div(x.na, BN);
+  p.mtiles = 1;
+  p.tiles = p.ntiles * tiles;
+  oz_gemm_kernel<1><<<(unsigned)std::min(p.tiles, sm_count()), THREADS, SMEM, s>>>(p);
   ++launch_counter();
   return cudaGetLastError();
 }

@@ -87,3 +87,34 @@ def test_sri_after_cached_block(B):
     assert np.array_equal(a[0], c[0])
     assert np.abs(h.export("SIGMA_DD")).max() > 0
     h.close()
+
+
+def test_destroy_returns_every_device_allocation():
+    """A handle frees all its device memory: after one warm-up handle (the
+    context and per-process state), setting up and sampling with fresh
+    handles in every form and destroying them leaves free device memory
+    where it was."""
+    from paper_2005_12338_gb300 import binding as B, build
+    build.build()
+    s = synth.make_system(48, 20, 120, 3, input_seed=8)
+    dev = [torch.from_numpy(a).cuda() for a in (s.eri3, s.metric, s.orb_e, s.orb_c, s.tau,
+                                                 s.tau_w)]
+    sig = torch.empty((s.n_tau, s.n, s.n), dtype=torch.float64, device="cuda")
+    forms = [(B.RSSRI_PREC_BF16, B.RSSRI_DD_OZ), (B.RSSRI_PREC_DF64, B.RSSRI_DD_DF64),
+             (B.RSSRI_PREC_FP64, B.RSSRI_DD_FP64)]
+
+    def cycle():
+        for prec, dd in forms:
+            o = B.Handle.options(0.02, 1e-2, 8, 3, precision=prec, dd_arith=dd)
+            h = B.Handle(0)
+            h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
+            h.sigma(o, sig)
+            h.close()
+        torch.cuda.synchronize()
+
+    cycle()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        cycle()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (2 << 20), (free0 - free1) / 2 ** 20
