@@ -587,12 +587,16 @@ def our_arm(args):
 
     # learned control variate (fp64 chain): train on an independent run, then
     # estimate with it on the first timed seed, next to the plain estimate
-    cv_report = None
-    if not args.no_cv:
-        # the learned control variate on the chosen form: trained on an independent
-        # run (seed 777; statistics need the fp64-accurate double-float chain),
-        # then the same draws (seeds[0]) with and without it
-        tr = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, replicas.rank_seed(rank, 777),
+    def at_eps(eps, plain_ttt=None):
+        """Time to a 1 mEh standard error at one eps: the plain form, the
+        chosen form, and the chosen form with the learned control variate
+        (trained on an independent run, seed 777; statistics need the
+        fp64-accurate double-float chain), the latter two on the same draws."""
+        def o_e(form, seed, cvf=0):
+            prec, dd = FORMS[form]
+            return binding.Handle.options(cfg["eps_prime"], eps, ns, seed, cv=cvf,
+                                          precision=prec_code[prec], dd_arith=dd_code[dd])
+        tr = binding.Handle.options(cfg["eps_prime"], eps, ns, replicas.rank_seed(rank, 777),
                                     dd_arith=binding.RSSRI_DD_OZ,
                                     precision=binding.RSSRI_PREC_DF64)
         h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=tr)
@@ -600,30 +604,40 @@ def our_arm(args):
         lb, la = h.cv_train(tr, synth.mlp_init(0), 400, 4096, 1e-3)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - c0
-        pr, dd = FORMS["chosen"]
         rows = {}
-        for name, cvf in (("chosen", 0), ("chosen+cv", 1)):
-            o = binding.Handle.options(cfg["eps_prime"], cfg["eps"], ns, seeds[0],
-                                       dd_arith=dd_code[dd], precision=prec_code[pr], cv=cvf)
-            h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
-            h.sigma(o, sig, ep)  # warm-up: graph capture, tile tuning
-            torch.cuda.synchronize()
-            e_, se_, st_ = h.sigma(o, sig, ep)
-            torch.cuda.synchronize()
+        runs = [("chosen", "chosen", 0), ("chosen+cv", "chosen", 1)]
+        if plain_ttt is None:
+            runs.insert(0, ("plain", "plain", 0))
+        for name, form_, cvf in runs:
+            o = o_e(form_, seeds[0], cvf)
+            for _ in range(2):  # a warm-up call (graph capture, tile tuning), then the timed one
+                h.setup(*dev, n_occ=s.n_occ, mu=s.mu, beta=s.beta, opts=o)
+                torch.cuda.synchronize()
+                e_, se_, st_ = h.sigma(o, sig, ep)
+                torch.cuda.synchronize()
             rows[name] = (e_, se_, st_["t_setup_ms"] + st_["t_green_dd_ms"], st_["t_sample_ms"],
                           ep.cpu().numpy().copy())
+        ttt = {k: time_to_target([v[:4]], ns, 1e-3) for k, v in rows.items()}
+        if plain_ttt is not None:
+            ttt["plain"] = plain_ttt
         a, b = rows["chosen"][4], rows["chosen+cv"][4]
-        cv_report = {"form": "chosen (bf16 chain, sliced block)", "eps": cfg["eps"],
-                     "fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
-                     "e_corr_plain": rows["chosen"][0], "stderr_plain": rows["chosen"][1],
-                     "e_corr_learned": rows["chosen+cv"][0],
-                     "stderr_learned": rows["chosen+cv"][1],
-                     "stderr_ratio_plain_over_learned": rows["chosen"][1] / rows["chosen+cv"][1],
-                     "paired_sd_ratio": float(np.std(a) / np.std(b)),
-                     "sampling_ms": {k: v[3] for k, v in rows.items()},
-                     "time_to_1mEh": {k: time_to_target([v[:4]], ns, 1e-3)
-                                      for k, v in rows.items()},
-                     "note": "time_to_1mEh of chosen+cv excludes the one-time training (train_s)"}
+        return {"eps": eps, "time_to_1mEh": ttt,
+                "speedup_vs_plain": {k: ttt["plain"]["seconds"] / v["seconds"]
+                                     for k, v in ttt.items() if k != "plain"},
+                "stderr": {k: v[1] for k, v in rows.items()},
+                "e_corr": {k: v[0] for k, v in rows.items()},
+                "sampling_ms": {k: v[3] for k, v in rows.items()},
+                "learned_cv": {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
+                               "paired_sd_ratio_plain_over_learned": float(np.std(a) / np.std(b))},
+                "note": "chosen = bf16 chain + sliced fp64-accurate block; chosen+cv adds the "
+                        "learned control variate (its one-time training, train_s, excluded); "
+                        "setup once plus sample pairs at the measured cost per pair"}
+
+    cv_report, by_eps = None, None
+    if not args.no_cv:
+        by_eps = {str(cfg["eps"]): at_eps(cfg["eps"], forms.get("plain", {}).get("time_to_1mEh")),
+                  "0.1": at_eps(0.1) if cfg["eps"] != 0.1 else None}
+        cv_report = dict(by_eps[str(cfg["eps"])]["learned_cv"], eps=cfg["eps"])
 
     many_report = None
     if args.many > 0:
@@ -753,6 +767,7 @@ def our_arm(args):
                       "measured_pipe_peaks_tflops": pipes,
                       "rs_vs_sri_same_n_s": rs_vs_sri,
                       "learned_control_variate": cv_report,
+                      "time_to_1mEh_by_eps": by_eps,
                       "literal_estimator": literal_report,
                       "many_systems": many_report}}
     if not args.no_cpu_baseline and world == 1:

@@ -321,6 +321,7 @@ cudaError_t oz_product(rssri_handle *h, int cls, const OzView &va, int batch, in
                        const OzView *vb, int N, long long K, double *C, long long ldc,
                        long long sC, int *err);
 OzView oz_rows(const double *x, long long ld, long long K, long long len);
+cudaError_t df_gemm_w(rssri_handle *h, const DfGemm &g);
 OzView oz_cols(const double *x, long long ld, long long K, long long len);
 
 // ------------------------------------------------------------ S1: V^-1/2 --
@@ -375,7 +376,7 @@ int metric_inv_sqrt(rssri_handle *h, int *rc, bool df64) {
     g.A = h->nsA2.as<float2>(); g.lda = na;
     g.B = h->nsB2.as<float2>(); g.ldb = na;
     g.C64 = C; g.ldc = na;
-    return df_gemm(g, nullptr, 0, s);
+    return df_gemm_w(h, g);
   };
   const int max_it = 100;
   double resid = 0;
@@ -656,7 +657,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
         g.A = h->KPhl.as<float2>(); g.lda = na;
         g.B = h->KPhl.as<float2>(); g.ldb = na; g.transB = 1;
         g.C64 = h->D.as<double>(); g.ldc = P;
-        RS_CK(df_gemm(g, nullptr, 0, s));
+        RS_CK(df_gemm_w(h, g));
       }
       { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(to_df64(h->D.as<double>(), (long long)P * P, h->Dhl.as<float2>(), s, range_flag(h))); }
       h->d_df64_ready = true;
@@ -775,6 +776,13 @@ cudaError_t sigma_dd_tau(rssri_handle *h, const double *G, const double *Gb, dou
     RS_TRY(gemm_p(h, RSSRI_PROF_DD_GEMM, g));
   }
   return cudaSuccess;
+}
+
+// A double-float product with the handle's split-over-K scratch (no span).
+cudaError_t df_gemm_w(rssri_handle *h, const DfGemm &g) {
+  const size_t need = df_gemm_work(g) * sizeof(double);
+  if (need > h->gwork.bytes) RS_TRY(ensure(h->gwork, need));
+  return df_gemm(g, h->gwork.as<double>(), h->gwork.bytes / sizeof(double), h->stream);
 }
 
 // A double-float product counted under kernel class `cls`.
@@ -1788,7 +1796,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
     g.A = h->ut_hl.as<float2>(); g.lda = na; g.sA = (long long)ns * na;
     g.B = h->eri_hl.as<float2>(); g.ldb = na; g.transB = 1; g.sB = 0;
     g.C64 = fac; g.ldc = nn; g.sC = 2LL * ns * nn;  // kind 0 of each set
-    RS_CK(df_gemm(g, nullptr, 0, s));
+    RS_CK(df_gemm_w(h, g));
   } else {
     GemmArgs g;
     g.M = ns; g.N = (int)nn; g.K = na; g.batch = 2;
@@ -1816,7 +1824,7 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
     g.A = h->ut_hl.as<float2>(); g.lda = na; g.sA = (long long)ns * na;
     g.B = h->KPhl.as<float2>(); g.ldb = na; g.transB = 1; g.sB = 0;
     g.C64 = h->RLp.as<double>(); g.ldc = P; g.sC = (long long)ns * P;
-    RS_CK(df_gemm(g, nullptr, 0, s));
+    RS_CK(df_gemm_w(h, g));
   } else if (P > 0) {
     GemmArgs g;
     g.M = ns; g.N = P; g.K = na; g.batch = 2;
