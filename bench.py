@@ -615,8 +615,10 @@ def our_arm(args):
                 torch.cuda.synchronize()
                 e_, se_, st_ = h.sigma(o, sig, ep)
                 torch.cuda.synchronize()
-            rows[name] = (e_, se_, st_["t_setup_ms"] + st_["t_green_dd_ms"], st_["t_sample_ms"],
-                          ep.cpu().numpy().copy())
+            # the coefficients c are computed once per setup: fixed cost, not per pair
+            cvc = st_["t_cv_c_ms"]
+            rows[name] = (e_, se_, st_["t_setup_ms"] + st_["t_green_dd_ms"] + cvc,
+                          st_["t_sample_ms"] - cvc, ep.cpu().numpy().copy())
         ttt = {k: time_to_target([v[:4]], ns, 1e-3) for k, v in rows.items()}
         if plain_ttt is not None:
             ttt["plain"] = plain_ttt
@@ -630,7 +632,8 @@ def our_arm(args):
                 "learned_cv": {"fit_loss_before": lb, "fit_loss_after": la, "train_s": t_train,
                                "paired_sd_ratio_plain_over_learned": float(np.std(a) / np.std(b))},
                 "note": "chosen = bf16 chain + sliced fp64-accurate block; chosen+cv adds the "
-                        "learned control variate (its one-time training, train_s, excluded); "
+                        "learned control variate (its one-time training, train_s, excluded; "
+                        "its coefficients, computed once per setup, in the fixed part); "
                         "setup once plus sample pairs at the measured cost per pair"}
 
     cv_report, by_eps = None, None

@@ -255,6 +255,10 @@ typedef struct {
                                            per class (digit products of the sliced
                                            block and bf16/tf32 chain products, over
                                            the padded tiles actually computed)   */
+  double t_cv_c_ms;         /* device time of the learned control variate's
+                               coefficients c in the last sampling call (0 when it
+                               reused them: c is computed once per setup, caller G
+                               and parameter set; included in t_sample_ms)      */
 } rssri_stats;
 
 /* ------------------------------------------------------------- lifetime */

@@ -56,7 +56,7 @@ class rssri_stats(C.Structure):
                 ("t_green_dd_ms", C.c_double), ("t_sample_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("prof_launches", C.c_int64 * 8),
                 ("prof_ms", C.c_double * 8), ("prof_gflop", C.c_double * 8),
-                ("prof_tensor_gflop", C.c_double * 8)]
+                ("prof_tensor_gflop", C.c_double * 8), ("t_cv_c_ms", C.c_double)]
 
     def as_dict(self):
         d = {}

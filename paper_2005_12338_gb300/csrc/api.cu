@@ -83,7 +83,7 @@ int map_err(cudaError_t e) {
 struct rssri_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
-  cudaEvent_t ev[6] = {};
+  cudaEvent_t ev[8] = {};  // 6, 7: the control variate's coefficients
   // results of an enqueued sigma call, copied into pinned host memory:
   // [0..3] the energy scalars, then the tensor-core timeout flag
   double *host_res = nullptr;
@@ -118,6 +118,7 @@ struct rssri_handle {
   DevBuf cv_params, cv_m, cv_v, cv_grad, cv_ptmp, cv_act, cv_work, cv_X, cv_t, cv_w, cv_stats, cv_c,
       cv_scr, cv_bx, cv_bt, cv_bw, cv_loss;
   bool cv_ready = false, cv_c_ready = false;
+  bool pending_cv_c = false;  // the last sampling call computed c
   // double-float copies for the exchange contraction
   DevBuf Dhl, Ahl, KPhl, PGhl, APhl, Gamhl, GGhl;
   // literal estimator: pair gathers / J, aux traces, pair form of the batch
@@ -456,7 +457,8 @@ int rssri_create(rssri_handle **out, int device, void *stream) {
   if (e == cudaSuccess) e = cudaMallocHost(&h->host_res, 8 * sizeof(double));
   if (e != cudaSuccess) {
     rssri_destroy(h);
-    { note_error_site(__FILE__, __LINE__); return map_err(e); }
+    if (e != cudaSuccess) note_error_site(__FILE__, __LINE__);
+    return map_err(e);
   }
   *out = h;
   return RSSRI_OK;
@@ -511,6 +513,7 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   h->have_sigma = false;
   h->d_df64_ready = false;
   h->kp_hl_ready = false;
+  h->cv_c_ready = false;
   h->block_ok = false;
   h->gg_valid = false;
   h->oz_ready = false;
@@ -1008,7 +1011,9 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
   const OzExch &x = h->oz_geo;
   int *err = h->flags.as<int>() + 5;
   float2 *PGhl = h->PGhl.as<float2>();
-  double *At = h->At.as<double>(), *T = h->T.as<double>();
+  // T (the exchange's output) takes At's buffer once At's rows at the kept
+  // pairs are gathered and At is sliced
+  double *At = h->At.as<double>(), *T = At;
   // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]   (double-float)
   { SPAN(RSSRI_PROF_DD_GEMM, 2.0 * n * (double)na * P * 1e-9);
     RS_TRY(df_gemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), Ghl, n,
@@ -1035,10 +1040,11 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
     v.k2off = x.lsh;
     v.k2n = n; v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dAt)); }
+  // At_P: the rows of At at the kept pairs (for Gamma below)
+  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
   { SPAN_T(RSSRI_PROF_DD_SPMM, 2.0 * na * (double)P * P * 1e-9, oz_exch_flops(x) * 1e-9);
     RS_TRY(oz_exch(x, h->ozX.v, dAt, T, nna, -1.0, err, s, h->test_wait_polls)); }
-  // Gamma = K_P^T At_P (At_P: the rows of At at the kept pairs)
-  { SPAN(RSSRI_PROF_OTHER, 0.0); RS_TRY(gather_rows(At, h->pij.as<int>(), P, na, h->AP.as<double>(), s)); }
+  // Gamma = K_P^T At_P
   { OzView v; v.x = h->AP.as<double>(); v.rs = 1; v.cs2 = na; v.k2pad = v.k2n = P;
     v.xlen = (long long)P * na;
     RS_TRY(oz_slice_p(h, v, h->ozAtP.v)); }
@@ -1159,14 +1165,16 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
   const bool dd_oz = P > 0 && dd_arith == RSSRI_DD_OZ;
   if (P > 0) {
     if (dd_oz) {
-      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
-      RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
-      RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
+      // the exchange operand first (its fp64 gather is freed before the
+      // per-tau buffers are made), then the per-tau buffers; T shares At's
       RS_CK(ensure_kp_df64(h));
       if (!h->oz_ready) {
         const int rc = oz_setup(h);
         if (rc) return rc;
       }
+      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
       // the largest per-tau digit operand: n*na rows of ld16(n), n rows of ld16(n*na), or
       // na rows of n*ldl
       const long long ld_n = (n + 15) / 16 * 16, ld_kmq = ((long long)n * na + 15) / 16 * 16;
@@ -1186,7 +1194,7 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
       RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
       RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
     }
-    RS_CK(ensure(h->T, (size_t)nn * na * sizeof(double)));
+    if (!dd_oz) RS_CK(ensure(h->T, (size_t)nn * na * sizeof(double)));
     RS_CK(ensure(h->L, (size_t)P * na * sizeof(double)));
     RS_CK(ensure(h->Gam, (size_t)na * na * sizeof(double)));
     RS_CK(ensure(h->gwork, std::max(h->gwork.bytes, dd_work_need(h) * 8)));
@@ -1845,9 +1853,15 @@ int issue_sigma(rssri_handle *h, const rssri_options *o, const double *g_in, con
   }
 
   // ---- learned control variate: coefficients, or statistics for training
-  if (use_cv) {
+  // c depends on the network and the setup's G, Sigma_DD and [K]^L only, not on
+  // the draws: computed once per setup (or caller G) and parameter set
+  h->pending_cv_c = false;
+  if (use_cv && (!h->cv_c_ready || h->pending_block)) {
+    RS_CK(cudaEventRecord(h->ev[6], s));
     RS_CK(cv_compute_c(h, G, Gb));
+    RS_CK(cudaEventRecord(h->ev[7], s));
     h->cv_c_ready = true;
+    h->pending_cv_c = true;
   }
   if (collect_stats) {
     RS_CK(ensure(h->cv_stats, (size_t)nt * 5 * nn * sizeof(double)));
@@ -2012,6 +2026,9 @@ int finish_sigma(rssri_handle *h, double *e_corr, double *e_stderr, rssri_stats 
   S.t_setup_ms = h->t_setup_ms;
   S.t_green_dd_ms = h->pending_block ? t_dd : 0.0;
   S.t_sample_ms = t_samp;
+  float t_cv = 0;
+  if (h->pending_cv_c) cudaEventElapsedTime(&t_cv, h->ev[6], h->ev[7]);
+  S.t_cv_c_ms = t_cv;
   long long pl[RSSRI_PROF_NCLASS];
   double pm[RSSRI_PROF_NCLASS], pg[RSSRI_PROF_NCLASS], pt[RSSRI_PROF_NCLASS];
   collect(h, pl, pm, pg, pt);
@@ -2169,6 +2186,7 @@ int rssri_cv_train(rssri_handle *h, const rssri_options *o, const float *init_pa
   eval(loss_after);
   if (e != cudaSuccess) { note_error_site(__FILE__, __LINE__); return map_err(e); }
   h->cv_ready = true;
+  h->cv_c_ready = false;
   return RSSRI_OK;
 }
 
@@ -2181,8 +2199,12 @@ int rssri_cv_set_params(rssri_handle *h, const float *params) {
     e = cudaMemcpyAsync(h->cv_params.p, params, CV_NPARAM * sizeof(float), cudaMemcpyHostToDevice,
                         h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) h->cv_ready = true;
-  { note_error_site(__FILE__, __LINE__); return map_err(e); }
+  if (e == cudaSuccess) {
+    h->cv_ready = true;
+    h->cv_c_ready = false;
+  }
+  if (e != cudaSuccess) note_error_site(__FILE__, __LINE__);
+  return map_err(e);
 }
 
 int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, const float *weight,
@@ -2219,7 +2241,8 @@ int rssri_cv_loss_grad(rssri_handle *h, const float *x, const float *target, con
   ck(cudaMemcpyAsync(loss, h->cv_loss.p, sizeof(float), cudaMemcpyDeviceToHost, s));
   ck(cudaMemcpyAsync(grad, h->cv_grad.p, pb, cudaMemcpyDeviceToHost, s));
   ck(cudaStreamSynchronize(s));
-  { note_error_site(__FILE__, __LINE__); return map_err(e); }
+  if (e != cudaSuccess) note_error_site(__FILE__, __LINE__);
+  return map_err(e);
 }
 
 int rssri_buffer_bytes(rssri_handle *h, int which, size_t *bytes) {
@@ -2305,7 +2328,8 @@ int rssri_export(rssri_handle *h, int which, void *dst, size_t bytes, int dst_ki
     default: return RSSRI_ERR_INVALID_ARG;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  { note_error_site(__FILE__, __LINE__); return map_err(e); }
+  if (e != cudaSuccess) note_error_site(__FILE__, __LINE__);
+  return map_err(e);
 }
 
 }  // extern "C"

@@ -24,6 +24,14 @@ __device__ __forceinline__ void put(float *p, double v) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(__double2float_rn(v)));
   *p = __uint_as_float(r);
 }
+// From fp32 (the fold's operands: fp32 products rounded once more to the
+// operand type; no fp64 instruction on the way)
+__device__ __forceinline__ void putf(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void putf(float *p, float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  *p = __uint_as_float(r);
+}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -105,7 +113,8 @@ __global__ void __launch_bounds__(256) fold_traces_kernel(const float *__restric
   const long long nn = (long long)n * n;
   const float *X = xy + x * nn, *Y = xy + (ns + x) * nn;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double dx = 0, dy = 0, sxx = 0, sxy = 0;
+  double dx = 0, dy = 0;
+  float sxx = 0.f, sxy = 0.f;  // per thread: 4 rows x the tile columns (fp32)
   if (ty == 0) {
     const int i = bi * 32 + tx;
     if (i < n) {
@@ -125,13 +134,13 @@ __global__ void __launch_bounds__(256) fold_traces_kernel(const float *__restric
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
-      const double xt = tb[tx][r];  // X_ji, i = bi*32 + r, j = bj*32 + tx
-      sxx += (double)ta[r][tx] * xt;
-      sxy += (double)tc[r][tx] * xt;
+      const float xt = tb[tx][r];  // X_ji, i = bi*32 + r, j = bj*32 + tx
+      sxx = fmaf(ta[r][tx], xt, sxx);
+      sxy = fmaf(tc[r][tx], xt, sxy);
     }
   }
-  const double v0 = block_sum_d(dx), v1 = block_sum_d(dy), v2 = block_sum_d(sxx),
-               v3 = block_sum_d(sxy);
+  const double v0 = block_sum_d(dx), v1 = block_sum_d(dy), v2 = block_sum_d((double)sxx),
+               v3 = block_sum_d((double)sxy);
   if (threadIdx.x == 0) {
     double *o = part + ((long long)x * nt + bi) * 4;
     o[0] = v0;
@@ -157,6 +166,7 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
   }
   __syncthreads();
   const double dt = sums[0], tl = sums[1];
+  const float dt2 = (float)(2.0 * dt), tl2 = (float)(2.0 * tl);
   const float *X = xy + x * nn, *Y = xy + (ns + x) * nn;
   const float *DC = dc + x * nn, *CL = cl + x * nn;
   T *A = a6 + x * mat, *Ab = a6 + (ns + x) * mat;
@@ -170,12 +180,11 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
         const long long o = (long long)i * ldp + j;
         if (j < n) {
           const long long s2 = (long long)i * n + j;
-          const double d = (i == j) ? 1.0 : 0.0;
-          put(&A[o], 2.0 * dt * d - (double)X[s2]);
-          put(&Ab[o], 2.0 * tl * d - (double)Y[s2]);
+          putf(&A[o], (i == j ? dt2 : 0.f) - X[s2]);
+          putf(&Ab[o], (i == j ? tl2 : 0.f) - Y[s2]);
         } else {
-          put(&A[o], 0.0);
-          put(&Ab[o], 0.0);
+          putf(&A[o], 0.f);
+          putf(&Ab[o], 0.f);
         }
       }
     }
@@ -192,9 +201,9 @@ __global__ void __launch_bounds__(256) fold_operands_kernel(
       const int i = bi * 32 + r, j = bj * 32 + tx;  // destination (i, j) = source (j, i)
       if (i < n && j < ldp) {
         const long long o = (long long)i * ldp + j;
-        put(&Ct[o], j < n ? (double)ta[tx][r] : 0.0);
-        put(&Dt[o], j < n ? (double)tb[tx][r] : 0.0);
-        if (clt) put(&clt[x * mat + o], j < n ? (double)tl32[tx][r] : 0.0);
+        putf(&Ct[o], j < n ? ta[tx][r] : 0.f);
+        putf(&Dt[o], j < n ? tb[tx][r] : 0.f);
+        if (clt) putf(&clt[x * mat + o], j < n ? tl32[tx][r] : 0.f);
       }
     }
     __syncthreads();

@@ -706,20 +706,29 @@ __device__ __forceinline__ void load8(const OzView &v, int b, long long r, long 
   }
 }
 
-// ef[b][r] = max biased exponent over the row; grid (rows * ceil(K / 2048), 1, batch),
-// blockIdx.x = r + rows * (2048-column block).
+// ef[b][r] = max biased exponent over the row; grid (rows * ceil(K / KCB), 1, batch),
+// blockIdx.x = r + rows * (KCB-column block); each thread takes KCB / 2048 groups
+// of 8 columns, their loads issued together.
+constexpr int KCU = 4, KCB = 256 * KC * KCU;
 __global__ void __launch_bounds__(256) oz_rowmax_kc_kernel(OzView v, int rows, long long K,
                                                            int *__restrict__ ef) {
   __shared__ int wm[8];
   const int b = blockIdx.z, r = (int)(blockIdx.x % (unsigned)rows);
-  const long long k0 = ((long long)(blockIdx.x / (unsigned)rows) * 256 + threadIdx.x) * KC;
+  const long long kb = (long long)(blockIdx.x / (unsigned)rows) * KCB;
   int m = 0;
-  if (k0 < K) {
-    double x[KC];
-    load8(v, b, r, k0, K, x);
+  double x[KCU][KC];
 #pragma unroll
-    for (int u = 0; u < KC; ++u) m = max(m, ef_of(x[u]));
+  for (int g = 0; g < KCU; ++g) {
+    const long long k0 = kb + ((long long)g * 256 + threadIdx.x) * KC;
+    if (k0 < K) load8(v, b, r, k0, K, x[g]);
+    else
+#pragma unroll
+      for (int u = 0; u < KC; ++u) x[g][u] = 0.0;
   }
+#pragma unroll
+  for (int g = 0; g < KCU; ++g)
+#pragma unroll
+    for (int u = 0; u < KC; ++u) m = max(m, ef_of(x[g][u]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
@@ -1029,7 +1038,7 @@ cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
   const long long rtiles = ((long long)out.rows + SR - 1) / SR;
   // rows contiguous along K, 16-byte aligned: the vectorised path
   const uintptr_t base = v.x2 ? (uintptr_t)v.x2 : (uintptr_t)v.x;
-  const long long kcb = (out.K + 256LL * KC - 1) / (256LL * KC);  // 2048-column blocks
+  const long long kcb = (out.K + KCB - 1) / KCB;  // column blocks of the maximum pass
   const bool kc = v.cs2 == 1 && v.k2off == 0 && v.k2pad >= out.K && v.k2n >= out.K &&
                   base % 16 == 0 && v.rs % 2 == 0 && v.bs % 2 == 0 &&
                   kcb * out.rows <= 0x7FFFFFFFLL;

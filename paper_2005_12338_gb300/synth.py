@@ -118,8 +118,9 @@ def make_system_torch(n: int, n_occ: int, n_aux: int, n_tau: int, input_seed: in
     del b
     orb_e = torch.cat([torch.linspace(-1.0, gap_lo, n_occ, **f64),
                        torch.linspace(gap_hi, 2.0, n - n_occ, **f64)])
-    q, r = torch.linalg.qr(torch.randn((n, n), generator=gen, **f64))
-    q = (q * torch.sign(torch.diagonal(r))[None, :]).contiguous()
+    # the QR on the host (small; no dependence on the device linear-algebra library)
+    q, r = torch.linalg.qr(torch.randn((n, n), generator=gen, **f64).cpu())
+    q = (q * torch.sign(torch.diagonal(r))[None, :]).contiguous().to(device)
     tau, tau_w = tau_grid(n_tau, beta, tau_s)
     return System(n=n, n_occ=n_occ, n_aux=n_aux, eri3=eri3.contiguous(), metric=metric,
                   orb_e=orb_e.contiguous(), orb_c=q, mu=0.5 * (gap_lo + gap_hi), beta=beta,
