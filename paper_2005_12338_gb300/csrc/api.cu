@@ -127,6 +127,7 @@ struct rssri_handle {
   DevBuf eri_hl, ut_hl;
   // pair copies of the Newton-Schulz operands (double-float metric root)
   DevBuf nsA2, nsB2;
+  DevBuf elHl;  // (ij|A)^L rows as pairs (double-float [K]^L)
   // double-float chain: factor pairs, X G and C pairs, (2tI - B) pairs
   DevBuf facHl, xgHl, cHl, bHl;
   bool d_df64_ready = false;
@@ -164,6 +165,9 @@ struct rssri_handle {
   DevBuf oz_pidx, oz_tmp;
   OzBuf ozX, ozKP, ozKPt, ozGb, ozBig0, ozBig1, ozAtP, ozGam;
   OzBuf ozPA, ozPB;  // operands of the setup and factor products (RSSRI_DD_OZ)
+  OzBuf ozKPr, ozGr;  // row-batched operands of K^Q G (see oz_rows_kp)
+  DevBuf oz_gr;       // G gathered by pair rows, fp64 [n][n][oz_w]
+  int oz_w = 0;       // longest row of the pair list, rounded up to 16
   rssri_stats stats{};
 
   // per-class launch counts and (when profiling) event timings
@@ -357,7 +361,9 @@ int metric_inv_sqrt(rssri_handle *h, int *rc, bool df64) {
     RS_CK(ensure(h->nsA2, (size_t)na * na * sizeof(float2)));
     RS_CK(ensure(h->nsB2, (size_t)na * na * sizeof(float2)));
   }
-  // C = A B (na x na), in fp64 or in double-float on split copies
+  // C = A B (na x na), in fp64 or in double-float on split copies (the
+  // coupled iteration keeps the errors of its products as a perturbation of
+  // the metric it implies, so it runs in fp64-accurate arithmetic throughout)
   auto mm = [&](const double *A, const double *B, double *C) -> cudaError_t {
     if (!df64) {
       GemmArgs g;
@@ -478,14 +484,16 @@ void rssri_destroy(rssri_handle *h) {
                     &h->trdd, &h->tr, &h->res, &h->sig_out, &h->e_pair, &h->gwork, &h->outbuf,
                     &h->hxsl, &h->hy3, &h->hg, &h->hgb, &h->hP, &h->hdc32, &h->hcl32,
                     &h->hdcl16, &h->hxy32, &h->ha6, &h->hct, &h->hdct, &h->hpart, &h->hfold, &h->hclt, &h->hfl, &h->Dhl,
-                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->facHl, &h->xgHl, &h->cHl, &h->bHl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
+                    &h->Ahl, &h->KPhl, &h->PGhl, &h->APhl, &h->Gamhl, &h->GGhl, &h->litMP, &h->litT, &h->litMhl, &h->eri_hl, &h->ut_hl, &h->nsA2, &h->nsB2, &h->elHl, &h->facHl, &h->xgHl, &h->cHl, &h->bHl, &h->cv_params, &h->cv_m, &h->cv_v, &h->cv_grad, &h->cv_ptmp,
                     &h->cv_act, &h->cv_work, &h->cv_X, &h->cv_t, &h->cv_w, &h->cv_stats, &h->cv_c,
                     &h->cv_scr, &h->cv_bx, &h->cv_bt, &h->cv_bw, &h->cv_loss, &h->sdd0, &h->oz_gs, &h->oz_gexp};
   for (DevBuf *b : bufs) release(*b);
   release(h->oz_pidx);
   release(h->oz_tmp);
+  release(h->oz_gr);
   for (rssri_handle::OzBuf *o : {&h->ozX, &h->ozKP, &h->ozKPt, &h->ozGb, &h->ozBig0, &h->ozBig1,
-                                 &h->ozAtP, &h->ozGam, &h->ozPA, &h->ozPB}) {
+                                 &h->ozAtP, &h->ozGam, &h->ozPA, &h->ozPB, &h->ozKPr,
+                                 &h->ozGr}) {
     release(o->d);
     release(o->e);
   }
@@ -611,13 +619,29 @@ int rssri_setup(rssri_handle *h, const rssri_problem *p, const rssri_options *o)
   if (P_s > 0) {
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(eri_gather_rows(h->eri3, n, na, h->colmax.as<double>(), o->eps_prime,
                           h->spairs.as<int>(), P_s, h->EL.as<double>(), s)); }
-    // in IEEE fp64 in every form: the cut of Eq. 13 compares these values
-    GemmArgs g;
-    g.M = P_s; g.N = na; g.K = na;
-    g.A = h->EL.as<double>(); g.lda = na;
-    g.B = h->W.as<double>(); g.ldb = na;
-    g.C = h->KLs.as<double>(); g.ldc = na;
-    RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    // in IEEE fp64, or in double-float (~1e-14) under the double-float and
+    // sliced blocks: the cut of Eq. 13 compares these values
+    if (o->dd_arith != RSSRI_DD_FP64) {
+      RS_CK(ensure(h->elHl, (size_t)P_s * na * sizeof(float2)));
+      RS_CK(ensure(h->nsB2, (size_t)na * na * sizeof(float2)));
+      { SPAN(RSSRI_PROF_OTHER, 0.0);
+        RS_CK(to_df64(h->EL.as<double>(), (long long)P_s * na, h->elHl.as<float2>(), s, range_flag(h)));
+        RS_CK(to_df64(h->W.as<double>(), (long long)na * na, h->nsB2.as<float2>(), s, range_flag(h))); }
+      SPAN(RSSRI_PROF_SETUP_GEMM, 2.0 * P_s * (double)na * na * 1e-9);
+      DfGemm g;
+      g.M = P_s; g.N = na; g.K = na;
+      g.A = h->elHl.as<float2>(); g.lda = na;
+      g.B = h->nsB2.as<float2>(); g.ldb = na;
+      g.C64 = h->KLs.as<double>(); g.ldc = na;
+      RS_CK(df_gemm_w(h, g));
+    } else {
+      GemmArgs g;
+      g.M = P_s; g.N = na; g.K = na;
+      g.A = h->EL.as<double>(); g.lda = na;
+      g.B = h->W.as<double>(); g.ldb = na;
+      g.C = h->KLs.as<double>(); g.ldc = na;
+      RS_CK(gemm_p(h, RSSRI_PROF_SETUP_GEMM, g));
+    }
     double *scal = h->scal.as<double>();
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(absmax(h->KLs.as<double>(), (long long)P_s * na, scal + 2, h->part.as<double>(), s)); }
     { SPAN(RSSRI_PROF_OTHER, 0.0); RS_CK(kl_cut(h->KLs.as<double>(), P_s, na, scal + 2, o->eps, h->cnt2.as<int>(), s)); }
@@ -992,6 +1016,24 @@ int oz_setup(rssri_handle *h) {
     t.rs = 1; t.cs2 = na; t.k2pad = t.k2n = P; t.xlen = (long long)P * na;
     RS_CK(oz_slice_p(h, t, h->ozKPt.v));
   }
+  // K_P by rows i of the pair list, padded to W: the right operand of K^Q G
+  {
+    std::vector<int> rp(n + 1);
+    RS_CK(fetch(rp.data(), h->rowptr.p, s, n + 1));
+    int wmax = 1;
+    for (int i = 0; i < n; ++i) wmax = std::max(wmax, rp[i + 1] - rp[i]);
+    h->oz_w = (wmax + 15) / 16 * 16;
+    const int W = h->oz_w;
+    const long long len = (long long)n * na * W;
+    RS_CK(ensure(h->oz_tmp, std::max(h->oz_tmp.bytes, (size_t)len * sizeof(double))));
+    { SPAN(RSSRI_PROF_OTHER, 0.0);
+      RS_CK(oz_rows_kp(h->KP.as<double>(), h->rowptr.as<int>(), n, na, W, h->oz_tmp.as<double>(), s)); }
+    RS_CK(oz_make(h->ozKPr, n, na, W));
+    OzView v;
+    v.x = h->oz_tmp.as<double>();
+    v.bs = (long long)na * W; v.rs = W; v.cs2 = 1; v.k2pad = v.k2n = W; v.xlen = len;
+    RS_CK(oz_slice_p(h, v, h->ozKPr.v));
+  }
   RS_CK(cudaStreamSynchronize(s));
   release(h->oz_tmp);
   h->oz_ready = true;
@@ -1003,28 +1045,41 @@ int oz_setup(rssri_handle *h) {
 // the tensor cores (sliced fp64-accurate products), the segmented K^Q G in
 // double-float.  With T stored negated by the contraction, U = 2 L - T and
 // Sigma_DD = sum_Q PG^Q U^Q, PG^Q = K^Q G (see sigma_dd_tau).
-cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb, double *out) {
+cudaError_t sigma_dd_tau_oz(rssri_handle *h, const double *Gt, const double *Gb, double *out) {
   cudaStream_t s = h->stream;
   const int n = h->n, na = h->n_aux, P = h->P;
   const long long nn = (long long)n * n, nna = nn * na;
   if (P == 0) return cudaMemsetAsync(out, 0, nn * sizeof(double), s);
   const OzExch &x = h->oz_geo;
   int *err = h->flags.as<int>() + 5;
-  float2 *PGhl = h->PGhl.as<float2>();
+  double *PG = h->PG.as<double>();
   // T (the exchange's output) takes At's buffer once At's rows at the kept
   // pairs are gathered and At is sliced
   double *At = h->At.as<double>(), *T = At;
-  // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]   (double-float)
-  { SPAN(RSSRI_PROF_DD_GEMM, 2.0 * n * (double)na * P * 1e-9);
-    RS_TRY(df_gemm_segmented(n, n, na, h->rowptr.as<int>(), h->pcol.as<int>(), Ghl, n,
-                             h->KPhl.as<float2>(), na, PGhl, na, (long long)n * na, s)); }
+  // PG[i][m][Q] = sum_{k in row i} K_P[(i,k)][Q] G[k][m]: batched over the rows i of the
+  // pair list, K = the row's pairs (padded to W), both operands sliced
+  {
+    const int W = h->oz_w;
+    { SPAN(RSSRI_PROF_OTHER, 0.0);
+      RS_TRY(oz_rows_g(Gt, h->rowptr.as<int>(), h->pcol.as<int>(), n, W, h->oz_gr.as<double>(), s)); }
+    OzView v;
+    v.x = h->oz_gr.as<double>();
+    v.bs = (long long)n * W; v.rs = W; v.cs2 = 1; v.k2pad = v.k2n = W;
+    v.xlen = (long long)n * n * W;
+    RS_TRY(oz_slice_p(h, v, h->ozGr.v));
+    OzGemm g;
+    g.A = h->ozGr.v; g.B = h->ozKPr.v;
+    g.M = n; g.N = na; g.batch = n;
+    g.C = PG; g.ldc = na; g.sC = (long long)n * na; g.ccap = nna; g.err = err;
+    RS_TRY(oz_gemm_p(h, RSSRI_PROF_DD_GEMM, g));
+  }
   // At[k][(l,Q)] = sum_m Gb[k][m] PG[m][(l,Q)]
   OzDigits &dGb = h->ozGb.v;
   { OzView v; v.x = Gb; v.rs = n; v.cs2 = 1; v.k2pad = v.k2n = n; v.xlen = nn;
     RS_TRY(oz_slice_p(h, v, dGb)); }
   OzDigits dPGb = h->ozBig0.v;
   dPGb.rows = (int)(n * (long long)na); dPGb.K = n; dPGb.ld = (n + 15) / 16 * 16;
-  { OzView v; v.x2 = PGhl; v.rs = 1; v.cs2 = (long long)n * na; v.k2pad = v.k2n = n;
+  { OzView v; v.x = PG; v.rs = 1; v.cs2 = (long long)n * na; v.k2pad = v.k2n = n;
     v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dPGb)); }
   {
@@ -1076,7 +1131,7 @@ cudaError_t sigma_dd_tau_oz(rssri_handle *h, const float2 *Ghl, const double *Gb
     RS_TRY(oz_slice_p(h, v, dU)); }
   OzDigits dPGa = h->ozBig1.v;
   dPGa.rows = n; dPGa.K = kmq; dPGa.ld = (kmq + 15) / 16 * 16;
-  { OzView v; v.x2 = PGhl; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dPGa.K;
+  { OzView v; v.x = PG; v.rs = (long long)n * na; v.cs2 = 1; v.k2pad = v.k2n = dPGa.K;
     v.xlen = nna;
     RS_TRY(oz_slice_p(h, v, dPGa)); }
   {
@@ -1167,12 +1222,13 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
     if (dd_oz) {
       // the exchange operand first (its fp64 gather is freed before the
       // per-tau buffers are made), then the per-tau buffers; T shares At's
-      RS_CK(ensure_kp_df64(h));
       if (!h->oz_ready) {
         const int rc = oz_setup(h);
         if (rc) return rc;
       }
-      RS_CK(ensure(h->PGhl, (size_t)nn * na * sizeof(float2)));
+      RS_CK(ensure(h->PG, (size_t)nn * na * sizeof(double)));
+      RS_CK(ensure(h->oz_gr, (size_t)nn * h->oz_w * sizeof(double)));
+      RS_CK(oz_make(h->ozGr, n, n, h->oz_w));
       RS_CK(ensure(h->At, (size_t)nn * na * sizeof(double)));
       RS_CK(ensure(h->AP, (size_t)P * na * sizeof(double)));
       // the largest per-tau digit operand: n*na rows of ld16(n), n rows of ld16(n*na), or
@@ -1218,19 +1274,10 @@ int build_block(rssri_handle *h, int dd_arith, const double *g_in, const double 
   }
   // S7 per tau
   if (dd_df64) RS_CK(ensure_gg(h));
-  if (dd_oz) {
-    // K^Q G in double-float on G(tau) 2^-e(tau); Sigma_DD is then 2^(2 e) times the result
-    RS_CK(ensure(h->oz_gs, (size_t)nt * nn * sizeof(float2)));
-    RS_CK(ensure(h->oz_gexp, (size_t)nt * sizeof(int)));
-    SPAN(RSSRI_PROF_OTHER, 0.0);
-    RS_CK(to_df64_scaled(G, nt, nn, h->oz_gs.as<float2>(), h->oz_gexp.as<int>(), s));
-  }
   for (int t = 0; t < nt; ++t) {
     double *out = h->sdd.as<double>() + t * nn;
     if (dd_oz) {
-      RS_CK(sigma_dd_tau_oz(h, h->oz_gs.as<float2>() + t * nn, Gb + t * nn, out));
-      SPAN(RSSRI_PROF_OTHER, 0.0);
-      RS_CK(scale_pow2(out, nn, h->oz_gexp.as<int>() + t, 2, s));
+      RS_CK(sigma_dd_tau_oz(h, G + t * nn, Gb + t * nn, out));
     } else if (dd_df64)
       RS_CK(sigma_dd_tau_df64(h, h->GGhl.as<float2>() + t * nn,
                               h->GGhl.as<float2>() + (nt + t) * nn, out));

@@ -150,65 +150,64 @@ __global__ void __launch_bounds__(256) fold_traces_kernel(const float *__restric
   }
 }
 
+// One 32 x 32 tile (bi, bj) of pair x per block: every load of the tile is
+// issued before the first store; the transposes go through shared memory.
 template <class T>
 __global__ void __launch_bounds__(256) fold_operands_kernel(
     const float *__restrict__ xy, const float *__restrict__ dc, const float *__restrict__ cl, int ns,
-    int n, int ldp, const double *__restrict__ part, double w, double ne, T *__restrict__ a6,
-    T *__restrict__ ct, T *__restrict__ dct, T *__restrict__ clt, double *__restrict__ e_st) {
+    int n, int ldp, int nt, const double *__restrict__ part, double w, double ne,
+    T *__restrict__ a6, T *__restrict__ ct, T *__restrict__ dct, T *__restrict__ clt,
+    double *__restrict__ e_st) {
   __shared__ float ta[32][33], tb[32][33], tl32[32][33];
   __shared__ double sums[4];
-  const int bi = blockIdx.x, x = blockIdx.y, nt = gridDim.x;
+  const int bj = blockIdx.x, bi = blockIdx.y, x = blockIdx.z;
   const long long nn = (long long)n * n, mat = (long long)n * ldp;
   if (threadIdx.x < 4) {
     double v = 0;
     for (int t = 0; t < nt; ++t) v += part[((long long)x * nt + t) * 4 + threadIdx.x];
     sums[threadIdx.x] = v;
   }
-  __syncthreads();
-  const double dt = sums[0], tl = sums[1];
-  const float dt2 = (float)(2.0 * dt), tl2 = (float)(2.0 * tl);
   const float *X = xy + x * nn, *Y = xy + (ns + x) * nn;
   const float *DC = dc + x * nn, *CL = cl + x * nn;
   T *A = a6 + x * mat, *Ab = a6 + (ns + x) * mat;
   T *Ct = ct + x * mat, *Dt = dct + x * mat;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int ntp = (ldp + 31) / 32;
-  for (int bj = 0; bj < ntp; ++bj) {
-    for (int r = ty; r < 32; r += 8) {
-      const int i = bi * 32 + r, j = bj * 32 + tx;
-      if (i < n && j < ldp) {
-        const long long o = (long long)i * ldp + j;
-        if (j < n) {
-          const long long s2 = (long long)i * n + j;
-          putf(&A[o], (i == j ? dt2 : 0.f) - X[s2]);
-          putf(&Ab[o], (i == j ? tl2 : 0.f) - Y[s2]);
-        } else {
-          putf(&A[o], 0.f);
-          putf(&Ab[o], 0.f);
-        }
-      }
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const int i = bj * 32 + r, j = bi * 32 + tx;  // source (i, j) of C and dC
-      const bool in = i < n && j < n;
-      ta[r][tx] = in ? CL[(long long)i * n + j] + DC[(long long)i * n + j] : 0.f;
-      tb[r][tx] = in ? DC[(long long)i * n + j] : 0.f;
-      tl32[r][tx] = in ? CL[(long long)i * n + j] : 0.f;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const int i = bi * 32 + r, j = bj * 32 + tx;  // destination (i, j) = source (j, i)
-      if (i < n && j < ldp) {
-        const long long o = (long long)i * ldp + j;
-        putf(&Ct[o], j < n ? ta[tx][r] : 0.f);
-        putf(&Dt[o], j < n ? tb[tx][r] : 0.f);
-        if (clt) putf(&clt[x * mat + o], j < n ? tl32[tx][r] : 0.f);
-      }
-    }
-    __syncthreads();
+  // loads: rows ty, ty + 8, ... of the tile of X and Y, and of the
+  // transposed-source tile (bj, bi) of C^L and dC
+  float xv[4], yv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = ty + 8 * u;
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    const bool in = i < n && j < n;
+    xv[u] = in ? X[(long long)i * n + j] : 0.f;
+    yv[u] = in ? Y[(long long)i * n + j] : 0.f;
+    const int i2 = bj * 32 + r, j2 = bi * 32 + tx;  // source (i2, j2) of C and dC
+    const bool in2 = i2 < n && j2 < n;
+    const float c = in2 ? CL[(long long)i2 * n + j2] : 0.f;
+    const float d = in2 ? DC[(long long)i2 * n + j2] : 0.f;
+    ta[r][tx] = c + d;
+    tb[r][tx] = d;
+    tl32[r][tx] = c;
   }
-  if (bi == 0 && threadIdx.x == 0) {
+  __syncthreads();
+  const double dt = sums[0], tl = sums[1];
+  const float dt2 = (float)(2.0 * dt), tl2 = (float)(2.0 * tl);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = ty + 8 * u;
+    const int i = bi * 32 + r, j = bj * 32 + tx;  // destination (i, j) = source (j, i)
+    if (i < n && j < ldp) {
+      const long long o = (long long)i * ldp + j;
+      const bool in = j < n;
+      putf(&A[o], in ? (i == j ? dt2 : 0.f) - xv[u] : 0.f);
+      putf(&Ab[o], in ? (i == j ? tl2 : 0.f) - yv[u] : 0.f);
+      putf(&Ct[o], in ? ta[tx][r] : 0.f);
+      putf(&Dt[o], in ? tb[tx][r] : 0.f);
+      if (clt) putf(&clt[x * mat + o], in ? tl32[tx][r] : 0.f);
+    }
+  }
+  if (bi == 0 && bj == 0 && threadIdx.x == 0) {
     const double de = 2.0 * dt * (2.0 * tl + dt) - sums[2] - 2.0 * sums[3];
     e_st[x] += -w * de / ne;
   }
@@ -249,8 +248,17 @@ __global__ void reduce_tc_kernel(const float *__restrict__ part, int groups, lon
                                    double *__restrict__ sig) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
        e += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int g = 0; g < groups; ++g) acc += (double)part[g * nn + e];
+    // four independent partial sums (loads in flight), added in a fixed order
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int g = 0;
+    for (; g + 4 <= groups; g += 4) {
+      a0 += part[(long long)g * nn + e];
+      a1 += part[(long long)(g + 1) * nn + e];
+      a2 += part[(long long)(g + 2) * nn + e];
+      a3 += part[(long long)(g + 3) * nn + e];
+    }
+    for (; g < groups; ++g) a0 += part[(long long)g * nn + e];
+    const double acc = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
     sig[e] = base[e] + acc / ns;
   }
 }
@@ -284,18 +292,21 @@ cudaError_t chain_matrices(int kind, const double *src, int cnt, int n, int ldp,
 cudaError_t fold_tc(int kind, const float *xy, const float *dc, const float *cl, int ns, int n,
                     int ldp, double w, double ne, void *a6, void *ct, void *dct, void *clt,
                     double *e_st, double *part, cudaStream_t s) {
-  dim3 grid((n + 31) / 32, ns);
+  const int nt = (n + 31) / 32;
+  dim3 grid(nt, ns);
   fold_traces_kernel<<<grid, 256, 0, s>>>(xy, ns, n, part);
   ++launch_counter();
   RS_TRY(cudaGetLastError());
+  if (ns > 65535) return cudaErrorInvalidValue;
+  dim3 go((ldp + 31) / 32, nt, ns);
   if (kind == TC_BF16)
-    fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne,
+    fold_operands_kernel<<<go, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, nt, part, w, ne,
                                               static_cast<__nv_bfloat16 *>(a6),
                                               static_cast<__nv_bfloat16 *>(ct),
                                               static_cast<__nv_bfloat16 *>(dct),
                                               static_cast<__nv_bfloat16 *>(clt), e_st);
   else
-    fold_operands_kernel<<<grid, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, part, w, ne,
+    fold_operands_kernel<<<go, 256, 0, s>>>(xy, dc, cl, ns, n, ldp, nt, part, w, ne,
                                               static_cast<float *>(a6), static_cast<float *>(ct),
                                               static_cast<float *>(dct),
                                               static_cast<float *>(clt), e_st);

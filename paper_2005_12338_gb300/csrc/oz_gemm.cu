@@ -886,6 +886,33 @@ __global__ void oz_exch_gather_kernel(int n, int bk, int nl16, int jtiles, long 
   }
 }
 
+__global__ void oz_rows_kp_kernel(const double *__restrict__ KP, const int *__restrict__ rowptr,
+                                  int n, int na, int W, double *__restrict__ out) {
+  const long long tot = (long long)n * na * W;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % W);
+    const long long iq = e / W;
+    const int q = (int)(iq % na), i = (int)(iq / na);
+    const int a = rowptr[i] + c;
+    out[e] = a < rowptr[i + 1] ? KP[(long long)a * na + q] : 0.0;
+  }
+}
+
+__global__ void oz_rows_g_kernel(const double *__restrict__ G, const int *__restrict__ rowptr,
+                                 const int *__restrict__ pcol, int n, int W,
+                                 double *__restrict__ out) {
+  const long long tot = (long long)n * n * W;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % W);
+    const long long im = e / W;
+    const int m = (int)(im % n), i = (int)(im / n);
+    const int a = rowptr[i] + c;
+    out[e] = a < rowptr[i + 1] ? G[(long long)pcol[a] * n + m] : 0.0;
+  }
+}
+
 __global__ void oz_pair_index_kernel(const int *__restrict__ pij, int P, int n,
                                      int *__restrict__ pidx) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < P; a += gridDim.x * blockDim.x)
@@ -1144,6 +1171,26 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
     RS_TRY(cudaGetLastError());
   }
   return cudaSuccess;
+}
+
+cudaError_t oz_rows_kp(const double *KP, const int *rowptr, int n, int na, int W, double *out,
+                       cudaStream_t s) {
+  const long long tot = (long long)n * na * W;
+  if (tot <= 0) return cudaSuccess;
+  oz_rows_kp_kernel<<<(int)std::min<long long>((tot + 255) / 256, 152 * 16), 256, 0, s>>>(
+      KP, rowptr, n, na, W, out);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+cudaError_t oz_rows_g(const double *G, const int *rowptr, const int *pcol, int n, int W,
+                      double *out, cudaStream_t s) {
+  const long long tot = (long long)n * n * W;
+  if (tot <= 0) return cudaSuccess;
+  oz_rows_g_kernel<<<(int)std::min<long long>((tot + 255) / 256, 152 * 16), 256, 0, s>>>(
+      G, rowptr, pcol, n, W, out);
+  ++launch_counter();
+  return cudaGetLastError();
 }
 
 cudaError_t oz_pair_index(const int *pij, int P, int n, int *pidx, cudaStream_t s) {

@@ -114,6 +114,17 @@ cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, doub
                     long long tcap, double alpha, int *err, cudaStream_t s, int wait_polls = 0);
 double oz_exch_flops(const OzExch &x);
 
+// Row-batched operands of K^Q G, the block's first product (PG[i][m][Q] =
+// sum over the kept pairs a = (i, k) of row i of K_P[a][Q] G[k][m]), padded to
+// W columns per row i of the pair list (CSR rowptr, pair columns pcol):
+//   oz_rows_kp:  out[i][Q][c] = K_P[rowptr[i] + c][Q]   ([n][na][W])
+//   oz_rows_g:   out[i][m][c] = G[pcol[rowptr[i] + c]][m] ([n][n][W])
+// with zeros for c >= the row's length.
+cudaError_t oz_rows_kp(const double *KP, const int *rowptr, int n, int na, int W, double *out,
+                       cudaStream_t s);
+cudaError_t oz_rows_g(const double *G, const int *rowptr, const int *pcol, int n, int W,
+                      double *out, cudaStream_t s);
+
 // pidx[i*n + j] = index of pair (i, j) among the P kept pairs (linear
 // indices pij, ascending), -1 for pairs not kept.
 cudaError_t oz_pair_index(const int *pij, int P, int n, int *pidx, cudaStream_t s);

@@ -6,10 +6,10 @@ G) and return RSSRI_ERR_RANGE when its largest magnitude lies outside
 [2^-40, 2^40], instead of losing precision silently.  (The N=200 workload's
 block intermediates at its largest tau points lie below 2^-40 with no loss:
 the parity tests of the double-float forms cover them.)  The sliced tensor-core
-block (RSSRI_DD_OZ) scales each row by a power of two and runs its one
-double-float step (K^Q G) on G normalised per tau point, so it keeps fp64's
-range: with G(tau) and G(beta - tau) scaled by 2^-100 (entries near 1e-35 and
-below) it must still match the oracle to 1e-10, as the IEEE fp64 form does."""
+block (RSSRI_DD_OZ) scales each row of every operand by a power of two, so it
+keeps fp64's range: with G(tau) and G(beta - tau) scaled by 2^-100 (entries
+near 1e-35 and below) it must still match the oracle to 1e-10, as the IEEE
+fp64 form does."""
 import numpy as np
 import pytest
 
