@@ -527,6 +527,7 @@ __global__ void oz_reduce_kernel(const double *__restrict__ work, int ks, int M,
 // Tiles of 32 rows x 64 digit columns; the source is read along its
 // contiguous index (rows when rs == 1, else columns) through shared memory.
 constexpr int SR = 32, SK = 64;
+constexpr int KC = 8;  // columns per thread of the digit passes
 
 // Element (b, r, kk) of the view, kk = k1 k2pad + k2 given as (k1, k2).
 __device__ __forceinline__ double view_at(const OzView &v, int b, long long r, long long k1,
@@ -650,19 +651,30 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
   const long long r0 = ((long long)blockIdx.x % rtiles) * SR, k0 = ((long long)blockIdx.x / rtiles) * SK;
   load_tile(v, b, r0, k0, rows, K, s);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < SR * SK; idx += blockDim.x) {
-    const int k = idx % SK, r = idx / SK;
-    const long long rr = r0 + r, kk = k0 + k;
-    if (rr >= rows || kk >= ld) continue;
-    const int e = row_scale(ef[(long long)b * rows + rr]);
-    float d[OZ_S];
-    digits_of(s[r][k], e, d);
-    const long long blk = ((long long)b * rows + rr) * (ld / 16) + (kk >> 4);
-    if (!OZ_IN(blk * 64 + 63, g1, 31)) continue;
+  // one thread per 8 consecutive columns of one row (256 threads = 32 rows x
+  // 8 groups): 16-byte stores into each digit slot
+  const int r = threadIdx.x / 8, c0 = (threadIdx.x % 8) * KC;
+  const long long rr = r0 + r, kk0 = k0 + c0;
+  if (rr >= rows || kk0 >= ld) return;
+  const int e = row_scale(ef[(long long)b * rows + rr]);
+  uint32_t w[OZ_S][KC / 2];
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p)
-      out[digit_off(blk, (int)(kk & 15), p, g1)] = __float2bfloat16_rn(d[p]);
+  for (int u = 0; u < KC; u += 2) {
+    float d0[OZ_S], d1[OZ_S];
+    digits_of(s[r][c0 + u], e, d0);
+    digits_of(s[r][c0 + u + 1], e, d1);
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[p], d1[p]);
+      w[p][u / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+    }
   }
+  const long long blk = ((long long)b * rows + rr) * (ld / 16) + (kk0 >> 4);
+  if (!OZ_IN(blk * 64 + 63, g1, 31)) return;
+#pragma unroll
+  for (int p = 0; p < OZ_S; ++p)
+    *reinterpret_cast<uint4 *>(out + digit_off(blk, (int)(kk0 & 15), p, g1)) =
+        make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
 // ---------------------------------------- K-contiguous sources (fast path) --
@@ -670,7 +682,6 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
 // 16-byte aligned rows: each thread takes 8 consecutive columns of one row
 // (four 16-byte loads) and, in the digit pass, writes 16 bytes to each of the
 // six digit slots.  No shared-memory transpose.
-constexpr int KC = 8;  // columns per thread
 
 __device__ __forceinline__ void load8(const OzView &v, int b, long long r, long long k0,
                                       long long K, double *x) {
