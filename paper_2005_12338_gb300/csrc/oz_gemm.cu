@@ -78,7 +78,9 @@ struct OzParams {
   int bshared;       // dense: B has one batch entry
   const int *efa, *efb;
   long long efa_bs, efb_bs;
-  double alpha;
+  int neg;    // C = -(the product) instead of +(the product)
+  int vec2;   // every output row starts 16-byte aligned: column pairs go out as one store
+  int mfast;  // dense: m tile fastest in the tile order (else n tile fastest)
   double *C;
   long long ldc, sC;
   int bk, nl16, jtiles, lb0;  // exchange geometry
@@ -183,12 +185,13 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t *r) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
+// 16 lanes x 256 bits (8 columns): thread t holds lane (t >> 2) at columns
+// 2 (t & 3) and 2 (t & 3) + 1 in r[0], r[1], and lane (t >> 2) + 8 at the same
+// columns in r[2], r[3]; four threads cover a lane's 8 columns.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, uint32_t *r) {
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 
 // ----------------------------------------------------- exact float sums ----
@@ -230,6 +233,13 @@ __device__ __forceinline__ double f32_scaled(float f, int E) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)e64 << 52) | mant));
 }
 
+// The rare operands of df_to_f64 (zero, tiny, huge, non-finite): one fp64 add.
+// Kept out of line so that the fp64 work is never executed speculatively on
+// the common path (the fp64 pipe runs at 1/64 of the fp32 rate).
+__device__ __noinline__ double df_to_f64_add(float hi, float lo, int E) {
+  return f32_scaled(hi, E) + f32_scaled(lo, E);
+}
+
 // (hi + lo) 2^E as fp64 with integer operations only (the fp64 pipe runs at
 // 1/64 of the fp32 rate here): hi's 53-bit significand plus lo in units of
 // hi's fp64 ulp, renormalised by at most one bit.  (hi, lo) comes from a
@@ -245,7 +255,7 @@ __device__ __forceinline__ double df_to_f64(float hi, float lo, int E) {
   const int sh = el - eh + 29;  // lo's unit shift relative to hi's fp64 ulp
   const bool lo_zero = (ul << 1) == 0;
   if (eh < 64 || eh == 255 || e64 < 2 || e64 > 2045 || (!lo_zero && (el == 0 || sh > 6)))
-    return f32_scaled(hi, E) + f32_scaled(lo, E);
+    return df_to_f64_add(hi, lo, E);
   long long S = (long long)((1u << 23) | (uh & 0x7FFFFFu)) << 29;
   if (!lo_zero) {
     const long long ml = (long long)((1u << 23) | (ul & 0x7FFFFFu));
@@ -273,18 +283,29 @@ __device__ __forceinline__ int row_scale(int ef) { return max(ef, 1) - 1022; }
 struct OzTile {
   int n0, m0, zb, split, rt, mt, jt;
 };
+// With mfast: q = m tile + mtiles * (n tile + ntiles * (batch * ksplit + split)).
 template <int MODE>
 __device__ __forceinline__ OzTile oz_tile(const OzParams &p, int q) {
   OzTile t;
-  const int rest = q / p.ntiles;
-  t.n0 = (q - rest * p.ntiles) * BN;
   if (MODE == 0) {
-    const int z = rest / p.mtiles;
-    t.m0 = (rest - z * p.mtiles) * BM;
+    int z;
+    if (p.mfast) {
+      const int rest = q / p.mtiles;
+      t.m0 = (q - rest * p.mtiles) * BM;
+      z = rest / p.ntiles;
+      t.n0 = (rest - z * p.ntiles) * BN;
+    } else {
+      const int rest = q / p.ntiles;
+      t.n0 = (q - rest * p.ntiles) * BN;
+      z = rest / p.mtiles;
+      t.m0 = (rest - z * p.mtiles) * BM;
+    }
     t.zb = z / p.ksplit;
     t.split = z - t.zb * p.ksplit;
     t.rt = t.mt = t.jt = 0;
   } else {
+    const int rest = q / p.ntiles;
+    t.n0 = (q - rest * p.ntiles) * BN;
     t.rt = rest;
     t.mt = rest / p.jtiles;
     t.jt = rest - t.mt * p.jtiles;
@@ -415,10 +436,14 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
       mma_commit(done);
     }
   } else {
-    // drain warps
-    const int lq = warp & 3;            // tensor-memory lanes this warp may access
-    const int cq = (warp - 2) >> 2;     // column quarter of the tile
-    const int row = lq * 32 + lane;
+    // drain warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (the
+    // rows of its lane quarter) and columns 32 cq .. + 31 of each accumulator,
+    // as eight 16 x 8 fragments (16x256b loads): fragment f = 4 h + g covers
+    // rows 16 h .. + 15 of the quarter and columns 8 g .. + 7.  Value c = 4 f + u
+    // of a thread is row 16 h + fr + 8 (u >> 1), column 8 g + fc + (u & 1).
+    const int lq = warp & 3;
+    const int cq = (warp - 2) >> 2;
+    const int fr = lane >> 2, fc = 2 * (lane & 3);
     bool ok = true;
     int gc = 0;  // chunks drained so far (all tiles)
     for (int q = blockIdx.x; q < p.tiles && ok; q += gridDim.x) {
@@ -433,18 +458,19 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * DC);
 #pragma unroll
-        for (int c0 = 0; c0 < DC; c0 += 4) {
+        for (int f = 0; f < 8; ++f) {
+          const uint32_t tl = tmem + ((uint32_t)(lq * 32 + 16 * (f >> 2)) << 16) +
+                              (uint32_t)(cq * DC + 8 * (f & 3));
           uint32_t r0[4], r1[4], r2[4], r3[4];
-          tmem_ld4(tl + c0, r0);
-          tmem_ld4(tl + 128 + c0, r1);
-          tmem_ld4(tl + 256 + c0, r2);
-          tmem_ld4(tl + 384 + c0, r3);
+          tmem_ld16x256(tl, r0);
+          tmem_ld16x256(tl + 128, r1);
+          tmem_ld16x256(tl + 256, r2);
+          tmem_ld16x256(tl + 384, r3);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            fold(hi[c0 + u], lo[c0 + u], __uint_as_float(r0[u]), __uint_as_float(r1[u]),
+            fold(hi[4 * f + u], lo[4 * f + u], __uint_as_float(r0[u]), __uint_as_float(r1[u]),
                  __uint_as_float(r2[u]), __uint_as_float(r3[u]));
         }
         // the accumulators are free for the next chunk (of this tile or the next)
@@ -453,46 +479,67 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(const __grid_consta
         if (lane == 0) bar_arrive(acce);
       }
       if (!ok) break;
-      // assemble fp64 (while the issuer runs the next tile): C = alpha 2^(eA + eB - 14) (hi + lo)
-      int i = 0, valid;
-      double *dst;
-      int ea;
-      if (MODE == 0) {
-        i = t.m0 + row;
-        valid = i < p.M;
-        if (valid && !OZ_IN(t.zb * p.efa_bs + i, p.efa_cap, 10)) valid = 0;
-        ea = valid ? row_scale(p.efa[t.zb * p.efa_bs + i]) : 0;
-        dst = p.ksplit > 1
-                  ? p.C + (long long)(t.zb * p.ksplit + t.split) * p.M * p.N + (long long)i * p.N
-                  : p.C + t.zb * p.sC + (long long)i * p.ldc;
-      } else {
-        const int m = t.mt * 8 + (row >> 4), j = t.jt * 16 + (row & 15);
-        valid = m < p.M && j < p.M;
-        if (!OZ_IN((long long)t.rt * BM + row, p.efa_cap, 11)) valid = 0;
-        ea = valid ? row_scale(p.efa[(long long)t.rt * BM + row]) : 0;
-        dst = p.C + ((long long)j * p.M + m) * p.N;
+      // assemble fp64 (while the issuer runs the next tile): C = +-2^(eA + eB - 14) (hi + lo).
+      // A thread's four rows: hr = 2 h + (u >> 1), tile row 32 lq + 16 h + fr + 8 (u >> 1).
+      double *dst[4];
+      int ea[4];
+      bool valid[4];
+#pragma unroll
+      for (int hr = 0; hr < 4; ++hr) {
+        const int row = lq * 32 + 16 * (hr >> 1) + fr + 8 * (hr & 1);
+        bool v;
+        if (MODE == 0) {
+          const int i = t.m0 + row;
+          v = i < p.M;
+          if (v && !OZ_IN(t.zb * p.efa_bs + i, p.efa_cap, 10)) v = false;
+          ea[hr] = v ? row_scale(p.efa[t.zb * p.efa_bs + i]) : 0;
+          dst[hr] = p.ksplit > 1 ? p.C + (long long)(t.zb * p.ksplit + t.split) * p.M * p.N +
+                                       (long long)i * p.N
+                                 : p.C + t.zb * p.sC + (long long)i * p.ldc;
+        } else {
+          const int m = t.mt * 8 + (row >> 4), j = t.jt * 16 + (row & 15);
+          v = m < p.M && j < p.M;
+          if (!OZ_IN((long long)t.rt * BM + row, p.efa_cap, 11)) v = false;
+          ea[hr] = v ? row_scale(p.efa[(long long)t.rt * BM + row]) : 0;
+          dst[hr] = p.C + ((long long)j * p.M + m) * p.N;
+        }
+        valid[hr] = v;
       }
       const int ncol = p.N;
-      if (valid) {
-        const int j0 = t.n0 + cq * DC;
-        // alpha = +-1 (every product of the block) flips the sign bit only;
-        // any other alpha takes one fp64 multiply per output
-        const bool neg = p.alpha == -1.0, plain = p.alpha == 1.0 || neg;
-        const unsigned long long sgn = neg ? (1ull << 63) : 0ull;
-        const long long eb_off = MODE == 0 && !p.bshared ? t.zb * p.efb_bs : 0;
+      // the sign of -1 products flips the sign bit only
+      const unsigned long long sgn = p.neg ? (1ull << 63) : 0ull;
+      const long long eb_off = MODE == 0 && !p.bshared ? t.zb * p.efb_bs : 0;
 #pragma unroll
-        for (int c = 0; c < DC; ++c) {
-          const int j = j0 + c;
-          if (j < ncol) {
-            const long long ie = eb_off + j;
-            if (!OZ_IN(ie, p.efb_cap, 12)) continue;
-            if (!OZ_IN((long long)(dst + j - p.C), p.ccap, 13)) continue;
-            const int E = ea + row_scale(p.efb[ie]) - 14;
-            const double v = df_to_f64(hi[c], lo[c], E);
-            if (plain)
-              dst[j] = __longlong_as_double((long long)((unsigned long long)__double_as_longlong(v) ^ sgn));
-            else
-              dst[j] = v * p.alpha;
+      for (int f = 0; f < 8; ++f) {
+        const int j = t.n0 + cq * DC + 8 * (f & 3) + fc;  // this thread's column pair j, j + 1
+        if (j >= ncol) continue;
+        const bool two = j + 1 < ncol;
+        if (!OZ_IN(eb_off + j + (two ? 1 : 0), p.efb_cap, 12)) continue;
+        const int eb0 = row_scale(p.efb[eb_off + j]) - 14;
+        const int eb1 = two ? row_scale(p.efb[eb_off + j + 1]) - 14 : 0;
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+          const int hr = 2 * (f >> 2) + rr, c = 4 * f + 2 * rr;
+          if (!valid[hr]) continue;
+          double *d = dst[hr] + j;
+          if (!OZ_IN((long long)(d - p.C) + (two ? 1 : 0), p.ccap, 13)) continue;
+          const double v0 = __longlong_as_double(
+              (long long)((unsigned long long)__double_as_longlong(
+                              df_to_f64(hi[c], lo[c], ea[hr] + eb0)) ^
+                          sgn));
+          if (two) {
+            const double v1 = __longlong_as_double(
+                (long long)((unsigned long long)__double_as_longlong(
+                                df_to_f64(hi[c + 1], lo[c + 1], ea[hr] + eb1)) ^
+                            sgn));
+            if (p.vec2) {
+              *reinterpret_cast<double2 *>(d) = make_double2(v0, v1);
+            } else {
+              d[0] = v0;
+              d[1] = v1;
+            }
+          } else {
+            d[0] = v0;
           }
         }
       }
@@ -552,11 +599,20 @@ __device__ __forceinline__ double view_at(const OzView &v, int b, long long r, l
   return v.x[o];
 }
 
-// Load a 32 x 64 tile of the view into s[r][k] (zeros outside); blockDim.x
+// Column k of row r of a 32 x 64 shared tile sits at s[r][tile_col(r, k)]: the
+// low four bits of k are XORed with bits 4-5 of k (times 2) and with r, so
+// that the tile's writes (16 rows at one column, or 16 columns of one row)
+// and the digit pass's reads (2 rows x 8 columns 8 apart) each touch 16
+// different 8-byte bank pairs per half warp.
+__device__ __forceinline__ int tile_col(int r, int k) {
+  return k ^ ((((k >> 4) & 3) << 1) ^ (r & 15));
+}
+
+// Load a 32 x 64 tile of the view into s (zeros outside); blockDim.x
 // == 256, eight values per thread, all eight loads issued before the stores.
 constexpr int SLICE_THREADS = 256, SLICE_PER = SR * SK / SLICE_THREADS;
 __device__ __forceinline__ void load_tile(const OzView &v, int b, long long r0, long long k0,
-                                          int rows, long long K, double (*s)[SK + 1]) {
+                                          int rows, long long K, double (*s)[SK]) {
   const bool rmaj = v.rs == 1;
   const long long k1_0 = k0 / v.k2pad, k2_0 = k0 - k1_0 * v.k2pad;  // once per tile
   double val[SLICE_PER];
@@ -580,7 +636,7 @@ __device__ __forceinline__ void load_tile(const OzView &v, int b, long long r0, 
   for (int i = 0; i < SLICE_PER; ++i) {
     const int idx = threadIdx.x + i * SLICE_THREADS;
     const int r = rmaj ? idx % SR : idx / SK, k = rmaj ? idx / SR : idx % SK;
-    s[r][k] = val[i];
+    s[r][tile_col(r, k)] = val[i];
   }
 }
 
@@ -590,7 +646,7 @@ __device__ __forceinline__ int ef_of(double x) {
 
 __global__ void __launch_bounds__(256) oz_rowmax_kernel(OzView v, int rows, long long K,
                                                         int *__restrict__ ef) {
-  __shared__ double s[SR][SK + 1];
+  __shared__ double s[SR][SK];
   const int b = blockIdx.z;
   // one tile per block: blockIdx.x = row tile + (rows / SR) * column tile
   const long long rtiles = (rows + SR - 1) / SR;
@@ -599,15 +655,16 @@ __global__ void __launch_bounds__(256) oz_rowmax_kernel(OzView v, int rows, long
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int r = warp; r < SR; r += blockDim.x / 32) {
-    int m = max(ef_of(s[r][lane]), ef_of(s[r][lane + 32]));
+    int m = max(ef_of(s[r][tile_col(r, lane)]), ef_of(s[r][tile_col(r, lane + 32)]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0 && r0 + r < rows && m > 0) atomicMax(&ef[(long long)b * rows + r0 + r], m);
   }
 }
 
-// The OZ_S balanced base-256 digits of x relative to the row scale 2^e.
-__device__ __forceinline__ void digits_of(double x, int e, float *d) {
+// The OZ_S balanced base-256 digits of x relative to the row scale 2^e, as
+// integers carrying x's sign: x ~ 2^e sum_p dd[p] 2^(-7 - 8 p).
+__device__ __forceinline__ void digit_ints(double x, int e, int *dd) {
   const long long bits = __double_as_longlong(x);
   const int efx = (int)((bits >> 52) & 0x7FF);
   unsigned long long M = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
@@ -618,7 +675,6 @@ __device__ __forceinline__ void digits_of(double x, int e, float *d) {
   const int sh = 1075 - FB + e - max(efx, 1);
   long long F = 0;
   if (sh < 64) F = (long long)((M + (1ull << (sh - 1))) >> sh);
-  int dd[OZ_S];
 #pragma unroll
   for (int p = OZ_S - 1; p > 0; --p) {
     int lo8 = (int)(F & 255);
@@ -627,10 +683,29 @@ __device__ __forceinline__ void digits_of(double x, int e, float *d) {
     F = (F - lo8) >> 8;
   }
   dd[0] = (int)F;
-  const float sgn = bits < 0 ? -1.f : 1.f;
+  if (bits < 0) {
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) dd[p] = -dd[p];
+  }
+}
+
+// Digit p of x0 and of x1 as one bf16 pair (x0 in the low half) for every p.
+// A digit d 2^(-8 p) has |d| <= 2^7 + 1, at most 8 significant bits, so its
+// bf16 is exactly the upper half of its fp32 pattern; float(d) is formed as
+// (1.5 2^23 + d) read from its integer pattern minus 1.5 2^23, so that no
+// conversion instruction is needed (the conversion pipe runs at a quarter
+// of the fp32 rate and limited the slicer).
+__device__ __forceinline__ void digit_pairs(double x0, double x1, int e, uint32_t *w) {
+  int a[OZ_S], b[OZ_S];
+  digit_ints(x0, e, a);
+  digit_ints(x1, e, b);
   const float sc[6] = {1.f, 0x1p-8f, 0x1p-16f, 0x1p-24f, 0x1p-32f, 0x1p-40f};
 #pragma unroll
-  for (int p = 0; p < OZ_S; ++p) d[p] = sgn * (float)dd[p] * sc[p];
+  for (int p = 0; p < OZ_S; ++p) {
+    const float fa = (__int_as_float(0x4B400000 + a[p]) - 12582912.0f) * sc[p];
+    const float fb = (__int_as_float(0x4B400000 + b[p]) - 12582912.0f) * sc[p];
+    w[p] = __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632);
+  }
 }
 
 // Offsets of column kk of row br (= b rows + r) in the interleaved digit
@@ -644,7 +719,7 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
                                                         const int *__restrict__ ef,
                                                         __nv_bfloat16 *__restrict__ out,
                                                         long long ld, long long g1) {
-  __shared__ double s[SR][SK + 1];
+  __shared__ double s[SR][SK];
   const int b = blockIdx.z;
   // one tile per block: blockIdx.x = row tile + (rows / SR) * column tile
   const long long rtiles = (rows + SR - 1) / SR;
@@ -660,14 +735,10 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(OzView v, int rows, long
   uint32_t w[OZ_S][KC / 2];
 #pragma unroll
   for (int u = 0; u < KC; u += 2) {
-    float d0[OZ_S], d1[OZ_S];
-    digits_of(s[r][c0 + u], e, d0);
-    digits_of(s[r][c0 + u + 1], e, d1);
+    uint32_t wp[OZ_S];
+    digit_pairs(s[r][tile_col(r, c0 + u)], s[r][tile_col(r, c0 + u + 1)], e, wp);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) {
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[p], d1[p]);
-      w[p][u / 2] = *reinterpret_cast<const uint32_t *>(&h2);
-    }
+    for (int p = 0; p < OZ_S; ++p) w[p][u / 2] = wp[p];
   }
   const long long blk = ((long long)b * rows + rr) * (ld / 16) + (kk0 >> 4);
   if (!OZ_IN(blk * 64 + 63, g1, 31)) return;
@@ -768,14 +839,10 @@ __global__ void __launch_bounds__(256) oz_digits_kc_kernel(OzView v, int rows, l
     uint32_t w[OZ_S][KC / 2];
 #pragma unroll
     for (int u = 0; u < KC; u += 2) {
-      float d0[OZ_S], d1[OZ_S];
-      digits_of(x[u], e, d0);
-      digits_of(x[u + 1], e, d1);
+      uint32_t wp[OZ_S];
+      digit_pairs(x[u], x[u + 1], e, wp);
 #pragma unroll
-      for (int p = 0; p < OZ_S; ++p) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[p], d1[p]);
-        w[p][u / 2] = *reinterpret_cast<const uint32_t *>(&h2);
-      }
+      for (int p = 0; p < OZ_S; ++p) w[p][u / 2] = wp[p];
     }
     const long long blk = br * (ld / 16) + (k0 >> 4);
     if (!OZ_IN(blk * 64 + 63, g1, 32)) continue;
@@ -783,6 +850,62 @@ __global__ void __launch_bounds__(256) oz_digits_kc_kernel(OzView v, int rows, l
     for (int p = 0; p < OZ_S; ++p)
       *reinterpret_cast<uint4 *>(out + digit_off(blk, (int)(k0 & 15), p, g1)) =
           make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+}
+
+// Short rows (ld <= 256 NG) of the same sources in one pass: one warp per row
+// (grid-stride over batch x rows) holds the row in registers, 8 consecutive
+// columns per lane per group, reduces the maximum exponent across the warp
+// and writes the digits.  Reads the source once; no shared memory.
+template <int NG>
+__global__ void __launch_bounds__(256) oz_slice_rowwarp_kernel(OzView v, int rows, long long K,
+                                                               long long nrows,
+                                                               int *__restrict__ ef,
+                                                               __nv_bfloat16 *__restrict__ out,
+                                                               long long ld, long long g1) {
+  const int lane = threadIdx.x & 31;
+  const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long br = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; br < nrows;
+       br += wstride) {
+    const int b = (int)(br / rows);
+    const long long r = br - (long long)b * rows;
+    double x[NG][KC];
+    int m = 0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const long long k0 = ((long long)g * 32 + lane) * KC;
+      if (k0 < K) {
+        load8(v, b, r, k0, K, x[g]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < KC; ++u) x[g][u] = 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < KC; ++u) m = max(m, ef_of(x[g][u]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) ef[br] = m;
+    const int e = row_scale(m);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const long long k0 = ((long long)g * 32 + lane) * KC;
+      if (k0 >= ld) continue;
+      uint32_t w[OZ_S][KC / 2];
+#pragma unroll
+      for (int u = 0; u < KC; u += 2) {
+        uint32_t wp[OZ_S];
+        digit_pairs(x[g][u], x[g][u + 1], e, wp);
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) w[p][u / 2] = wp[p];
+      }
+      const long long blk = br * (ld / 16) + (k0 >> 4);
+      if (!OZ_IN(blk * 64 + 63, g1, 35)) continue;
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p)
+        *reinterpret_cast<uint4 *>(out + digit_off(blk, (int)(k0 & 15), p, g1)) =
+            make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
   }
 }
 
@@ -816,6 +939,10 @@ __global__ void __launch_bounds__(256) oz_rowmax_rmaj_kernel(OzView v, int rows,
 // reads across the rows), takes each row's maximum there and writes the
 // digits along K in 16-byte stores; ef is written, not accumulated.
 constexpr int SHORT_K = 256, SHORT_R = 16;
+// Row r of column kk sits at s[kk][r ^ ((kk >> 3) & 15)]: with the odd row
+// stride, a half warp's 16 rows at one column and the digit pass's 16 column
+// groups 8 apart in one row each fall on 16 different 8-byte bank pairs.
+__device__ __forceinline__ int short_col(int kk, int r) { return r ^ ((kk >> 3) & 15); }
 __global__ void __launch_bounds__(256) oz_slice_short_kernel(OzView v, int rows, long long K,
                                                              int *__restrict__ ef,
                                                              __nv_bfloat16 *__restrict__ out,
@@ -829,13 +956,14 @@ __global__ void __launch_bounds__(256) oz_slice_short_kernel(OzView v, int rows,
 #pragma unroll 4
   for (int idx = t; idx < SHORT_R * kn; idx += 256) {
     const int r = idx % SHORT_R, kk = idx / SHORT_R;
-    s[kk][r] = r0 + r < rows ? view_at(v, b, r0 + r, 0, kk) : 0.0;
+    s[kk][short_col(kk, r)] = r0 + r < rows ? view_at(v, b, r0 + r, 0, kk) : 0.0;
   }
   __syncthreads();
   {
     const int r = t % SHORT_R, part = t / SHORT_R;
     int m = 0;
-    for (int kk = part; kk < kn; kk += 256 / SHORT_R) m = max(m, ef_of(s[kk][r]));
+    for (int kk = part; kk < kn; kk += 256 / SHORT_R)
+      m = max(m, ef_of(s[kk][short_col(kk, r)]));
     wm[part][r] = m;
   }
   __syncthreads();
@@ -854,14 +982,11 @@ __global__ void __launch_bounds__(256) oz_slice_short_kernel(OzView v, int rows,
     uint32_t w[OZ_S][KC / 2];
 #pragma unroll
     for (int u = 0; u < KC; u += 2) {
-      float d0[OZ_S], d1[OZ_S];
-      digits_of(k0 + u < kn ? s[k0 + u][r] : 0.0, e, d0);
-      digits_of(k0 + u + 1 < kn ? s[k0 + u + 1][r] : 0.0, e, d1);
+      uint32_t wp[OZ_S];
+      digit_pairs(k0 + u < kn ? s[k0 + u][short_col(k0 + u, r)] : 0.0,
+                  k0 + u + 1 < kn ? s[k0 + u + 1][short_col(k0 + u + 1, r)] : 0.0, e, wp);
 #pragma unroll
-      for (int p = 0; p < OZ_S; ++p) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[p], d1[p]);
-        w[p][u / 2] = *reinterpret_cast<const uint32_t *>(&h2);
-      }
+      for (int p = 0; p < OZ_S; ++p) w[p][u / 2] = wp[p];
     }
     const long long blk = ((long long)b * rows + r0 + r) * (ld / 16) + (k0 >> 4);
     if (!OZ_IN(blk * 64 + 63, g1, 34)) continue;
@@ -1025,16 +1150,52 @@ cudaError_t prepare() {
   return cudaSuccess;
 }
 
+// K splits of a dense product: when its output tiles leave SMs idle, K is
+// split so that the rounds of tiles over the SMs times the K steps of a split,
+// plus the split partials' extra traffic, is least.  Costs in units of one K
+// step of one tile (21 digit products of 128 x 128 x 16, ~0.9 us at the
+// tensor rate): a tile's drain and stores ~9 steps; the partials are written
+// and read back at ~5.3 MB per step (HBM), plus ~6 steps for the reduction launch.
 void plan(const OzGemm &g, int *ksplit, int *kst) {
   const int steps = ceil_div(g.A.K, KS);
   const long long tiles = (long long)ceil_div(g.M, BM) * ceil_div(g.N, BN) * g.batch;
-  int ks = 1;
-  if (tiles < 152 && steps >= 2 * CHUNK)
-    ks = (int)std::max<long long>(1, std::min<long long>((152 + tiles - 1) / tiles, steps / CHUNK));
-  int per = ceil_div(steps, ks);
-  per = ceil_div(per, CHUNK) * CHUNK;  // whole chunks per split
-  *kst = std::min(per, steps);
-  *ksplit = ceil_div(steps, *kst);
+  const long long sms = 152;
+  int best_per = steps;
+  if (tiles < 4 * sms && steps >= 2) {
+    double best = (double)((tiles + sms - 1) / sms) * (steps + 9);
+    const double part = (double)g.M * g.N * g.batch * 8.0 / 5.3e6;
+    const int maxks = std::min(64, steps);
+    for (int ks = 2; ks <= maxks; ++ks) {
+      const int per = ceil_div(steps, ks);
+      const int kp = ceil_div(steps, per);  // splits actually made
+      if (kp != ks) continue;
+      const double cost =
+          (double)((tiles * kp + sms - 1) / sms) * (per + 9) + (kp + 1) * part + 6.0;
+      if (cost < best) {
+        best = cost;
+        best_per = per;
+      }
+    }
+  }
+  *kst = best_per;
+  *ksplit = ceil_div(steps, best_per);
+}
+
+// Tile order of a dense product.  The CTAs run in waves of one tile per SM
+// over consecutive queue entries and read each K window of the waves' row
+// tiles of A and column tiles of B about together, so a wave reads from HBM
+// the distinct m tiles and n tiles it spans; an operand held whole in L2
+// (~64 MB of digits at most) is read once.  m-fastest when that reads less.
+bool m_fastest(const OzGemm &g) {
+  const long long mt = ceil_div(g.M, BM), nt = ceil_div(g.N, BN), sms = 152;
+  const double kb = (double)g.A.K * OZ_S * 2.0;  // digit bytes of one row
+  const bool a_l2 = (double)g.M * kb * g.A.batch <= 64e6;
+  const bool b_l2 = (double)g.N * kb * g.B.batch <= 64e6;
+  const long long wn = std::min(nt, sms), wm = std::min(mt, sms);
+  // n fastest: a wave spans min(nt, sms) n tiles and ~sms / nt m tiles
+  const double cn = (b_l2 ? 0.0 : (double)wn) + (a_l2 ? 0.0 : (double)ceil_div(sms, wn));
+  const double cm = (a_l2 ? 0.0 : (double)wm) + (b_l2 ? 0.0 : (double)ceil_div(sms, wm));
+  return cm < cn;
 }
 
 }  // namespace
@@ -1080,6 +1241,21 @@ cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s) {
   const bool kc = v.cs2 == 1 && v.k2off == 0 && v.k2pad >= out.K && v.k2n >= out.K &&
                   base % 16 == 0 && v.rs % 2 == 0 && v.bs % 2 == 0 &&
                   kcb * out.rows <= 0x7FFFFFFFLL;
+  if (kc && out.ld <= 256 * 4) {
+    const long long nrows = (long long)out.batch * out.rows;
+    const int grid = (int)std::min<long long>(ceil_div(nrows, 8LL), 152LL * 16);
+    if (out.ld <= 256)
+      oz_slice_rowwarp_kernel<1><<<grid, 256, 0, s>>>(v, out.rows, out.K, nrows, out.ef, out.d,
+                                                      out.ld, g1);
+    else if (out.ld <= 512)
+      oz_slice_rowwarp_kernel<2><<<grid, 256, 0, s>>>(v, out.rows, out.K, nrows, out.ef, out.d,
+                                                      out.ld, g1);
+    else
+      oz_slice_rowwarp_kernel<4><<<grid, 256, 0, s>>>(v, out.rows, out.K, nrows, out.ef, out.d,
+                                                      out.ld, g1);
+    ++launch_counter();
+    return cudaGetLastError();
+  }
   if (kc) {
     dim3 gm((unsigned)(kcb * out.rows), 1, out.batch);
     oz_rowmax_kc_kernel<<<gm, 256, 0, s>>>(v, out.rows, out.K, out.ef);
@@ -1137,7 +1313,7 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   if (g.A.K != g.B.K || g.A.rows != g.M || g.B.rows != g.N || g.A.batch != g.batch ||
       (g.B.batch != 1 && g.B.batch != g.batch))
     return cudaErrorInvalidValue;
-  if (g.A.K <= 0) return cudaErrorInvalidValue;
+  if (g.A.K <= 0 || (g.alpha != 1.0 && g.alpha != -1.0)) return cudaErrorInvalidValue;
   int ks, kst;
   plan(g, &ks, &kst);
   if (ks > 1 && work_elems < (size_t)ks * g.batch * g.M * g.N) return cudaErrorInvalidValue;
@@ -1156,8 +1332,11 @@ cudaError_t oz_gemm(const OzGemm &g, double *work, size_t work_elems, cudaStream
   p.efb = g.B.ef;
   p.efa_bs = g.M;
   p.efb_bs = g.N;
-  p.alpha = g.alpha;
+  p.neg = g.alpha == -1.0;
   p.C = ks > 1 ? work : g.C;
+  p.vec2 = ((uintptr_t)p.C % 16 == 0) &&
+           (ks > 1 ? g.N % 2 == 0 : g.ldc % 2 == 0 && (g.batch == 1 || g.sC % 2 == 0));
+  p.mfast = m_fastest(g);
   p.ldc = g.ldc;
   p.sC = g.sC;
   p.err = g.err;
@@ -1262,7 +1441,7 @@ cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, doub
   const int tiles = x.mtiles * x.jtiles;
   if (X.batch != tiles || X.rows != BM || X.K != x.kx || At.rows != x.na ||
       At.K != (long long)x.n * x.ldl || At.ld != At.K || At.batch != 1 || tiles > 65535 ||
-      X.ld % 16 || x.ldl % 16)
+      X.ld % 16 || x.ldl % 16 || (alpha != 1.0 && alpha != -1.0))
     return cudaErrorInvalidValue;
   OzParams p;
   std::memset(&p, 0, sizeof(p));
@@ -1286,7 +1465,8 @@ cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, doub
   p.ksplit = 1;
   p.efa = X.ef;
   p.efb = At.ef;
-  p.alpha = alpha;
+  p.neg = alpha == -1.0;
+  p.vec2 = ((uintptr_t)T % 16 == 0) && x.na % 2 == 0;
   p.C = T;
   p.bk = x.bk;
   p.lb0 = x.lb0;

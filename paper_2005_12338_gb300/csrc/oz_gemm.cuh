@@ -67,7 +67,8 @@ struct OzView {
 cudaError_t oz_slice(const OzView &v, const OzDigits &out, cudaStream_t s);
 
 // C[b][i][j] = alpha * sum_k A[b][i][k] B[b'][j][k] in fp64, b' = b or 0 when
-// B.batch == 1.  A: M x K, B: N x K digits.  C[b*sC + i*ldc + j].
+// B.batch == 1.  A: M x K, B: N x K digits.  C[b*sC + i*ldc + j].  alpha is
+// +1 or -1 (anything else: cudaErrorInvalidValue).
 // K is split over CTAs when the output has few tiles; the split partials go
 // to `work` (oz_gemm_work() doubles) and are reduced in a fixed order.
 struct OzGemm {
@@ -108,7 +109,7 @@ OzExch oz_exch_geometry(int n, int na, int bk);
 // mtiles * jtiles), from D [P][P] and pidx; then sliced with oz_slice.
 cudaError_t oz_exch_gather(const OzExch &x, const double *D, int P, const int *pidx,
                            double *xs, long long xs_cap, cudaStream_t s);
-// T[(j*n + m)*na + q] = alpha * the contraction, fp64.  X: digits [tiles][128][kx];
+// T[(j*n + m)*na + q] = alpha * the contraction, fp64, alpha = +1 or -1.  X: digits [tiles][128][kx];
 // At: digits [1][na][n*ldl] (k major, l' minor).
 cudaError_t oz_exch(const OzExch &x, const OzDigits &X, const OzDigits &At, double *T,
                     long long tcap, double alpha, int *err, cudaStream_t s, int wait_polls = 0);
