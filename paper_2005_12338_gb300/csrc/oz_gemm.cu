@@ -953,10 +953,20 @@ __global__ void __launch_bounds__(256) oz_slice_short_kernel(OzView v, int rows,
   const int b = blockIdx.z;
   const long long r0 = (long long)blockIdx.x * SHORT_R;
   const int t = threadIdx.x, kn = (int)K;
-#pragma unroll 4
-  for (int idx = t; idx < SHORT_R * kn; idx += 256) {
-    const int r = idx % SHORT_R, kk = idx / SHORT_R;
-    s[kk][short_col(kk, r)] = r0 + r < rows ? view_at(v, b, r0 + r, 0, kk) : 0.0;
+  // all of a thread's loads are issued before any is stored: the 16 rows of a
+  // column are one 128-byte piece and the columns lie far apart, so the
+  // pass needs many loads in flight per SM
+  constexpr int LPT = SHORT_K * SHORT_R / 256;
+  double val[LPT];
+#pragma unroll
+  for (int i = 0; i < LPT; ++i) {
+    const int idx = t + i * 256, r = idx % SHORT_R, kk = idx / SHORT_R;
+    val[i] = kk < kn && r0 + r < rows ? view_at(v, b, r0 + r, 0, kk) : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < LPT; ++i) {
+    const int idx = t + i * 256, r = idx % SHORT_R, kk = idx / SHORT_R;
+    if (kk < kn) s[kk][short_col(kk, r)] = val[i];
   }
   __syncthreads();
   {
