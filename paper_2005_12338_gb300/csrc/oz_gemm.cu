@@ -14,11 +14,12 @@
 //                  accumulators in tensor memory, one per level p + q = 0, 1,
 //                  2 and one for p + q >= 3 (4 x 128 of the 512 columns);
 //   warps 2-17     drain: after every 256 terms of K (16 steps) they read the
-//                  four accumulators (tcgen05.ld) and add them exactly into
-//                  double-float running totals held in registers (each thread:
-//                  one row, 32 columns), then release the accumulators; at the
-//                  end they assemble fp64 from the running totals with integer
-//                  exponent arithmetic and one fp64 add per output.
+//                  four accumulators (tcgen05.ld, 16 x 8 fragments) and add them
+//                  exactly into double-float running totals held in registers
+//                  (each thread: 32 outputs, column pairs of four rows), then
+//                  release the accumulators; at the end they assemble fp64 from
+//                  the running totals with integer exponent arithmetic and
+//                  store column pairs as 16-byte stores.
 // Levels 0-2 are exact over 256 terms (< 2^24 grid units), so a chunk's sum
 // a0 + a1 + a2 is exact in two TwoSums; level >= 3 (~2^-24 of the result)
 // and the running sum round at ~2^-48 relative.
@@ -179,11 +180,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           s_u32(bar))
       : "memory");
-}
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t *r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
 }
 // 16 lanes x 256 bits (8 columns): thread t holds lane (t >> 2) at columns
 // 2 (t & 3) and 2 (t & 3) + 1 in r[0], r[1], and lane (t >> 2) + 8 at the same
